@@ -1,0 +1,206 @@
+/*
+ * cimmino.h -- C ABI of the GB300 (sm_103a) CG-accelerated block Cimmino solver.
+ *
+ * The library solves a sparse nonsymmetric, nonsingular system A x = f that is
+ * split into K block rows A_i (m_i x n, sum m_i = n; the block-row partition of
+ * Eq. 1.2).  It runs Algorithm 2 of Torun, Manguoglu and Aykanat, "A Novel
+ * Partitioning Method for Accelerating the Block Cimmino Algorithm" (arXiv
+ * 1710.07769): classical CG on H x = xi with H = sum_i A_i^+ A_i (Eq. 1.5),
+ * A_i^+ = A_i^T (A_i A_i^T)^{-1} (Section 1) and xi = sum_i A_i^+ f_i
+ * (Section 1.1), from x^(0) = 0 (Section 3.1).
+ *
+ * The projections are applied through the Gram blocks G_i = A_i A_i^T, the
+ * diagonal blocks of C = A A^T (Section 2.3, whose pattern and |values| are the
+ * row inner-product graph of Section 2.1), factorised once as G_i = L_i L_i^T.
+ * Rows are first scaled to unit 2-norm (Section 2.1; H does not depend on row
+ * scaling) and permuted into block order (A^Pi = P A, Section 2.2; columns keep
+ * their order).
+ *
+ * Conventions for every entry point:
+ *  - Return value: CIMMINO_OK (0) or a negative CIMMINO_E* code; the message of
+ *    the last failure of a context is available from cimmino_last_error().
+ *  - Device pointers refer to the CUDA device that is current when
+ *    cimmino_setup() is called; the context stays bound to that device.
+ *  - All device work is ordered on opts.stream (a cudaStream_t; NULL selects
+ *    the legacy default stream).  Every call returns after its results are
+ *    complete, i.e. calls synchronise the stream before returning.
+ *  - A context may be used by one host thread at a time.  There is no global
+ *    mutable state: independent contexts may be used concurrently.
+ */
+#ifndef CIMMINO_H
+#define CIMMINO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CIMMINO_OK 0
+#define CIMMINO_EINVAL (-1)       /* invalid argument or malformed CSR / partition   */
+#define CIMMINO_ENOMEM (-2)       /* device or host allocation failed                */
+#define CIMMINO_ESINGULAR (-3)    /* a Gram block is not positive definite in FP64:  */
+                                  /* A_i is rank deficient (or a row is zero)        */
+#define CIMMINO_ENOCONV (-4)      /* max_iter reached; X holds the last iterate      */
+#define CIMMINO_EBREAKDOWN (-5)   /* CG breakdown: p^T H p <= 0 or not finite        */
+#define CIMMINO_ETIMEOUT (-6)     /* a device-side wait ran out of its budget        */
+#define CIMMINO_ECUDA (-7)        /* a CUDA runtime call failed                      */
+#define CIMMINO_EUNSUPPORTED (-8) /* input beyond a documented size limit           */
+
+/* ---- precision of the Gram factors and triangular solves ---- */
+#define CIMMINO_FP64 0        /* FP64 factors, FP64 solves, no refinement             */
+#define CIMMINO_FP32_REFINE 1 /* FP32 factors and solves with FP32 accumulation, FP64 */
+                              /* iterative refinement of every inner solve, FP64       */
+                              /* refactorisation of blocks with a poor pivot ratio     */
+
+/* ---- storage of the factors ---- */
+#define CIMMINO_LAYOUT_DENSE 0   /* every T x T tile of the lower triangle is stored    */
+#define CIMMINO_LAYOUT_SKYLINE 1 /* tile row I stores tiles J0(I)..I, where J0(I) is   */
+                                 /* the first tile column holding a nonzero of G_i in  */
+                                 /* that tile row; Cholesky fill stays inside this     */
+                                 /* envelope, so the factor is exact, not approximate  */
+
+/* A square sparse matrix in CSR form.  Column indices must be sorted strictly
+ * increasing inside each row and lie in [0, n).  The arrays are read only and
+ * stay owned by the caller; they are copied during cimmino_setup(). */
+typedef struct cimmino_csr {
+  int64_t n;              /* rows = columns                                         */
+  int64_t nnz;            /* = row_ptr[n]                                           */
+  const int64_t *row_ptr; /* n + 1 offsets, row_ptr[0] = 0                          */
+  const int32_t *col_idx; /* nnz column indices                                     */
+  const double *val;      /* nnz values                                             */
+  int32_t on_device;      /* 1: the three arrays are device pointers, 0: host       */
+} cimmino_csr;
+
+typedef struct cimmino_opts {
+  int32_t precision;      /* CIMMINO_FP64 (default) or CIMMINO_FP32_REFINE           */
+  int32_t layout;         /* CIMMINO_LAYOUT_SKYLINE (default) or _DENSE              */
+  int32_t tile;           /* tile edge T of the factor layout: 0 = default (64)      */
+  int32_t refine_max;     /* refinement steps per inner solve (default 6)           */
+  double refine_tol;      /* stop refining when ||G_i y - u_i||_2 <= refine_tol *   */
+                          /* ||u_i||_2 (default 1e-13)                               */
+  double pivot_ratio_min; /* FP32 block refactored in FP64 when min_j L_jj^2 /      */
+                          /* max_j G_jj < pivot_ratio_min (default 1e-4)            */
+  int32_t max_iter;       /* CG iteration limit (default 10000, Section 3.1)        */
+  int32_t use_graph;      /* 1 (default): capture CG iterations as a CUDA graph     */
+  int32_t check_every;    /* CG iterations between convergence read-backs (def. 8)  */
+  int32_t keep_aat;       /* 1: keep C = A A^T for cimmino_get_aat() (default 0)    */
+  void *stream;           /* cudaStream_t for all device work (NULL: default)      */
+} cimmino_opts;
+
+/* Statistics of one right-hand side of one system. */
+typedef struct cimmino_stats {
+  int32_t status;             /* CIMMINO_OK, _ENOCONV or _EBREAKDOWN               */
+  int32_t iters;              /* projection sums H p evaluated (xi excluded)       */
+  double rel_res;             /* ||f - A x||_2 / ||f||_2 of the returned x          */
+  double backward_err;        /* gamma of Eq. 3.1 for the returned x                */
+  int64_t refine_steps_total; /* refinement steps summed over blocks and solves     */
+  int32_t refine_steps_max;   /* largest number of steps of one inner solve         */
+  int32_t fallbacks;          /* blocks refactored in FP64 (whole context)          */
+  double t_setup_ms;          /* scaling, permutation, A^T, C = A A^T, G_i extraction */
+  double t_factor_ms;         /* Cholesky of all G_i (including FP64 fallbacks)     */
+  double t_solve_ms;          /* this solve: xi plus all CG iterations              */
+  int64_t nnz_aat;            /* nnz(C)                                              */
+  int64_t factor_bytes;       /* bytes of all stored factor tiles                    */
+} cimmino_stats;
+
+typedef struct cimmino_ctx cimmino_ctx;
+
+/* Fill *opts with the defaults listed in cimmino_opts. */
+void cimmino_opts_default(cimmino_opts *opts);
+
+/* Set up one system: copy A, scale rows to unit 2-norm (Section 2.1), permute rows
+ * by perm (Section 2.2), build A^T, C = A A^T (Section 2.3), the Gram blocks G_i
+ * and their Cholesky factors.
+ *   A          the matrix (host or device arrays, see cimmino_csr).
+ *   K          number of blocks, 1 <= K <= n.
+ *   perm       host array of n int32: permuted row r is original row perm[r]
+ *              (a permutation of 0..n-1), or NULL for the identity.
+ *   block_ptr  host array of K+1 int64 offsets over the permuted rows:
+ *              0 = block_ptr[0] < block_ptr[1] < ... < block_ptr[K] = n.
+ *   opts       NULL for the defaults.
+ *   out        receives the new context (NULL on failure).
+ * Errors: EINVAL (malformed input), ESINGULAR (a zero row, or a Gram block that is
+ * not positive definite in FP64), EUNSUPPORTED (a block with more than 4096 rows, or
+ * a row of C with more than 8192 structural candidates), ENOMEM, ECUDA. */
+int cimmino_setup(const cimmino_csr *A, int32_t K, const int32_t *perm, const int64_t *block_ptr,
+                  const cimmino_opts *opts, cimmino_ctx **out);
+
+/* Set up a batch of nsys independent systems that are solved together: system s
+ * has matrix A[s], K[s] blocks, perm[s] (NULL entry or NULL array = identity) and
+ * block_ptr[s].  Every stage runs as one launch over all blocks of all systems. */
+int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
+                        const int32_t *const *perm, const int64_t *const *block_ptr,
+                        const cimmino_opts *opts, cimmino_ctx **out);
+
+/* Solve A X = F for nrhs right-hand sides of a single-system context
+ * (Algorithm 2 per right-hand side, all right-hand sides sharing every pass over
+ * A and the factors).
+ *   F, X       n x nrhs, column k at F + k*ld (column-major), original row order
+ *              for F and original column order for X; X is caller-allocated and
+ *              receives the solutions.
+ *   on_device  1: F and X are device pointers, 0: host pointers.
+ *   tol        stop right-hand side k once ||f_k - A x_k||_2 <= tol * ||f_k||_2.
+ *   stats      NULL or an array of nrhs entries.
+ * Returns CIMMINO_OK when every right-hand side converged, else the first
+ * failure (ENOCONV / EBREAKDOWN; X still holds the last iterates). */
+int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, double tol,
+                  double *X, int32_t on_device, cimmino_stats *stats);
+
+/* Solve every system of a batch context once: F[s] and X[s] are n_s-vectors
+ * (host or device as on_device says); stats NULL or nsys entries. */
+int cimmino_solve_batch(cimmino_ctx *ctx, const double *const *F, double tol, double *const *X,
+                        int32_t on_device, cimmino_stats *stats);
+
+/* Release a context and all of its device memory.  NULL is allowed. */
+void cimmino_free(cimmino_ctx *ctx);
+
+/* Message of the last failure of ctx (or of the last failed setup when ctx is NULL,
+ * per host thread).  The string stays valid until the next call on ctx. */
+const char *cimmino_last_error(const cimmino_ctx *ctx);
+
+/* ---- inspection hooks (tests, partitioners) ----
+ * All copy into caller-allocated HOST buffers. */
+
+/* nnz of C = A A^T of the scaled permuted matrix; then its CSR (columns sorted,
+ * structural pattern: entries whose value cancels to 0.0 are kept).  Needs
+ * opts.keep_aat = 1 at setup, else EINVAL.  Single-system contexts only. */
+int cimmino_get_aat_nnz(cimmino_ctx *ctx, int64_t *nnz);
+int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val);
+
+/* Scaled permuted matrix D^{-1} P A (CSR, nnz entries) and the row norms d (n). */
+int cimmino_get_scaled(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val,
+                       double *d);
+
+/* Number of rows m of global block b (blocks of all systems in order). */
+int cimmino_block_rows(cimmino_ctx *ctx, int32_t b, int32_t *m);
+
+/* Dense m x m row-major copy of the Cholesky factor L_b (upper part zero),
+ * converted to double; *is_fp64 tells which precision the block was factored in. */
+int cimmino_get_factor(cimmino_ctx *ctx, int32_t b, double *L, int32_t *is_fp64);
+
+/* One projection sum psi = H v = sum_i A_i^+ A_i v (Eq. 1.5) of a single-system
+ * context, with the same kernels (and refinement) as the CG iterations; v and psi
+ * are n-vectors in the original column order (host or device as on_device says). */
+int cimmino_project(cimmino_ctx *ctx, const double *v, double *psi, int32_t on_device);
+
+/* xi = sum_i A_i^+ f_i (Section 1.1) for f in the original row order. */
+int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t on_device);
+
+/* Standalone C = A A^T of a caller matrix (no scaling, no permutation) on the
+ * GPU, e.g. to build the row inner-product graph for a partitioner.  Two calls:
+ * first with col_idx = val = NULL to get *nnz and row_ptr (n+1), then with
+ * buffers of *nnz entries.  Host buffers.  stream: cudaStream_t or NULL. */
+int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
+                int32_t *col_idx, double *val);
+
+/* Library build information (compile-time architecture, version). */
+const char *cimmino_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CIMMINO_H */

@@ -1,0 +1,423 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form derived by hand, an independent numpy/LAPACK computation, an invariant
+stated in the paper, brute force on tiny inputs, or the one worked number the
+paper prints.  None of them retypes the oracle's own formula.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense(A):
+    return A.to_dense()
+
+
+def csr_from_dense(D):
+    n = D.shape[0]
+    rp = np.zeros(n + 1, np.int64)
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        cols.append(nz)
+        vals.append(D[i, nz])
+        rp[i + 1] = rp[i] + len(nz)
+    return inputs.CSR(n, rp, np.concatenate(cols).astype(np.int32), np.concatenate(vals))
+
+
+def small_system(n=96, k=3, seed=7):
+    return inputs.random_dd(n, k, seed)
+
+
+def dense_H(A_scaled_dense, bp):
+    """H = sum_i A_i^T (A_i A_i^T)^{-1} A_i with numpy.linalg.solve (independent of the oracle)."""
+    n = A_scaled_dense.shape[0]
+    H = np.zeros((n, n))
+    for b in range(len(bp) - 1):
+        Ai = A_scaled_dense[bp[b]:bp[b + 1]]
+        H += Ai.T @ np.linalg.solve(Ai @ Ai.T, Ai)
+    return H
+
+
+def oracle_H(o):
+    n = o.n
+    return np.stack([o.project(np.eye(n)[j]) for j in range(n)], axis=1)
+
+
+# ---------------------------------------------------------------- SpGEMM (Section 2.3)
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_aat_matches_dense_product(seed):
+    A = inputs.random_dd(120, 4, seed)
+    crp, cci, cv = oracle.aat_plain(A)
+    D = dense(A)
+    ref = D @ D.T
+    pat = (np.abs(D) > 0).astype(np.int64)
+    ref_pat = (pat @ pat.T) > 0                      # structural pattern, integer product
+    got = np.zeros_like(ref)
+    got_pat = np.zeros(ref.shape, bool)
+    for i in range(A.n):
+        cols = cci[crp[i]:crp[i + 1]]
+        assert np.all(np.diff(cols) > 0), "columns of C must be sorted and unique"
+        got[i, cols] = cv[crp[i]:crp[i + 1]]
+        got_pat[i, cols] = True
+    assert np.array_equal(got_pat, ref_pat)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_aat_keeps_structural_zero():
+    # rows 0 and 1 share columns 0 and 1 with products that cancel exactly: 1*1 + 1*(-1) = 0
+    D = np.array([[1.0, 1.0, 0.0], [1.0, -1.0, 0.0], [0.0, 0.0, 2.0]])
+    crp, cci, cv = oracle.aat_plain(csr_from_dense(D))
+    row0 = dict(zip(cci[crp[0]:crp[1]].tolist(), cv[crp[0]:crp[1]].tolist()))
+    assert 1 in row0 and row0[1] == 0.0          # kept, value exactly 0.0
+    assert 2 not in row0                          # no shared column: no entry
+
+
+def test_aat_closed_form_2d_stencil_interior():
+    """Interior row of C = A A^T for the 5-point upwind stencil (diag a = 4+hb,
+    west w = -1-hb, east/north/south -1), derived by hand:
+      c_ii = a^2 + w^2 + 3, c_{i,i+-1} = a(w-1), c_{i,i+-2} = -w,
+      c_{i,i+-N} = -2a, c_{i,i+-2N} = 1, c_{i,i+-(N+1)} = c_{i,i+-(N-1)} = 1 - w."""
+    N, b, h = 16, 20.0, 1.0 / 17
+    A = inputs.convdiff2d(N, b, h)
+    crp, cci, cv = oracle.aat_plain(A)
+    a, w = 4 + h * b, -1 - h * b
+    expect = {0: a * a + w * w + 3, 1: a * (w - 1), -1: a * (w - 1), 2: -w, -2: -w,
+              N: -2 * a, -N: -2 * a, 2 * N: 1.0, -2 * N: 1.0,
+              N + 1: 1 - w, -(N + 1): 1 - w, N - 1: 1 - w, -(N - 1): 1 - w}
+    i = 8 * N + 8                                    # far from every boundary
+    row = dict(zip(cci[crp[i]:crp[i + 1]].tolist(), cv[crp[i]:crp[i + 1]].tolist()))
+    assert sorted(row) == sorted(i + o for o in expect)
+    for o, e in expect.items():
+        assert row[i + o] == pytest.approx(e, rel=1e-14)
+
+
+def test_aat_paper_inner_product_216():
+    g = json.load(open(os.path.join(GOLDEN, "rip_inner_product_216.json")))
+    n = g["n"]
+    D = np.zeros((n, n))
+    for i in range(n):
+        D[i, i] = 1.0 + i          # rows other than r2, r4: a diagonal only
+    D[2, :] = 0.0
+    D[4, :] = 0.0
+    D[2, g["row2"]["cols"]] = g["row2"]["vals"]
+    D[4, g["row4"]["cols"]] = g["row4"]["vals"]
+    crp, cci, cv = oracle.aat_plain(csr_from_dense(D))
+    row = dict(zip(cci[crp[2]:crp[3]].tolist(), cv[crp[2]:crp[3]].tolist()))
+    assert row[4] == g["expected_c24"]
+
+
+def test_scaled_gram_diagonal_is_one():
+    """After the Section 2.1 prescaling every row has unit 2-norm, so diag(C) = 1 and
+    every |c_ij| is a cosine <= 1 (the edge costs of G_RIP lie in (0, 1])."""
+    w = inputs.workload(1)
+    o = oracle.Oracle(w.A, w.block_ptr, factor=False)
+    crp, cci, cv = o.aat()
+    rows = np.repeat(np.arange(o.n), np.diff(crp))
+    diag = cv[rows == cci]
+    np.testing.assert_allclose(diag, 1.0, rtol=0, atol=4e-16)
+    assert np.abs(cv).max() <= 1.0 + 1e-15
+
+
+# ---------------------------------------------------------------- Cholesky
+
+@pytest.mark.parametrize("m", [1, 2, 7, 33, 64])
+def test_cholesky_matches_lapack(m):
+    rng = np.random.default_rng(m)
+    B = rng.standard_normal((m, m + 3))
+    G = B @ B.T
+    L, st = oracle.cholesky_dense(G)
+    assert st == 0
+    np.testing.assert_allclose(L, np.linalg.cholesky(G), rtol=1e-11, atol=1e-12)
+    assert np.linalg.norm(L @ L.T - G) / np.linalg.norm(G) < 1e-14
+
+
+def test_cholesky_detects_non_spd():
+    G = np.array([[1.0, 2.0], [2.0, 1.0]])     # eigenvalues 3 and -1
+    _, st = oracle.cholesky_dense(G)
+    assert st == -2                             # pivot of column 1 is -3 <= 0
+
+
+def test_block_factor_is_cholesky_of_numpy_gram():
+    A = small_system(128, 4, 3)
+    bp = np.array([0, 40, 41, 90, 128])         # ragged, with a 1-row block
+    o = oracle.Oracle(A, bp)
+    rp, ci, v, d = o.scaled()
+    S = inputs.CSR(A.n, rp, ci, v).to_dense()
+    for b in range(len(bp) - 1):
+        Ai = S[bp[b]:bp[b + 1]]
+        G = Ai @ Ai.T
+        np.testing.assert_allclose(o.gram(b), G, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(o.factor(b), np.linalg.cholesky(G), rtol=1e-11, atol=1e-13)
+
+
+def test_singular_block_reported():
+    D = np.eye(6) * 2.0
+    D[1, 4] = 1.0
+    D[2] = D[1]                                 # duplicate row -> G_0 singular
+    D[2, 2] = 0.0
+    D[2, 1] = 2.0
+    D[3] = D[1] * 1.0                           # rows 1 and 3 parallel: A_0 rank deficient
+    A = csr_from_dense(D)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.Oracle(A, np.array([0, 4, 6]))
+    assert e.value.code == oracle.ORC_ESINGULAR
+
+
+# ---------------------------------------------------------------- projections (Eqs. 1.4-1.5, 1.10-1.12)
+
+def test_projection_equals_numpy_pseudoinverse_sum():
+    A = small_system(80, 3, 11)
+    bp = np.array([0, 17, 50, 80])
+    o = oracle.Oracle(A, bp)
+    rp, ci, v, d = o.scaled()
+    S = inputs.CSR(A.n, rp, ci, v).to_dense()
+    H = oracle_H(o)
+    Href = dense_H(S, bp)
+    np.testing.assert_allclose(H, Href, atol=1e-12)
+    # also through the unscaled matrix and numpy's pseudoinverse: H is row-scaling invariant
+    D = dense(A)
+    Hp = sum(np.linalg.pinv(D[bp[b]:bp[b + 1]]) @ D[bp[b]:bp[b + 1]] for b in range(3))
+    np.testing.assert_allclose(H, Hp, atol=1e-11)
+
+
+def test_projections_symmetric_idempotent_trace():
+    A = small_system(72, 4, 5)
+    bp = np.array([0, 9, 30, 31, 72])
+    o = oracle.Oracle(A, bp)
+    H = oracle_H(o)
+    assert np.abs(H - H.T).max() < 1e-13
+    assert np.trace(H) == pytest.approx(A.n, rel=1e-13)        # sum of ranks m_i
+    for b in range(len(bp) - 1):
+        ob = oracle.Oracle(A, bp, perm=None)
+        # P_b alone: a partition with only block b "active" is emulated by projecting
+        # with the block's own rows: P_b = A_b^T G_b^{-1} A_b from the oracle's factor
+        L = ob.factor(b)
+        rp, ci, v, d = ob.scaled()
+        Ab = inputs.CSR(A.n, rp, ci, v).to_dense()[bp[b]:bp[b + 1]]
+        Y = np.linalg.solve(L.T, np.linalg.solve(L, Ab))
+        P = Ab.T @ Y
+        assert np.abs(P @ P - P).max() < 1e-12
+        assert np.trace(P) == pytest.approx(bp[b + 1] - bp[b], rel=1e-12)
+
+
+def test_qr_form_of_H():
+    """Eq. 1.10: H = sum_i Q_i Q_i^T with A_i^T = Q_i R_i."""
+    A = small_system(60, 3, 21)
+    bp = np.array([0, 20, 45, 60])
+    H = oracle_H(oracle.Oracle(A, bp))
+    D = dense(A)
+    Hq = np.zeros_like(H)
+    for b in range(3):
+        Q, _ = np.linalg.qr(D[bp[b]:bp[b + 1]].T)
+        Hq += Q @ Q.T
+    np.testing.assert_allclose(H, Hq, atol=1e-12)
+
+
+def test_K2_spectrum_principal_angles():
+    """Eqs. 1.11-1.12 with K = 2: H is similar to [[I, Q1^T Q2], [Q2^T Q1, I]], whose
+    eigenvalues are 1 +- sigma_j(Q1^T Q2) plus 1 for the unmatched dimensions."""
+    A = small_system(50, 3, 8)
+    bp = np.array([0, 22, 50])
+    H = oracle_H(oracle.Oracle(A, bp))
+    D = dense(A)
+    Q1, _ = np.linalg.qr(D[:22].T)
+    Q2, _ = np.linalg.qr(D[22:].T)
+    s = np.linalg.svd(Q1.T @ Q2, compute_uv=False)
+    expect = np.sort(np.concatenate([1 + s, 1 - s, np.ones(50 - 2 * len(s))]))
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(H)), expect, atol=1e-11)
+
+
+def test_K1_projection_is_identity_and_one_step():
+    """K = 1: A_1 = A nonsingular, so H = A^+ A = I and CG converges in one iteration."""
+    A = inputs.convdiff2d(24, 20.0)
+    n = A.n
+    o = oracle.Oracle(A, np.array([0, n]))
+    v = np.random.default_rng(0).standard_normal(n)
+    np.testing.assert_allclose(o.project(v), v, rtol=0, atol=1e-10 * np.abs(v).max())
+    f = inputs.matvec(A, inputs.uniform_x(n, 1, 0)[0])
+    x, it, rr, g, st = o.solve(f)
+    assert st == 0 and it == 1 and rr <= 1e-10
+
+
+def test_Kn_is_normal_equations():
+    """K = n (one row per block): H = Ahat^T Ahat with Ahat the row-normalised A."""
+    A = small_system(40, 3, 2)
+    o = oracle.Oracle(A, np.arange(A.n + 1))
+    D = dense(A)
+    Ah = D / np.linalg.norm(D, axis=1, keepdims=True)
+    np.testing.assert_allclose(oracle_H(o), Ah.T @ Ah, atol=1e-13)
+
+
+def test_row_order_inside_block_irrelevant():
+    """Section 2.2: the order of rows inside a block row does not change H."""
+    A = small_system(64, 3, 4)
+    bp = np.array([0, 20, 64])
+    rng = np.random.default_rng(1)
+    perm = np.concatenate([rng.permutation(20), 20 + rng.permutation(44)]).astype(np.int32)
+    H0 = oracle_H(oracle.Oracle(A, bp))
+    H1 = oracle_H(oracle.Oracle(A, bp, perm=perm))
+    np.testing.assert_allclose(H0, H1, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Algorithm 2
+
+def numpy_cg_iterations(H, xi, A, f, tol, maxit=5000):
+    """Textbook CG on the dense system (H, xi), stopping on the true residual of A x = f."""
+    x = np.zeros_like(xi)
+    r = xi.copy()
+    p = r.copy()
+    rho = r @ r
+    nf = np.linalg.norm(f)
+    for t in range(maxit):
+        q = H @ p
+        a = rho / (p @ q)
+        x += a * p
+        r -= a * q
+        rho1 = r @ r
+        p = r + (rho1 / rho) * p
+        rho = rho1
+        if np.linalg.norm(f - A @ x) / nf <= tol:
+            return t + 1, x
+    return -1, x
+
+
+@pytest.mark.parametrize("seed,bp", [(3, [0, 30, 70, 100, 150]), (9, [0, 1, 75, 150])])
+def test_cg_matches_dense_textbook_cg(seed, bp):
+    A = small_system(150, 4, seed)
+    bp = np.array(bp)
+    D = dense(A)
+    xt = np.random.default_rng(seed).uniform(-1, 1, A.n)
+    f = D @ xt
+    o = oracle.Oracle(A, bp)
+    x, it, rr, g, st = o.solve(f)
+    rp, ci, v, d = o.scaled()
+    S = inputs.CSR(A.n, rp, ci, v).to_dense()
+    H = dense_H(S, bp)
+    fs = f / np.linalg.norm(D, axis=1)
+    xi = S.T @ np.concatenate([np.linalg.solve(S[bp[b]:bp[b + 1]] @ S[bp[b]:bp[b + 1]].T,
+                                               fs[bp[b]:bp[b + 1]]) for b in range(len(bp) - 1)])
+    it_ref, x_ref = numpy_cg_iterations(H, xi, D, f, 1e-10)
+    assert st == 0 and abs(it - it_ref) <= 1
+    np.testing.assert_allclose(x, np.linalg.solve(D, f), rtol=0, atol=1e-8)
+    # CG bound of Eq. 1.9: after t steps the H-norm error shrinks by 2((sqrt k-1)/(sqrt k+1))^t;
+    # the stopping residual 1e-10 is reached well inside the bound for eps = 1e-10 / kappa(A)
+    ev = np.linalg.eigvalsh(H)
+    kappa = ev[-1] / ev[0]
+    assert 0 < ev[0] and ev[-1] <= len(bp) - 1 + 1e-12
+    q = (np.sqrt(kappa) - 1) / (np.sqrt(kappa) + 1)
+    bound = np.log(1e-10 / (2 * np.linalg.cond(D) * np.sqrt(kappa))) / np.log(q)
+    assert it <= np.ceil(bound) + 1
+
+
+def test_config1_solution_matches_dense_lu():
+    w = inputs.workload(1)
+    o = oracle.Oracle(w.A, w.block_ptr)
+    x, it, rr, g, st = o.solve(w.F[0])
+    D = dense(w.A)
+    x_lu = np.linalg.solve(D, w.F[0])
+    Di = np.linalg.inv(D)
+    # kappa_2 <= sqrt(kappa_1 * kappa_inf), cheaper than an SVD of the 4096 x 4096 matrix
+    kappa = np.sqrt(np.linalg.norm(D, 1) * np.linalg.norm(D, np.inf)
+                    * np.linalg.norm(Di, 1) * np.linalg.norm(Di, np.inf))
+    assert st == 0 and rr <= 1e-10 and g < 1e-10
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) <= kappa * 1e-10
+    # the spectrum of H lies in (0, K] and its mean is 1 (trace H = n)
+    assert 300 < it < 400
+
+
+def test_row_scaling_and_column_permutation_invariance():
+    A = small_system(120, 4, 13)
+    bp = np.array([0, 40, 80, 120])
+    D = dense(A)
+    rng = np.random.default_rng(2)
+    xt = rng.uniform(-1, 1, A.n)
+    f = D @ xt
+    x0, it0, *_ = oracle.Oracle(A, bp).solve(f)
+    # rows scaled by an arbitrary positive diagonal: same H, same xi (Section 2.1, 3.1)
+    s = rng.uniform(0.1, 10, A.n)
+    x1, it1, *_ = oracle.Oracle(csr_from_dense(D * s[:, None]), bp).solve(f * s)
+    assert abs(it1 - it0) <= 1
+    np.testing.assert_allclose(x1, x0, atol=1e-8)
+    # columns permuted: the iterates are the permuted iterates (Section 1.2)
+    q = rng.permutation(A.n)
+    x2, it2, *_ = oracle.Oracle(csr_from_dense(D[:, q]), bp).solve(f)
+    assert abs(it2 - it0) <= 1
+    np.testing.assert_allclose(x2, x0[q], atol=1e-8)
+
+
+def test_algorithm1_first_sweep_and_convergence():
+    """Algorithm 1 from x^(0) = 0: the first sweep gives omega * xi; with 0 < omega <
+    2 / lambda_max(H) the sweeps converge to A^{-1} f."""
+    A = small_system(60, 3, 6)
+    bp = np.array([0, 20, 40, 60])
+    D = dense(A)
+    f = D @ np.random.default_rng(3).uniform(-1, 1, A.n)
+    o = oracle.Oracle(A, bp)
+    np.testing.assert_allclose(o.cimmino_sweeps(f, 0.7, 1), 0.7 * o.project_rhs(f), atol=1e-14)
+    lam = np.linalg.eigvalsh(oracle_H(o))
+    omega = 2.0 / (lam[0] + lam[-1])
+    x = o.cimmino_sweeps(f, omega, 400)
+    rate = (lam[-1] - lam[0]) / (lam[-1] + lam[0])
+    err = np.linalg.norm(x - np.linalg.solve(D, f)) / np.linalg.norm(np.linalg.solve(D, f))
+    assert err <= 10 * np.sqrt(lam[-1] / lam[0]) * rate ** 400 + 1e-12
+
+
+def test_zero_rhs_and_zero_row():
+    w = inputs.workload(1)
+    o = oracle.Oracle(w.A, w.block_ptr)
+    x, it, rr, g, st = o.solve(np.zeros(w.A.n))
+    assert st == 0 and it == 0 and not x.any()
+    D = np.eye(4)
+    D[2, 2] = 0.0
+    with pytest.raises(oracle.OracleError):
+        oracle.Oracle(csr_from_dense(D + np.diag([0, 0, 0, 0])), np.array([0, 2, 4]))
+
+
+# ---------------------------------------------------------------- partition metrics (Eqs. 2.6-2.9)
+
+def test_cutsize_equals_interblock_sum_and_ip_matrix():
+    A = small_system(90, 4, 17)
+    crp, cci, cv = oracle.aat_plain(A)
+    D = dense(A)
+    C = D @ D.T
+    part = np.random.default_rng(0).integers(0, 4, A.n).astype(np.int32)
+    cut = oracle.cutsize(crp, cci, cv, part)
+    mask = part[:, None] != part[None, :]
+    assert cut == pytest.approx(np.abs(C[mask]).sum() / 2, rel=1e-12)
+    ip = oracle.ip_matrix(crp, cci, cv, part, 4)
+    for k in range(4):
+        for m in range(4):
+            if k != m:
+                blk = np.abs(C[np.ix_(part == k, part == m)]).sum()
+                assert ip[k, m] == pytest.approx(blk, rel=1e-12)
+    off = ip.sum() - np.trace(ip)
+    assert off == pytest.approx(2 * cut, rel=1e-12)
+
+
+def test_cutsize_brute_force_bisection():
+    """Every balanced 2-way partition of a 10-row matrix: the oracle's cutsize equals the
+    sum of |r_i r_j^T| over pairs split by the partition computed by brute force."""
+    A = inputs.random_dd(10, 2, 4)
+    D = dense(A)
+    crp, cci, cv = oracle.aat_plain(A)
+    best = None
+    for left in itertools.combinations(range(10), 5):
+        part = np.ones(10, np.int32)
+        part[list(left)] = 0
+        brute = sum(abs(D[i] @ D[j]) for i in range(10) for j in range(i + 1, 10)
+                    if part[i] != part[j])
+        cut = oracle.cutsize(crp, cci, cv, part)
+        assert cut == pytest.approx(brute, rel=1e-12, abs=1e-12)
+        best = cut if best is None else min(best, cut)
+    assert best >= 0
