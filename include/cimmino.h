@@ -104,6 +104,7 @@ typedef struct cimmino_stats {
   double t_solve_ms;          /* this solve: xi plus all CG iterations              */
   int64_t nnz_aat;            /* nnz(C)                                              */
   int64_t factor_bytes;       /* bytes of all stored factor tiles                    */
+  int64_t kernel_launches;    /* kernels launched by the setup plus by this solve     */
 } cimmino_stats;
 
 typedef struct cimmino_ctx cimmino_ctx;
@@ -195,6 +196,15 @@ int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t o
  * buffers of *nnz entries.  Host buffers.  stream: cudaStream_t or NULL. */
 int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
                 int32_t *col_idx, double *val);
+
+/* Benchmark hook: after a cimmino_solve() on a single-system context, launch each
+ * per-iteration kernel `reps` times back to back on the context's stream, on the
+ * vectors of the last solve, and write the average device time per launch in
+ * milliseconds (CUDA events recorded on that stream):
+ *   ms[0] projection kernel y_i = G_i^{-1} u_i over all blocks (with refinement in
+ *         FP32 mode), ms[1] u = A p, ms[2] psi = A^T y.
+ * ms is a caller array of 3 doubles.  Errors: EINVAL (no solve yet, reps < 1). */
+int cimmino_time_kernels(cimmino_ctx *ctx, int32_t reps, double *ms);
 
 /* Library build information (compile-time architecture, version). */
 const char *cimmino_version(void);

@@ -1,0 +1,1066 @@
+// C ABI of the block Cimmino library (declared in include/cimmino.h).
+//
+// Setup pipeline (one launch per stage over all rows / blocks of all systems):
+//   validate -> scale rows to unit 2-norm and permute (Sections 2.1-2.2) ->
+//   transpose -> C = A A^T (Section 2.3) -> block-diagonal part G_i of C ->
+//   tile envelope J0 -> scatter G_i into the tiled factor -> batched Cholesky ->
+//   (FP32 mode) FP64 refactorisation of blocks with a poor pivot ratio.
+// Solve: Algorithm 2 (Section 1.1) from x = 0, with every CG iteration a fixed
+// sequence of five kernels, captured in a CUDA graph of check_every iterations;
+// the host reads one status word per right-hand side between graph launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace cimmino;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      fail(e == cudaErrorMemoryAllocation ? CIMMINO_ENOMEM : CIMMINO_ECUDA,
+           "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
+               cudaGetErrorString(e));
+    }
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+template <typename T>
+void h2d(T *dst, const T *src, size_t count, cudaStream_t s) {
+  if (count) CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDefault, s));
+}
+template <typename T>
+void d2h(T *dst, const T *src, size_t count, cudaStream_t s) {
+  if (count) CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDefault, s));
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  void start(cudaStream_t s) { cudaEventRecord(a, s); }
+  double stop_ms(cudaStream_t s) {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+};
+
+__global__ void k_interleave_to_cols(const double *__restrict__ x, int64_t N, int nrhs,
+                                     double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * nrhs) return;
+  int64_t j = i / nrhs;
+  int k = (int)(i % nrhs);
+  out[(int64_t)k * N + j] = x[i];
+}
+
+}  // namespace
+
+struct cimmino_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cimmino_opts opts{};
+  std::string err;
+  int32_t nsys = 0;
+  int64_t N = 0, nnz = 0;
+  std::vector<SysDesc> hsys;
+  std::vector<BlockDesc> hblk;
+  std::vector<TileRow> htrow;
+  std::vector<CtaDesc> hcta;
+  int32_t max_mp = 0;
+  // matrices
+  DBuf<int64_t> rp, cp, brp, crp;
+  DBuf<int32_t> ci, ri, bci, cci, perm;
+  DBuf<double> va, cv, d, bcv, ccv, rowabs;
+  DBuf<BlockDesc> blk;
+  DBuf<TileRow> trow;
+  DBuf<SysDesc> sys;
+  DBuf<CtaDesc> cta;
+  DBuf<float> fac32, dinv32;
+  DBuf<double> fac64, dinv64;
+  int64_t nnzc = 0, nnz_bd = 0, factor_bytes = 0;
+  int32_t fallbacks = 0;
+  int64_t setup_launches = 0;  // kernels launched by the setup
+  double t_setup_ms = 0.0, t_factor_ms = 0.0;
+  bool have_aat = false;
+  // solve state
+  int32_t nrhs = 0;
+  DBuf<LaneState> lane;
+  DBuf<double> fs, x, p, r, psi, u, y, part, Fin, stats4;
+  DBuf<int32_t> cnt, refine_max;
+  DBuf<int64_t> refine_total;
+  cudaGraphExec_t graph = nullptr;
+  int32_t graph_nrhs = 0, graph_iters = 0;
+  IterArgs args{};
+
+  ~cimmino_ctx() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+void opts_default(cimmino_opts *o) {
+  std::memset(o, 0, sizeof(*o));
+  o->precision = CIMMINO_FP64;
+  o->layout = CIMMINO_LAYOUT_SKYLINE;
+  o->tile = 0;
+  o->refine_max = 6;
+  o->refine_tol = 1e-13;
+  o->pivot_ratio_min = 1e-4;
+  o->max_iter = 10000;
+  o->use_graph = 1;
+  o->check_every = 8;
+  o->keep_aat = 0;
+  o->stream = nullptr;
+}
+
+void check_opts(const cimmino_opts &o) {
+  if (o.precision != CIMMINO_FP64 && o.precision != CIMMINO_FP32_REFINE)
+    fail(CIMMINO_EINVAL, "opts.precision must be CIMMINO_FP64 or CIMMINO_FP32_REFINE");
+  if (o.layout != CIMMINO_LAYOUT_DENSE && o.layout != CIMMINO_LAYOUT_SKYLINE)
+    fail(CIMMINO_EINVAL, "opts.layout must be CIMMINO_LAYOUT_DENSE or CIMMINO_LAYOUT_SKYLINE");
+  if (o.tile != 0 && o.tile != kTile) fail(CIMMINO_EUNSUPPORTED, "opts.tile must be 0 or 64");
+  if (o.refine_max < 0 || o.refine_max > 64) fail(CIMMINO_EINVAL, "opts.refine_max not in [0,64]");
+  if (!(o.refine_tol >= 0.0)) fail(CIMMINO_EINVAL, "opts.refine_tol must be >= 0");
+  if (o.max_iter < 0) fail(CIMMINO_EINVAL, "opts.max_iter must be >= 0");
+  if (o.check_every < 1 || o.check_every > 1024)
+    fail(CIMMINO_EINVAL, "opts.check_every not in [1,1024]");
+}
+
+// ------------------------------------------------------------------ setup
+void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_t *K,
+                const int32_t *const *perms, const int64_t *const *bps) {
+  cudaStream_t s = c->stream;
+  c->nsys = nsys;
+  // ---- host-side validation and global layout
+  int64_t N = 0, NNZ = 0;
+  c->hsys.resize(nsys);
+  for (int32_t q = 0; q < nsys; ++q) {
+    const cimmino_csr &M = A[q];
+    if (M.n <= 0 || M.nnz < 0 || !M.row_ptr || !M.col_idx || (M.nnz > 0 && !M.val))
+      fail(CIMMINO_EINVAL, "system " + std::to_string(q) + ": bad CSR header");
+    if (K[q] < 1 || K[q] > M.n) fail(CIMMINO_EINVAL, "K must be in [1, n]");
+    if (!bps || !bps[q]) fail(CIMMINO_EINVAL, "block_ptr is NULL");
+    const int64_t *bp = bps[q];
+    if (bp[0] != 0 || bp[K[q]] != M.n) fail(CIMMINO_EINVAL, "block_ptr must start at 0 and end at n");
+    for (int32_t b = 0; b < K[q]; ++b) {
+      if (bp[b + 1] <= bp[b]) fail(CIMMINO_EINVAL, "block_ptr must be strictly increasing");
+      if (bp[b + 1] - bp[b] > kMaxBlockRows)
+        fail(CIMMINO_EUNSUPPORTED, "a block has more than 4096 rows");
+    }
+    const int32_t *pm = perms ? perms[q] : nullptr;
+    if (pm) {
+      std::vector<char> seen(M.n, 0);
+      for (int64_t r = 0; r < M.n; ++r) {
+        if (pm[r] < 0 || pm[r] >= M.n || seen[pm[r]])
+          fail(CIMMINO_EINVAL, "perm is not a permutation of 0..n-1");
+        seen[pm[r]] = 1;
+      }
+    }
+    c->hsys[q].row0 = N;
+    c->hsys[q].n = M.n;
+    N += M.n;
+    NNZ += M.nnz;
+  }
+  if (N >= (int64_t(1) << 31) - 1) fail(CIMMINO_EUNSUPPORTED, "total rows exceed 2^31 - 1");
+  c->N = N;
+  c->nnz = NNZ;
+
+  Timer tsetup;
+  tsetup.start(s);
+  // ---- concatenated unscaled matrix A0 (block-diagonal over systems)
+  DBuf<int64_t> rp0;
+  DBuf<int32_t> ci0;
+  DBuf<double> v0;
+  const int64_t *drp0;
+  const int32_t *dci0;
+  const double *dv0;
+  if (nsys == 1 && A[0].on_device) {
+    drp0 = A[0].row_ptr;
+    dci0 = A[0].col_idx;
+    dv0 = A[0].val;
+  } else if (nsys == 1) {
+    rp0.alloc(N + 1);
+    ci0.alloc(NNZ);
+    v0.alloc(NNZ);
+    h2d(rp0.p, A[0].row_ptr, N + 1, s);
+    h2d(ci0.p, A[0].col_idx, NNZ, s);
+    h2d(v0.p, A[0].val, NNZ, s);
+    drp0 = rp0.p;
+    dci0 = ci0.p;
+    dv0 = v0.p;
+  } else {
+    std::vector<int64_t> hrp(N + 1);
+    std::vector<int32_t> hci(NNZ);
+    std::vector<double> hv(NNZ);
+    int64_t z = 0;
+    for (int32_t q = 0; q < nsys; ++q) {
+      const cimmino_csr &M = A[q];
+      std::vector<int64_t> trp(M.n + 1);
+      const int64_t *srp = M.row_ptr;
+      const int32_t *sci = M.col_idx;
+      const double *sv = M.val;
+      std::vector<int32_t> tci;
+      std::vector<double> tv;
+      if (M.on_device) {
+        CUDA_TRY(cudaMemcpy(trp.data(), M.row_ptr, sizeof(int64_t) * (M.n + 1), cudaMemcpyDefault));
+        tci.resize(M.nnz);
+        tv.resize(M.nnz);
+        CUDA_TRY(cudaMemcpy(tci.data(), M.col_idx, sizeof(int32_t) * M.nnz, cudaMemcpyDefault));
+        CUDA_TRY(cudaMemcpy(tv.data(), M.val, sizeof(double) * M.nnz, cudaMemcpyDefault));
+        srp = trp.data();
+        sci = tci.data();
+        sv = tv.data();
+      }
+      if (srp[0] != 0 || srp[M.n] != M.nnz)
+        fail(CIMMINO_EINVAL, "system " + std::to_string(q) + ": row_ptr ends do not match nnz");
+      const int64_t r0 = c->hsys[q].row0;
+      for (int64_t i = 0; i < M.n; ++i) hrp[r0 + i] = z + srp[i];
+      for (int64_t e = 0; e < M.nnz; ++e) {
+        hci[z + e] = sci[e] < 0 || sci[e] >= M.n ? -1 : (int32_t)(sci[e] + r0);
+        hv[z + e] = sv[e];
+      }
+      z += M.nnz;
+    }
+    hrp[N] = z;
+    rp0.alloc(N + 1);
+    ci0.alloc(NNZ);
+    v0.alloc(NNZ);
+    h2d(rp0.p, hrp.data(), N + 1, s);
+    h2d(ci0.p, hci.data(), NNZ, s);
+    h2d(v0.p, hv.data(), NNZ, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    drp0 = rp0.p;
+    dci0 = ci0.p;
+    dv0 = v0.p;
+  }
+  DBuf<int32_t> flag;
+  flag.alloc(4);
+  CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4 * sizeof(int32_t), s));
+  launch_validate_csr(drp0, dci0, N, NNZ, flag.p, s);
+  c->setup_launches += 1;
+  int32_t hflag[4] = {0, 0, 0, 0};
+  d2h(hflag, flag.p, 1, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hflag[0]) {
+    std::string why = (hflag[0] & 1) ? "row_ptr not monotone or inconsistent with nnz"
+                      : (hflag[0] & 2) ? "column index out of range"
+                                       : "column indices not strictly increasing within a row";
+    fail(CIMMINO_EINVAL, "malformed CSR: " + why);
+  }
+  // ---- permutation and blocks
+  std::vector<int32_t> hperm(N);
+  for (int32_t q = 0; q < nsys; ++q) {
+    const int64_t r0 = c->hsys[q].row0;
+    const int32_t *pm = perms ? perms[q] : nullptr;
+    for (int64_t r = 0; r < c->hsys[q].n; ++r) hperm[r0 + r] = (int32_t)(r0 + (pm ? pm[r] : r));
+  }
+  c->perm.alloc(N);
+  h2d(c->perm.p, hperm.data(), N, s);
+  int32_t ntrow = 0;
+  c->max_mp = 0;
+  for (int32_t q = 0; q < nsys; ++q) {
+    for (int32_t b = 0; b < K[q]; ++b) {
+      BlockDesc B{};
+      B.row0 = c->hsys[q].row0 + bps[q][b];
+      B.m = (int32_t)(bps[q][b + 1] - bps[q][b]);
+      B.nt = (B.m + kTile - 1) / kTile;
+      B.trow0 = ntrow;
+      B.sys = q;
+      B.prec64 = c->opts.precision == CIMMINO_FP64;
+      ntrow += B.nt;
+      c->max_mp = std::max(c->max_mp, B.nt * kTile);
+      c->hblk.push_back(B);
+    }
+  }
+  const int32_t nblk = (int32_t)c->hblk.size();
+  c->blk.alloc(nblk);
+  h2d(c->blk.p, c->hblk.data(), nblk, s);
+  const int psm = proj_smem_bytes(c->max_mp);
+  if (psm > 227 * 1024) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
+
+  // ---- scale and permute rows (Sections 2.1, 2.2)
+  DBuf<int64_t> len, tmp;
+  const int64_t tl = scan_tmp_len(N);
+  len.alloc(2 * N);
+  tmp.alloc(tl);
+  c->rp.alloc(N + 1);
+  launch_permuted_lengths(drp0, c->perm.p, N, len.p, s);
+  launch_scan_counts(len.p, c->rp.p, N, tmp.p, tl, s);
+  c->setup_launches += 4;  // lengths + 3-pass scan
+  c->ci.alloc(NNZ);
+  c->va.alloc(NNZ);
+  c->d.alloc(N);
+  launch_scale_permute(drp0, dci0, dv0, c->perm.p, c->rp.p, N, c->ci.p, c->va.p, c->d.p,
+                       flag.p + 1, s);
+  c->setup_launches += 1;
+  // ---- transpose
+  c->cp.alloc(N + 1);
+  c->ri.alloc(NNZ);
+  c->cv.alloc(NNZ);
+  launch_transpose(c->rp.p, c->ci.p, c->va.p, N, NNZ, c->cp.p, c->ri.p, c->cv.p, len.p, tmp.p,
+                   tl, s);
+  c->setup_launches += 6;  // count, 3-pass scan, fill, sort
+  d2h(hflag + 1, flag.p + 1, 1, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hflag[1]) fail(CIMMINO_ESINGULAR, "A has a zero row (the matrix is singular)");
+  rp0.release();
+  ci0.release();
+  v0.release();
+
+  // ---- C = A A^T (Section 2.3)
+  DBuf<int64_t> cntc;
+  DBuf<int32_t> ovf;
+  cntc.alloc(N);
+  ovf.alloc(N + 1);
+  spgemm_count(c->rp.p, c->ci.p, c->cp.p, c->ri.p, N, cntc.p, ovf.p + 1, ovf.p, s);
+  c->setup_launches += 1;
+  int32_t novf = 0;
+  d2h(&novf, ovf.p, 1, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (novf > 0) {
+    spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p, nullptr,
+                    nullptr, nullptr, flag.p + 2, s);
+    d2h(hflag + 2, flag.p + 2, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflag[2])
+      fail(CIMMINO_EUNSUPPORTED, "a row of A A^T has more than 8192 structural candidates");
+  }
+  c->crp.alloc(N + 1);
+  launch_scan_counts(cntc.p, c->crp.p, N, tmp.p, tl, s);
+  c->setup_launches += 3 + (novf > 0 ? 2 : 0);
+  d2h(&c->nnzc, c->crp.p + N, 1, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  c->cci.alloc(c->nnzc);
+  c->ccv.alloc(c->nnzc);
+  spgemm_fill(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, N, c->crp.p, c->cci.p, c->ccv.p, s);
+  c->setup_launches += 1;
+  if (novf > 0)
+    spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p,
+                    c->crp.p, c->cci.p, c->ccv.p, flag.p + 2, s);
+  c->have_aat = true;
+
+  // ---- block-diagonal part of C: the Gram blocks G_i (exact, FP64)
+  DBuf<int32_t> rowblk, rowmin;
+  rowblk.alloc(N);
+  rowmin.alloc(N);
+  launch_row_block_ids(c->blk.p, nblk, rowblk.p, s);
+  bd_count(c->crp.p, c->cci.p, c->blk.p, rowblk.p, N, cntc.p, s);
+  c->brp.alloc(N + 1);
+  launch_scan_counts(cntc.p, c->brp.p, N, tmp.p, tl, s);
+  c->setup_launches += 5;  // block ids, count, 3-pass scan
+  d2h(&c->nnz_bd, c->brp.p + N, 1, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  c->bci.alloc(c->nnz_bd);
+  c->bcv.alloc(c->nnz_bd);
+  bd_fill(c->crp.p, c->cci.p, c->ccv.p, c->blk.p, rowblk.p, N, c->brp.p, c->bci.p, c->bcv.p,
+          rowmin.p, s);
+  c->setup_launches += 2;  // fill, tile envelope
+
+  // ---- tile envelope and factor layout
+  DBuf<int32_t> dj0;
+  dj0.alloc(ntrow);
+  launch_tile_j0(c->blk.p, nblk, rowmin.p, c->opts.layout == CIMMINO_LAYOUT_DENSE, dj0.p, s);
+  std::vector<int32_t> hj0(ntrow);
+  d2h(hj0.data(), dj0.p, ntrow, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  c->htrow.resize(ntrow);
+  int64_t off = 0, doff = 0;
+  const int64_t TT = (int64_t)kTile * kTile;
+  for (auto &B : c->hblk) {
+    B.dinv_off = doff;
+    doff += (int64_t)B.nt * TT;
+    for (int32_t I = 0; I < B.nt; ++I) {
+      TileRow &R = c->htrow[B.trow0 + I];
+      R.j0 = hj0[B.trow0 + I];
+      R.off = off;
+      off += (int64_t)(I - R.j0 + 1) * TT;
+    }
+  }
+  c->trow.alloc(ntrow);
+  h2d(c->trow.p, c->htrow.data(), ntrow, s);
+  h2d(c->blk.p, c->hblk.data(), nblk, s);
+  const bool fp64 = c->opts.precision == CIMMINO_FP64;
+  if (fp64) {
+    c->fac64.alloc(off);
+    c->dinv64.alloc(doff);
+  } else {
+    c->fac32.alloc(off);
+    c->dinv32.alloc(doff);
+  }
+  c->factor_bytes = off * (fp64 ? 8 : 4);
+  c->t_setup_ms = tsetup.stop_ms(s);
+
+  // ---- batched Cholesky of all G_i
+  Timer tfac;
+  tfac.start(s);
+  std::vector<int32_t> hlist(nblk);
+  for (int32_t b = 0; b < nblk; ++b) hlist[b] = b;
+  DBuf<int32_t> blist, pfail;
+  DBuf<double> pmin;
+  blist.alloc(nblk);
+  pfail.alloc(nblk);
+  pmin.alloc(nblk);
+  h2d(blist.p, hlist.data(), nblk, s);
+  void *fac = fp64 ? (void *)c->fac64.p : (void *)c->fac32.p;
+  void *dinv = fp64 ? (void *)c->dinv64.p : (void *)c->dinv32.p;
+  launch_gram_scatter(c->blk.p, blist.p, nblk, c->trow.p, c->brp.p, c->bci.p, c->bcv.p, fac,
+                      fp64, s);
+  launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, fac, dinv, fp64, pmin.p, pfail.p, s);
+  c->setup_launches += 2;  // scatter, Cholesky
+  CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> hfail(nblk);
+  std::vector<double> hpmin(nblk);
+  d2h(hfail.data(), pfail.p, nblk, s);
+  d2h(hpmin.data(), pmin.p, nblk, s);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (fp64) {
+    for (int32_t b = 0; b < nblk; ++b)
+      if (hfail[b])
+        fail(CIMMINO_ESINGULAR, "Gram block " + std::to_string(b) +
+                                    " is not positive definite (A_i is rank deficient)");
+  } else {
+    // FP64 refactorisation of blocks whose FP32 pivots failed or fell below the ratio
+    std::vector<int32_t> fb;
+    for (int32_t b = 0; b < nblk; ++b)
+      if (hfail[b] || !(hpmin[b] >= c->opts.pivot_ratio_min)) fb.push_back(b);
+    c->fallbacks = (int32_t)fb.size();
+    if (!fb.empty()) {
+      int64_t off64 = 0, doff64 = 0;
+      for (int32_t b : fb) {
+        BlockDesc &B = c->hblk[b];
+        B.prec64 = 1;
+        B.dinv_off = doff64;
+        doff64 += (int64_t)B.nt * TT;
+        for (int32_t I = 0; I < B.nt; ++I) {
+          TileRow &R = c->htrow[B.trow0 + I];
+          R.off = off64;
+          off64 += (int64_t)(I - R.j0 + 1) * TT;
+        }
+      }
+      c->fac64.alloc(off64);
+      c->dinv64.alloc(doff64);
+      c->factor_bytes += off64 * 8;
+      h2d(c->trow.p, c->htrow.data(), ntrow, s);
+      h2d(c->blk.p, c->hblk.data(), nblk, s);
+      h2d(blist.p, fb.data(), fb.size(), s);
+      launch_gram_scatter(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->brp.p, c->bci.p,
+                          c->bcv.p, c->fac64.p, 1, s);
+      launch_cholesky(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
+                      c->dinv64.p, 1, pmin.p, pfail.p, s);
+      c->setup_launches += 2;
+      d2h(hfail.data(), pfail.p, nblk, s);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (int32_t b : fb)
+        if (hfail[b])
+          fail(CIMMINO_ESINGULAR, "Gram block " + std::to_string(b) +
+                                      " is not positive definite in FP64 (A_i is rank deficient)");
+    }
+  }
+  c->t_factor_ms = tfac.stop_ms(s);
+  if (!c->opts.keep_aat) {
+    c->crp.release();
+    c->cci.release();
+    c->ccv.release();
+    c->have_aat = false;
+  }
+  // ---- vector-kernel CTA table (256 rows per CTA, never straddling systems)
+  for (int32_t q = 0; q < nsys; ++q) {
+    SysDesc &S = c->hsys[q];
+    S.cta0 = (int32_t)c->hcta.size();
+    for (int64_t r = 0; r < S.n; r += 256) {
+      CtaDesc C;
+      C.row0 = S.row0 + r;
+      C.rows = (int32_t)std::min<int64_t>(256, S.n - r);
+      C.sys = q;
+      c->hcta.push_back(C);
+    }
+    S.ncta = (int32_t)c->hcta.size() - S.cta0;
+  }
+  c->sys.alloc(nsys);
+  h2d(c->sys.p, c->hsys.data(), nsys, s);
+  c->cta.alloc(c->hcta.size());
+  h2d(c->cta.p, c->hcta.data(), c->hcta.size(), s);
+  c->rowabs.alloc(N);
+  launch_row_abs(c->rp.p, c->va.p, c->d.p, N, c->rowabs.p, s);
+  c->setup_launches += 1;
+  set_proj_smem_attr(psm);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ solve
+void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
+  if (c->nrhs == nrhs) return;
+  const int64_t N = c->N;
+  const int64_t V = N * nrhs;
+  c->lane.alloc((size_t)c->nsys * nrhs);
+  c->fs.alloc(V);
+  c->x.alloc(V);
+  c->p.alloc(V);
+  c->r.alloc(V);
+  c->psi.alloc(V);
+  c->u.alloc(V);
+  c->y.alloc(V);
+  c->Fin.alloc(V);
+  c->part.alloc((size_t)4 * c->hcta.size() * nrhs);
+  c->stats4.alloc((size_t)4 * c->hcta.size() * nrhs);
+  c->cnt.alloc((size_t)4 * c->nsys);
+  c->refine_total.alloc(1);
+  c->refine_max.alloc(1);
+  c->nrhs = nrhs;
+  IterArgs &a = c->args;
+  a.rp = c->rp.p;
+  a.ci = c->ci.p;
+  a.va = c->va.p;
+  a.cp = c->cp.p;
+  a.ri = c->ri.p;
+  a.cv = c->cv.p;
+  a.d = c->d.p;
+  a.brp = c->brp.p;
+  a.bci = c->bci.p;
+  a.bcv = c->bcv.p;
+  a.blk = c->blk.p;
+  a.trow = c->trow.p;
+  a.fac32 = c->fac32.p;
+  a.dinv32 = c->dinv32.p;
+  a.fac64 = c->fac64.p;
+  a.dinv64 = c->dinv64.p;
+  a.sys = c->sys.p;
+  a.cta = c->cta.p;
+  a.lane = c->lane.p;
+  a.fs = c->fs.p;
+  a.x = c->x.p;
+  a.p = c->p.p;
+  a.r = c->r.p;
+  a.psi = c->psi.p;
+  a.u = c->u.p;
+  a.y = c->y.p;
+  a.part = c->part.p;
+  a.cnt = c->cnt.p;
+  a.refine_total = c->refine_total.p;
+  a.refine_max = c->refine_max.p;
+  a.N = N;
+  a.nsys = c->nsys;
+  a.ncta = (int32_t)c->hcta.size();
+  a.nblk = (int32_t)c->hblk.size();
+  a.nrhs = nrhs;
+  a.refine_steps = c->opts.precision == CIMMINO_FP32_REFINE ? c->opts.refine_max : 0;
+  a.refine_tol = c->opts.refine_tol;
+  a.max_iter = c->opts.max_iter;
+  a.max_mp = c->max_mp;
+  a.proj_smem = proj_smem_bytes(c->max_mp);
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+}
+
+// Fin ([nrhs][N], original row order) must be filled by the caller.
+int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
+  cudaStream_t s = c->stream;
+  IterArgs &a = c->args;
+  a.tol = tol;
+  Timer tsolve;
+  tsolve.start(s);
+  CUDA_TRY(cudaMemsetAsync(c->cnt.p, 0, sizeof(int32_t) * 4 * c->nsys, s));
+  CUDA_TRY(cudaMemsetAsync(c->refine_total.p, 0, sizeof(int64_t), s));
+  CUDA_TRY(cudaMemsetAsync(c->refine_max.p, 0, sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(c->lane.p, 0, sizeof(LaneState) * c->nsys * nrhs, s));
+  launch_rhs_scale(a, c->Fin.p, c->perm.p, s);
+  // xi = sum_i A_i^+ f_i, then r = p = xi, x = 0
+  launch_proj(a, c->fs.p, c->y.p, 0, s);
+  launch_spmv_t(a, c->y.p, c->psi.p, s);
+  launch_cg_init(a, s);
+  CUDA_TRY(cudaGetLastError());
+  const int32_t G = c->opts.check_every;
+  const int32_t nl = c->nsys * nrhs;
+  std::vector<LaneState> hl(nl);
+  int64_t launched = 0;
+  const int64_t limit = (int64_t)c->opts.max_iter + 2 * G + 2;
+  for (;;) {
+    if (c->opts.use_graph) {
+      if (!c->graph || c->graph_nrhs != nrhs || c->graph_iters != G) {
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        cudaGraph_t g;
+        CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int32_t i = 0; i < G; ++i) launch_iteration(a, s);
+        CUDA_TRY(cudaStreamEndCapture(s, &g));
+        cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_TRY(e);
+        c->graph_nrhs = nrhs;
+        c->graph_iters = G;
+      }
+      CUDA_TRY(cudaGraphLaunch(c->graph, s));
+    } else {
+      for (int32_t i = 0; i < G; ++i) launch_iteration(a, s);
+      CUDA_TRY(cudaGetLastError());
+    }
+    launched += G;
+    d2h(hl.data(), c->lane.p, nl, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    bool running = false;
+    for (const auto &L : hl) running |= (L.status == CIMMINO_RUNNING);
+    if (!running) break;
+    if (launched > limit) fail(CIMMINO_ETIMEOUT, "CG lanes still running past max_iter");
+  }
+  // backward error gamma (Eq. 3.1) per lane
+  launch_final_stats(a, c->Fin.p, c->rowabs.p, c->stats4.p, s);
+  std::vector<double> h4((size_t)4 * c->hcta.size() * nrhs);
+  d2h(h4.data(), c->stats4.p, h4.size(), s);
+  int64_t rtot = 0;
+  int32_t rmax = 0;
+  d2h(&rtot, c->refine_total.p, 1, s);
+  d2h(&rmax, c->refine_max.p, 1, s);
+  const double tms = tsolve.stop_ms(s);
+  CUDA_TRY(cudaGetLastError());
+  int ret = CIMMINO_OK;
+  for (int32_t q = 0; q < c->nsys; ++q) {
+    const SysDesc &S = c->hsys[q];
+    for (int32_t k = 0; k < nrhs; ++k) {
+      const LaneState &L = hl[q * nrhs + k];
+      double rinf = 0, x1 = 0, finf = 0, ainf = 0;
+      for (int32_t cc = S.cta0; cc < S.cta0 + S.ncta; ++cc) {
+        const double *o = &h4[((size_t)cc * nrhs + k) * 4];
+        rinf = std::max(rinf, o[0]);
+        x1 += o[1];
+        finf = std::max(finf, o[2]);
+        ainf = std::max(ainf, o[3]);
+      }
+      int st = L.status == CIMMINO_CONVERGED ? CIMMINO_OK : L.status;
+      if (st != CIMMINO_OK && ret == CIMMINO_OK) ret = st;
+      if (stats) {
+        cimmino_stats &o = stats[q * nrhs + k];
+        o.status = st;
+        o.iters = L.iters;
+        o.rel_res = L.relres;
+        double den = ainf * x1 + finf;
+        o.backward_err = den > 0 ? rinf / den : 0.0;
+        o.refine_steps_total = rtot;
+        o.refine_steps_max = rmax;
+        o.fallbacks = c->fallbacks;
+        o.t_setup_ms = c->t_setup_ms;
+        o.t_factor_ms = c->t_factor_ms;
+        o.t_solve_ms = tms;
+        o.nnz_aat = c->nnzc;
+        o.factor_bytes = c->factor_bytes;
+        // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
+        o.kernel_launches = c->setup_launches + 5 + 5 * launched + (nrhs > 1 ? 1 : 0);
+      }
+    }
+  }
+  return ret;
+}
+
+int set_error(cimmino_ctx *c, const Error &e) {
+  if (c)
+    c->err = e.msg;
+  else
+    g_last_error = e.msg;
+  g_last_error = e.msg;
+  return e.code;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void cimmino_opts_default(cimmino_opts *opts) {
+  if (opts) opts_default(opts);
+}
+
+const char *cimmino_version(void) { return "cimmino-gb300 1.0 (sm_103a)"; }
+
+int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
+                        const int32_t *const *perm, const int64_t *const *block_ptr,
+                        const cimmino_opts *opts, cimmino_ctx **out) {
+  if (out) *out = nullptr;
+  if (!out || !A || !K || !block_ptr || nsys < 1) {
+    g_last_error = "invalid argument (NULL pointer or nsys < 1)";
+    return CIMMINO_EINVAL;
+  }
+  cimmino_ctx *c = new (std::nothrow) cimmino_ctx();
+  if (!c) return CIMMINO_ENOMEM;
+  try {
+    if (opts)
+      c->opts = *opts;
+    else
+      opts_default(&c->opts);
+    check_opts(c->opts);
+    CUDA_TRY(cudaGetDevice(&c->device));
+    if (c->opts.stream) {
+      c->stream = static_cast<cudaStream_t>(c->opts.stream);
+    } else {
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    setup_impl(c, nsys, A, K, perm, block_ptr);
+  } catch (const Error &e) {
+    int code = set_error(nullptr, e);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    delete c;
+    return code;
+  }
+  *out = c;
+  return CIMMINO_OK;
+}
+
+int cimmino_setup(const cimmino_csr *A, int32_t K, const int32_t *perm, const int64_t *block_ptr,
+                  const cimmino_opts *opts, cimmino_ctx **out) {
+  const int32_t *pa[1] = {perm};
+  const int64_t *ba[1] = {block_ptr};
+  if (!block_ptr) {
+    if (out) *out = nullptr;
+    g_last_error = "block_ptr is NULL";
+    return CIMMINO_EINVAL;
+  }
+  return cimmino_setup_batch(1, A, &K, pa, ba, opts, out);
+}
+
+void cimmino_free(cimmino_ctx *ctx) {
+  if (!ctx) return;
+  int cur = 0;
+  const int dev = ctx->device;
+  cudaGetDevice(&cur);
+  if (cur != dev) cudaSetDevice(dev);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+  if (cur != dev) cudaSetDevice(cur);
+}
+
+const char *cimmino_last_error(const cimmino_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, double tol,
+                  double *X, int32_t on_device, cimmino_stats *stats) {
+  if (!ctx) return CIMMINO_EINVAL;
+  try {
+    if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_solve needs a single-system context");
+    if (!F || !X || nrhs < 1 || ld < ctx->N) fail(CIMMINO_EINVAL, "bad F / X / nrhs / ld");
+    if (!(tol > 0.0)) fail(CIMMINO_EINVAL, "tol must be > 0");
+    (void)on_device;  // copies use unified addressing, host or device alike
+    ensure_solve_buffers(ctx, nrhs);
+    cudaStream_t s = ctx->stream;
+    const int64_t N = ctx->N;
+    CUDA_TRY(cudaMemcpy2DAsync(ctx->Fin.p, N * sizeof(double), F, ld * sizeof(double),
+                               N * sizeof(double), nrhs, cudaMemcpyDefault, s));
+    int ret = solve_impl(ctx, nrhs, tol, stats);
+    if (nrhs == 1) {
+      CUDA_TRY(cudaMemcpyAsync(X, ctx->x.p, N * sizeof(double), cudaMemcpyDefault, s));
+    } else {
+      int64_t tot = N * nrhs;
+      k_interleave_to_cols<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->x.p, N, nrhs,
+                                                                         ctx->Fin.p);
+      CUDA_TRY(cudaMemcpy2DAsync(X, ld * sizeof(double), ctx->Fin.p, N * sizeof(double),
+                                 N * sizeof(double), nrhs, cudaMemcpyDefault, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (ret != CIMMINO_OK)
+      ctx->err = ret == CIMMINO_ENOCONV ? "max_iter reached before convergence"
+                                        : "CG breakdown (p^T H p <= 0 or not finite)";
+    return ret;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_solve_batch(cimmino_ctx *ctx, const double *const *F, double tol, double *const *X,
+                        int32_t on_device, cimmino_stats *stats) {
+  if (!ctx) return CIMMINO_EINVAL;
+  try {
+    if (!F || !X) fail(CIMMINO_EINVAL, "F / X is NULL");
+    if (!(tol > 0.0)) fail(CIMMINO_EINVAL, "tol must be > 0");
+    (void)on_device;
+    ensure_solve_buffers(ctx, 1);
+    cudaStream_t s = ctx->stream;
+    for (int32_t q = 0; q < ctx->nsys; ++q) {
+      if (!F[q] || !X[q]) fail(CIMMINO_EINVAL, "F[s] / X[s] is NULL");
+      h2d(ctx->Fin.p + ctx->hsys[q].row0, F[q], ctx->hsys[q].n, s);
+    }
+    int ret = solve_impl(ctx, 1, tol, stats);
+    for (int32_t q = 0; q < ctx->nsys; ++q)
+      d2h(X[q], ctx->x.p + ctx->hsys[q].row0, ctx->hsys[q].n, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return ret;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_get_aat_nnz(cimmino_ctx *ctx, int64_t *nnz) {
+  if (!ctx || !nnz) return CIMMINO_EINVAL;
+  if (!ctx->have_aat) {
+    ctx->err = "C = A A^T was not kept (set opts.keep_aat = 1)";
+    return CIMMINO_EINVAL;
+  }
+  *nnz = ctx->nnzc;
+  return CIMMINO_OK;
+}
+
+int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val) {
+  if (!ctx || !row_ptr || !col_idx || !val) return CIMMINO_EINVAL;
+  if (!ctx->have_aat) {
+    ctx->err = "C = A A^T was not kept (set opts.keep_aat = 1)";
+    return CIMMINO_EINVAL;
+  }
+  try {
+    cudaStream_t s = ctx->stream;
+    d2h(row_ptr, ctx->crp.p, ctx->N + 1, s);
+    d2h(col_idx, ctx->cci.p, ctx->nnzc, s);
+    d2h(val, ctx->ccv.p, ctx->nnzc, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_get_scaled(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val,
+                       double *d) {
+  if (!ctx || !row_ptr || !col_idx || !val || !d) return CIMMINO_EINVAL;
+  try {
+    cudaStream_t s = ctx->stream;
+    d2h(row_ptr, ctx->rp.p, ctx->N + 1, s);
+    d2h(col_idx, ctx->ci.p, ctx->nnz, s);
+    d2h(val, ctx->va.p, ctx->nnz, s);
+    d2h(d, ctx->d.p, ctx->N, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_block_rows(cimmino_ctx *ctx, int32_t b, int32_t *m) {
+  if (!ctx || !m || b < 0 || b >= (int32_t)ctx->hblk.size()) return CIMMINO_EINVAL;
+  *m = ctx->hblk[b].m;
+  return CIMMINO_OK;
+}
+
+int cimmino_get_factor(cimmino_ctx *ctx, int32_t b, double *L, int32_t *is_fp64) {
+  if (!ctx || !L || b < 0 || b >= (int32_t)ctx->hblk.size()) return CIMMINO_EINVAL;
+  try {
+    const BlockDesc &B = ctx->hblk[b];
+    const int64_t TT = (int64_t)kTile * kTile;
+    const TileRow &first = ctx->htrow[B.trow0];
+    const TileRow &last = ctx->htrow[B.trow0 + B.nt - 1];
+    const int64_t span = last.off + (int64_t)(B.nt - 1 - last.j0 + 1) * TT - first.off;
+    std::vector<double> buf(span);
+    cudaStream_t s = ctx->stream;
+    if (B.prec64) {
+      d2h(buf.data(), ctx->fac64.p + first.off, span, s);
+    } else {
+      std::vector<float> f(span);
+      d2h(f.data(), ctx->fac32.p + first.off, span, s);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (int64_t i = 0; i < span; ++i) buf[i] = f[i];
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int m = B.m;
+    std::memset(L, 0, sizeof(double) * (size_t)m * m);
+    for (int32_t I = 0; I < B.nt; ++I) {
+      const TileRow &R = ctx->htrow[B.trow0 + I];
+      for (int32_t J = R.j0; J <= I; ++J) {
+        const double *t = buf.data() + (R.off - first.off) + (int64_t)(J - R.j0) * TT;
+        for (int rr = 0; rr < kTile; ++rr) {
+          int gr = I * kTile + rr;
+          if (gr >= m) break;
+          for (int cc = 0; cc < kTile; ++cc) {
+            int gc = J * kTile + cc;
+            if (gc >= m || gc > gr) break;
+            L[(int64_t)gr * m + gc] = t[rr * kTile + cc];
+          }
+        }
+      }
+    }
+    if (is_fp64) *is_fp64 = B.prec64;
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_project(cimmino_ctx *ctx, const double *v, double *psi, int32_t on_device) {
+  if (!ctx || !v || !psi) return CIMMINO_EINVAL;
+  try {
+    if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_project needs a single-system context");
+    (void)on_device;
+    ensure_solve_buffers(ctx, 1);
+    cudaStream_t s = ctx->stream;
+    CUDA_TRY(cudaMemsetAsync(ctx->refine_total.p, 0, sizeof(int64_t), s));
+    CUDA_TRY(cudaMemsetAsync(ctx->refine_max.p, 0, sizeof(int32_t), s));
+    h2d(ctx->p.p, v, ctx->N, s);
+    launch_spmv_plain(ctx->args, ctx->p.p, ctx->u.p, s);
+    launch_proj(ctx->args, ctx->u.p, ctx->y.p, 0, s);
+    launch_spmv_t(ctx->args, ctx->y.p, ctx->psi.p, s);
+    d2h(psi, ctx->psi.p, ctx->N, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t on_device) {
+  if (!ctx || !f || !xi) return CIMMINO_EINVAL;
+  try {
+    if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_project_rhs needs a single-system context");
+    (void)on_device;
+    ensure_solve_buffers(ctx, 1);
+    cudaStream_t s = ctx->stream;
+    CUDA_TRY(cudaMemsetAsync(ctx->cnt.p, 0, sizeof(int32_t) * 4 * ctx->nsys, s));
+    h2d(ctx->Fin.p, f, ctx->N, s);
+    launch_rhs_scale(ctx->args, ctx->Fin.p, ctx->perm.p, s);
+    launch_proj(ctx->args, ctx->fs.p, ctx->y.p, 0, s);
+    launch_spmv_t(ctx->args, ctx->y.p, ctx->psi.p, s);
+    d2h(xi, ctx->psi.p, ctx->N, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_time_kernels(cimmino_ctx *ctx, int32_t reps, double *ms) {
+  if (!ctx || !ms || reps < 1) return CIMMINO_EINVAL;
+  try {
+    if (ctx->nsys != 1 || ctx->nrhs < 1) fail(CIMMINO_EINVAL, "no solve on this context yet");
+    cudaStream_t s = ctx->stream;
+    const IterArgs &a = ctx->args;
+    Timer t;
+    t.start(s);
+    for (int32_t i = 0; i < reps; ++i) launch_proj(a, a.u, a.y, 0, s);
+    ms[0] = t.stop_ms(s) / reps;
+    t.start(s);
+    for (int32_t i = 0; i < reps; ++i) launch_spmv_plain(a, a.p, a.u, s);
+    ms[1] = t.stop_ms(s) / reps;
+    t.start(s);
+    for (int32_t i = 0; i < reps; ++i) launch_spmv_t(a, a.y, a.psi, s);
+    ms[2] = t.stop_ms(s) / reps;
+    CUDA_TRY(cudaGetLastError());
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
+                int32_t *col_idx, double *val) {
+  if (!A || !nnz || !row_ptr) {
+    g_last_error = "invalid argument";
+    return CIMMINO_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    const int64_t N = A->n, NNZ = A->nnz;
+    if (N <= 0 || NNZ < 0 || !A->row_ptr || !A->col_idx || (NNZ > 0 && !A->val))
+      fail(CIMMINO_EINVAL, "bad CSR header");
+    DBuf<int64_t> rp, cp, work, tmp, cnt, crp;
+    DBuf<int32_t> ci, ri, ovf, flag, cci;
+    DBuf<double> va, cv, ccv;
+    rp.alloc(N + 1);
+    ci.alloc(NNZ);
+    va.alloc(NNZ);
+    h2d(rp.p, A->row_ptr, N + 1, s);
+    h2d(ci.p, A->col_idx, NNZ, s);
+    h2d(va.p, A->val, NNZ, s);
+    flag.alloc(2);
+    CUDA_TRY(cudaMemsetAsync(flag.p, 0, 2 * sizeof(int32_t), s));
+    launch_validate_csr(rp.p, ci.p, N, NNZ, flag.p, s);
+    int32_t hf = 0;
+    d2h(&hf, flag.p, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hf) fail(CIMMINO_EINVAL, "malformed CSR");
+    const int64_t tl = scan_tmp_len(N);
+    cp.alloc(N + 1);
+    ri.alloc(NNZ);
+    cv.alloc(NNZ);
+    work.alloc(2 * N);
+    tmp.alloc(tl);
+    launch_transpose(rp.p, ci.p, va.p, N, NNZ, cp.p, ri.p, cv.p, work.p, tmp.p, tl, s);
+    cnt.alloc(N);
+    ovf.alloc(N + 1);
+    spgemm_count(rp.p, ci.p, cp.p, ri.p, N, cnt.p, ovf.p + 1, ovf.p, s);
+    int32_t novf = 0;
+    d2h(&novf, ovf.p, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (novf > 0) {
+      spgemm_overflow(rp.p, ci.p, va.p, cp.p, ri.p, ovf.p + 1, novf, cnt.p, nullptr, nullptr,
+                      nullptr, flag.p + 1, s);
+      d2h(&hf, flag.p + 1, 1, s);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hf) fail(CIMMINO_EUNSUPPORTED, "a row of A A^T has more than 8192 structural candidates");
+    }
+    crp.alloc(N + 1);
+    launch_scan_counts(cnt.p, crp.p, N, tmp.p, tl, s);
+    int64_t nc = 0;
+    d2h(&nc, crp.p + N, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *nnz = nc;
+    d2h(row_ptr, crp.p, N + 1, s);
+    if (col_idx && val) {
+      cci.alloc(nc);
+      ccv.alloc(nc);
+      spgemm_fill(rp.p, ci.p, va.p, cp.p, ri.p, N, crp.p, cci.p, ccv.p, s);
+      if (novf > 0)
+        spgemm_overflow(rp.p, ci.p, va.p, cp.p, ri.p, ovf.p + 1, novf, cnt.p, crp.p, cci.p,
+                        ccv.p, flag.p + 1, s);
+      d2h(col_idx, cci.p, nc, s);
+      d2h(val, ccv.p, nc, s);
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(nullptr, e);
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+// Internal declarations of the GB300 block Cimmino library (not part of the C ABI).
+//
+// Data layout in HBM (all systems of a batch concatenated into one block-diagonal
+// matrix, so every stage is a single launch over all rows / blocks):
+//   A     : scaled, permuted CSR  (rp int64 [N+1], ci int32 [nnz], va f64 [nnz])
+//   At    : its transpose (CSC of A), rows increasing inside a column
+//   d     : row 2-norms of the original rows, permuted order
+//   C_bd  : block-diagonal part of C = A A^T: CSR over global rows with column
+//           indices local to the block (int32) and FP64 values -- the exact G_i,
+//           used by the FP64 refinement residual and to rebuild G_i for fallbacks
+//   factors: per block, per tile row I, the T x T tiles J0(I)..I of L_i stored
+//           contiguously (row-major inside a tile); dinv holds inv(L_II) per tile row.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cimmino.h"
+
+namespace cimmino {
+
+constexpr int kTile = 64;          // tile edge T of the factor layout
+constexpr int kMaxBlockRows = 4096;
+constexpr int kSpgemmWarpCap = 1024;   // candidates per row handled by one warp
+constexpr int kSpgemmCtaCap = 8192;    // candidates per row handled by one CTA
+
+struct BlockDesc {
+  int64_t row0;      // first global (permuted, concatenated) row
+  int64_t dinv_off;  // element offset of this block's inv(L_II) tiles in its dinv array
+  int32_t m;         // rows of the block
+  int32_t nt;        // tile rows = ceil(m / T)
+  int32_t trow0;     // first entry of this block in the tile-row table
+  int32_t sys;       // system index
+  int32_t prec64;    // 1: factor stored in FP64 arrays, 0: FP32 arrays
+  int32_t pad;
+};
+
+struct TileRow {
+  int64_t off;  // element offset of tile (I, J0) in the factor array of the block
+  int32_t j0;   // first stored tile column J0(I)
+  int32_t pad;
+};
+
+struct SysDesc {
+  int64_t row0;  // first global row (and column) of the system
+  int64_t n;     // rows of the system
+  int32_t cta0;  // first CTA of the system in the vector-kernel CTA table
+  int32_t ncta;  // CTAs of the system
+};
+
+// CTA table of the vector kernels: every CTA covers rows of exactly one system,
+// so per-CTA partial sums belong to one lane and are reduced in a fixed order.
+struct CtaDesc {
+  int64_t row0;
+  int32_t rows;
+  int32_t sys;
+};
+
+// Per right-hand side of a system ("lane") CG state, written by the kernels.
+struct LaneState {
+  double fnorm2;   // ||f||_2^2 of the original right-hand side
+  double rho[2];   // r^T r, indexed by iteration parity
+  double alpha;
+  double beta;
+  double pq;       // p^T H p of the current iteration
+  double relres;   // true relative residual of the current x
+  int32_t status;  // 0 running, 1 converged, CIMMINO_ENOCONV, CIMMINO_EBREAKDOWN
+  int32_t iters;   // projections used to produce the current x
+  int32_t t;       // iteration counter
+  int32_t pad;
+};
+
+#define CIMMINO_RUNNING 0
+#define CIMMINO_CONVERGED 1
+
+// --------------------------------------------------------------------------
+// host-side error handling
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define CUDA_TRY(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      throw ::cimmino::Error{CIMMINO_ECUDA, std::string(#call) + ": " +      \
+                                                cudaGetErrorString(e_)};      \
+  } while (0)
+
+inline void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+// --------------------------------------------------------------------------
+// device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic CTA-wide sum (fixed tree); every thread gets the result.
+// scratch: >= 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (unsigned)nw) ? scratch[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// --------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+
+// setup_kernels.cu
+void launch_validate_csr(const int64_t *rp, const int32_t *ci, int64_t n, int64_t nnz,
+                         int32_t *flag, cudaStream_t s);
+int64_t scan_tmp_len(int64_t n);
+void launch_scan_counts(const int64_t *counts, int64_t *out, int64_t n, int64_t *tmp,
+                        int64_t tmp_len, cudaStream_t s);
+void launch_permuted_lengths(const int64_t *rp0, const int32_t *perm, int64_t N, int64_t *len,
+                             cudaStream_t s);
+void launch_scale_permute(const int64_t *rp0, const int32_t *ci0, const double *v0,
+                          const int32_t *perm, const int64_t *rp, int64_t N, int32_t *ci,
+                          double *va, double *d, int32_t *flag, cudaStream_t s);
+void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, int64_t N,
+                      int64_t nnz, int64_t *cp, int32_t *ri, double *cv, int64_t *work,
+                      int64_t *tmp, int64_t tmp_len, cudaStream_t s);
+void spgemm_count(const int64_t *rp, const int32_t *ci, const int64_t *cp, const int32_t *ri,
+                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s);
+void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
+                     const int32_t *ri, const int32_t *ovf, int32_t novf, int64_t *cnt,
+                     const int64_t *crp, int32_t *cci, double *ccv, int32_t *flag,
+                     cudaStream_t s);
+void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
+                 const int32_t *ri, int64_t N, const int64_t *crp, int32_t *cci, double *ccv,
+                 cudaStream_t s);
+void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s);
+void bd_count(const int64_t *crp, const int32_t *cci, const BlockDesc *blk, const int32_t *rowblk,
+              int64_t N, int64_t *cnt, cudaStream_t s);
+void bd_fill(const int64_t *crp, const int32_t *cci, const double *ccv, const BlockDesc *blk,
+             const int32_t *rowblk, int64_t N, const int64_t *brp, int32_t *bci, double *bcv,
+             int32_t *rowmin, cudaStream_t s);
+void launch_tile_j0(const BlockDesc *blk, int32_t nblk, const int32_t *rowmin, int dense,
+                    int32_t *j0, cudaStream_t s);
+void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                         const TileRow *trow, const int64_t *brp, const int32_t *bci,
+                         const double *bcv, void *fac, int prec64, cudaStream_t s);
+
+// chol_kernels.cu
+void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                     const TileRow *trow, void *fac, void *dinv, int prec64, double *pivmin,
+                     int32_t *pivfail, cudaStream_t s);
+
+// solve_kernels.cu
+struct IterArgs {
+  const int64_t *rp;
+  const int32_t *ci;
+  const double *va;
+  const int64_t *cp;
+  const int32_t *ri;
+  const double *cv;
+  const double *d;
+  const int64_t *brp;
+  const int32_t *bci;
+  const double *bcv;
+  const BlockDesc *blk;
+  const TileRow *trow;
+  const float *fac32;
+  const float *dinv32;
+  const double *fac64;
+  const double *dinv64;
+  const SysDesc *sys;
+  const CtaDesc *cta;
+  LaneState *lane;
+  double *fs;     // scaled permuted right-hand sides, [N][nrhs] (row space)
+  double *x;      // [N][nrhs] (column space)
+  double *p;
+  double *r;
+  double *psi;
+  double *u;      // [N][nrhs] (row space)
+  double *y;
+  double *part;   // partial sums: 4 kinds x [ncta][nrhs]
+  int32_t *cnt;   // last-CTA arrival counters: 4 kinds x nsys
+  int64_t *refine_total;
+  int32_t *refine_max;
+  int64_t N;
+  int32_t nsys;
+  int32_t ncta;
+  int32_t nblk;
+  int32_t nrhs;
+  int32_t refine_steps;  // refinement steps allowed per inner solve of FP32 blocks
+  int32_t max_mp;        // largest padded block (rows), sizes the projection smem
+  int32_t proj_smem;     // dynamic shared memory bytes of the projection kernel
+  int32_t max_iter;
+  double refine_tol;
+  double tol;
+};
+
+int proj_smem_bytes(int max_mp);
+void set_proj_smem_attr(int bytes);
+void launch_rhs_scale(const IterArgs &a, const double *Fin, const int32_t *perm, cudaStream_t s);
+void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStream_t s);
+void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s);
+void launch_spmv_t(const IterArgs &a, const double *y, double *out, cudaStream_t s);
+void launch_cg_init(const IterArgs &a, cudaStream_t s);
+void launch_iteration(const IterArgs &a, cudaStream_t s);
+void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,
+                        cudaStream_t s);
+void launch_row_abs(const int64_t *rp, const double *va, const double *d, int64_t N,
+                    double *rowabs, cudaStream_t s);
+
+}  // namespace cimmino

@@ -1,0 +1,605 @@
+// Setup-stage kernels: input validation, row 2-norm scaling and permutation
+// (Sections 2.1-2.2), transpose, C = A A^T SpGEMM (Section 2.3), extraction of the
+// Gram blocks G_i (diagonal blocks of C) and their scatter into the tiled factor
+// layout.
+//
+// Arithmetic that decides values (row norms, C entries) uses explicitly rounded
+// multiply and add (no fused multiply-add), summing in increasing column index,
+// so that scaled A and C are reproducible bit for bit run to run.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cimmino {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int per_cta) {
+  int64_t g = (n + per_cta - 1) / per_cta;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- validation
+// flag bits: 1 = row_ptr not monotone / bad ends, 2 = column out of range,
+// 4 = columns not strictly increasing
+__global__ void k_validate_csr(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               int64_t n, int64_t nnz, int32_t *flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(flag, 1);
+  if (i >= n) return;
+  int64_t a = rp[i], b = rp[i + 1];
+  if (a > b || a < 0 || b > nnz) {
+    atomicOr(flag, 1);
+    return;
+  }
+  int32_t prev = -1;
+  for (int64_t q = a; q < b; ++q) {
+    int32_t c = ci[q];
+    if (c < 0 || c >= n) atomicOr(flag, 2);
+    if (c <= prev) atomicOr(flag, 4);
+    prev = c;
+  }
+}
+
+// ---------------------------------------------------------------- scan
+// out[0] = 0, out[i+1] = counts[0] + ... + counts[i]; three passes over chunks of
+// kScanChunk elements (chunk scan, scan of chunk totals, add-back).
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kThreads * kScanPer;
+
+__global__ void k_scan_chunks(const int64_t *__restrict__ in, int64_t *__restrict__ out,
+                              int64_t n, int64_t *__restrict__ totals) {
+  __shared__ int64_t wsum[kThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  int64_t v[kScanPer];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    int64_t idx = base + k;
+    v[k] = idx < n ? in[idx] : 0;
+    s += v[k];
+  }
+  // exclusive scan of per-thread sums across the CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kThreads / 32 ? wsum[lane] : 0;
+    int64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kThreads / 32) wsum[lane] = wi - w;  // exclusive warp offsets
+    if (lane == kThreads / 32 - 1) totals[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  int64_t run = wsum[warp] + inc - s;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    run += v[k];
+    int64_t idx = base + k;
+    if (idx < n) out[idx + 1] = run;
+  }
+}
+
+__global__ void k_scan_totals(int64_t *totals, int64_t nb) {
+  // single CTA: exclusive scan of nb chunk totals, in place
+  __shared__ int64_t carry;
+  __shared__ int64_t wsum[kThreads / 32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t b0 = 0; b0 < nb; b0 += kThreads) {
+    int64_t idx = b0 + threadIdx.x;
+    int64_t v = idx < nb ? totals[idx] : 0;
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int64_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += wsum[w];
+    int64_t c = carry;
+    if (idx < nb) totals[idx] = c + woff + inc - v;
+    __syncthreads();
+    if (threadIdx.x == kThreads - 1) carry = c + woff + inc;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, int64_t n,
+                           const int64_t *__restrict__ totals) {
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  const int64_t add = totals[blockIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+  for (int k = threadIdx.x; k < kScanChunk; k += kThreads) {
+    int64_t idx = base + k;
+    if (idx < n) out[idx + 1] += add;
+  }
+}
+
+// ---------------------------------------------------------------- scale + permute
+__global__ void k_permuted_lengths(const int64_t *__restrict__ rp0, const int32_t *__restrict__ perm,
+                                   int64_t N, int64_t *__restrict__ len) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int64_t o = perm[r];
+  len[r] = rp0[o + 1] - rp0[o];
+}
+
+// Section 2.1: every row is divided by its 2-norm (so that the entries of
+// A A^T are cosines); Section 2.2: permuted row r is original row perm[r].
+__global__ void k_scale_permute(const int64_t *__restrict__ rp0, const int32_t *__restrict__ ci0,
+                                const double *__restrict__ v0, const int32_t *__restrict__ perm,
+                                const int64_t *__restrict__ rp, int64_t N,
+                                int32_t *__restrict__ ci, double *__restrict__ va,
+                                double *__restrict__ d, int32_t *flag) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int64_t o = perm[r];
+  int64_t a = rp0[o], b = rp0[o + 1];
+  double ss = 0.0;
+  for (int64_t q = a; q < b; ++q) ss = __dadd_rn(ss, __dmul_rn(v0[q], v0[q]));
+  double nr = sqrt(ss);
+  if (!(nr > 0.0) || !isfinite(nr)) {
+    atomicOr(flag, 1);
+    nr = 1.0;
+  }
+  d[r] = nr;
+  int64_t w = rp[r];
+  for (int64_t q = a; q < b; ++q, ++w) {
+    ci[w] = ci0[q];
+    va[w] = __ddiv_rn(v0[q], nr);
+  }
+}
+
+// ---------------------------------------------------------------- transpose
+__global__ void k_col_count(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            int64_t N, unsigned long long *__restrict__ cnt) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) atomicAdd(&cnt[ci[q]], 1ull);
+}
+
+__global__ void k_col_fill(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ va, int64_t N,
+                           unsigned long long *__restrict__ cursor, int32_t *__restrict__ ri,
+                           double *__restrict__ cv) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+    unsigned long long pos = atomicAdd(&cursor[ci[q]], 1ull);
+    ri[pos] = (int32_t)r;
+    cv[pos] = va[q];
+  }
+}
+
+// rows inside a column end up in atomic order; sort them (insertion sort, columns
+// of sparse matrices are short) so the transpose is deterministic.
+__global__ void k_col_sort(const int64_t *__restrict__ cp, int64_t N, int32_t *__restrict__ ri,
+                           double *__restrict__ cv) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int64_t a = cp[k], b = cp[k + 1];
+  for (int64_t q = a + 1; q < b; ++q) {
+    int32_t key = ri[q];
+    double val = cv[q];
+    int64_t t = q - 1;
+    while (t >= a && ri[t] > key) {
+      ri[t + 1] = ri[t];
+      cv[t + 1] = cv[t];
+      --t;
+    }
+    ri[t + 1] = key;
+    cv[t + 1] = val;
+  }
+}
+
+// ---------------------------------------------------------------- SpGEMM C = A A^T
+// Row i of C: the candidate set is the union, over the columns k of row i, of the
+// rows of column k.  A group (a warp, or a whole CTA for long rows) gathers the
+// candidates into shared memory, sorts them (bitonic) and keeps the distinct ones.
+// Values follow the definition c_ij = sum_k a_ik a_jk, evaluated by merging the two
+// sorted rows in increasing k -- the same order as Gustavson's accumulation.
+
+template <int G>
+__device__ __forceinline__ void group_sync() {
+  if (G == 32)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+template <int G>
+__device__ int gather_candidates(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
+                                 int64_t i, int32_t *buf, int cap, int gt) {
+  int U = 0;
+  for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+    int32_t k = ci[q];
+    int64_t s0 = cp[k];
+    int len = (int)(cp[k + 1] - s0);
+    for (int t = gt; t < len; t += G)
+      if (U + t < cap) buf[U + t] = ri[s0 + t];
+    U += len;
+  }
+  group_sync<G>();
+  return U;
+}
+
+template <int G>
+__device__ void bitonic_sort(int32_t *buf, int U, int gt) {
+  int P = 1;
+  while (P < U) P <<= 1;
+  for (int t = U + gt; t < P; t += G) buf[t] = 0x7fffffff;
+  group_sync<G>();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = gt; t < P; t += G) {
+        int ixj = t ^ j;
+        if (ixj > t) {
+          int32_t a = buf[t], b = buf[ixj];
+          bool up = (t & k) == 0;
+          if ((a > b) == up) {
+            buf[t] = b;
+            buf[ixj] = a;
+          }
+        }
+      }
+      group_sync<G>();
+    }
+  }
+}
+
+// in-place compaction of the distinct values of sorted buf[0..U); returns count
+template <int G>
+__device__ int unique_compact(int32_t *buf, int U, int gt) {
+  if (G == 32) {
+    int total = 0;
+    for (int base = 0; base < U; base += 32) {
+      int t = base + gt;
+      int32_t v = t < U ? buf[t] : 0;
+      bool keep = t < U && (t == 0 || buf[t - 1] != v);
+      unsigned m = __ballot_sync(0xffffffffu, keep);
+      int pos = total + __popc(m & ((1u << gt) - 1u));
+      __syncwarp();
+      if (keep) buf[pos] = v;  // pos <= t: never overwrites an unread later entry
+      __syncwarp();
+      total += __popc(m);
+    }
+    return total;
+  } else {
+    __shared__ int s_total;
+    if (gt == 0) {
+      int w = 0;
+      for (int t = 0; t < U; ++t)
+        if (t == 0 || buf[t] != buf[w - 1]) buf[w++] = buf[t];
+      s_total = w;
+    }
+    __syncthreads();
+    int r = s_total;
+    __syncthreads();
+    return r;
+  }
+}
+
+__device__ __forceinline__ double row_dot(const int64_t *__restrict__ rp,
+                                          const int32_t *__restrict__ ci,
+                                          const double *__restrict__ va, int64_t i, int64_t j) {
+  int64_t qa = rp[i], ea = rp[i + 1], qb = rp[j], eb = rp[j + 1];
+  double acc = 0.0;
+  bool first = true;
+  while (qa < ea && qb < eb) {
+    int32_t ka = ci[qa], kb = ci[qb];
+    if (ka == kb) {
+      double prod = __dmul_rn(va[qa], va[qb]);
+      acc = first ? prod : __dadd_rn(acc, prod);
+      first = false;
+      ++qa;
+      ++qb;
+    } else if (ka < kb) {
+      ++qa;
+    } else {
+      ++qb;
+    }
+  }
+  return acc;
+}
+
+constexpr int kSpgemmWarps = 8;
+
+// count pass, one warp per row; rows with more than kSpgemmWarpCap candidates are
+// appended to an overflow list (handled by the CTA-per-row variant).
+__global__ void __launch_bounds__(kSpgemmWarps * 32)
+    k_spgemm_count_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                        const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
+                        int64_t N, int64_t *__restrict__ cnt, int32_t *__restrict__ ovf_list,
+                        int32_t *__restrict__ ovf_n) {
+  __shared__ int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
+  if (i >= N) return;
+  int32_t *buf = sbuf[warp];
+  int U = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+  if (U > kSpgemmWarpCap) {
+    if (lane == 0) {
+      int slot = atomicAdd(ovf_n, 1);
+      ovf_list[slot] = (int32_t)i;
+      cnt[i] = 0;
+    }
+    return;
+  }
+  bitonic_sort<32>(buf, U, lane);
+  int u = unique_compact<32>(buf, U, lane);
+  if (lane == 0) cnt[i] = u;
+}
+
+__global__ void __launch_bounds__(kSpgemmWarps * 32)
+    k_spgemm_fill_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ va, const int64_t *__restrict__ cp,
+                       const int32_t *__restrict__ ri, int64_t N, const int64_t *__restrict__ crp,
+                       int32_t *__restrict__ cci, double *__restrict__ ccv) {
+  __shared__ int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
+  if (i >= N) return;
+  int32_t *buf = sbuf[warp];
+  int U = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+  if (U > kSpgemmWarpCap) return;  // CTA variant fills this row
+  bitonic_sort<32>(buf, U, lane);
+  int u = unique_compact<32>(buf, U, lane);
+  int64_t w = crp[i];
+  for (int t = lane; t < u; t += 32) {
+    int32_t j = buf[t];
+    cci[w + t] = j;
+    ccv[w + t] = row_dot(rp, ci, va, i, j);
+  }
+}
+
+__global__ void k_spgemm_cta(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ va, const int64_t *__restrict__ cp,
+                             const int32_t *__restrict__ ri, const int32_t *__restrict__ ovf_list,
+                             int64_t *__restrict__ cnt, const int64_t *__restrict__ crp,
+                             int32_t *__restrict__ cci, double *__restrict__ ccv,
+                             int32_t *flag) {
+  extern __shared__ int32_t dbuf[];
+  const int64_t i = ovf_list[blockIdx.x];
+  int U = gather_candidates<kThreads>(rp, ci, cp, ri, i, dbuf, kSpgemmCtaCap, threadIdx.x);
+  if (U > kSpgemmCtaCap) {
+    if (threadIdx.x == 0) atomicOr(flag, 8);
+    return;
+  }
+  bitonic_sort<kThreads>(dbuf, U, threadIdx.x);
+  int u = unique_compact<kThreads>(dbuf, U, threadIdx.x);
+  if (crp == nullptr) {
+    if (threadIdx.x == 0) cnt[i] = u;
+    return;
+  }
+  int64_t w = crp[i];
+  for (int t = threadIdx.x; t < u; t += kThreads) {
+    int32_t j = dbuf[t];
+    cci[w + t] = j;
+    ccv[w + t] = row_dot(rp, ci, va, i, j);
+  }
+}
+
+// ---------------------------------------------------------------- block-diagonal part of C
+__global__ void k_row_block_ids(const BlockDesc *__restrict__ blk, int32_t nblk,
+                                int32_t *__restrict__ rowblk) {
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  BlockDesc B = blk[b];
+  for (int r = threadIdx.x; r < B.m; r += blockDim.x) rowblk[B.row0 + r] = b;
+}
+
+__global__ void k_bd_count(const int64_t *__restrict__ crp, const int32_t *__restrict__ cci,
+                           const BlockDesc *__restrict__ blk, const int32_t *__restrict__ rowblk,
+                           int64_t N, int64_t *__restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  BlockDesc B = blk[rowblk[i]];
+  int64_t lo = B.row0, hi = B.row0 + B.m;
+  int64_t c = 0;
+  for (int64_t q = crp[i]; q < crp[i + 1]; ++q) {
+    int64_t j = cci[q];
+    c += (j >= lo && j < hi);
+  }
+  cnt[i] = c;
+}
+
+// G_i = C restricted to block i (both triangles, local column indices); rowmin[i]
+// = first local column of the row, the left end of its envelope.
+__global__ void k_bd_fill(const int64_t *__restrict__ crp, const int32_t *__restrict__ cci,
+                          const double *__restrict__ ccv, const BlockDesc *__restrict__ blk,
+                          const int32_t *__restrict__ rowblk, int64_t N,
+                          const int64_t *__restrict__ brp, int32_t *__restrict__ bci,
+                          double *__restrict__ bcv, int32_t *__restrict__ rowmin) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  BlockDesc B = blk[rowblk[i]];
+  int64_t lo = B.row0, hi = B.row0 + B.m;
+  int64_t w = brp[i];
+  int32_t mn = (int32_t)(i - lo);
+  for (int64_t q = crp[i]; q < crp[i + 1]; ++q) {
+    int64_t j = cci[q];
+    if (j >= lo && j < hi) {
+      int32_t lj = (int32_t)(j - lo);
+      bci[w] = lj;
+      bcv[w] = ccv[q];
+      ++w;
+      if (lj < mn) mn = lj;
+    }
+  }
+  rowmin[i] = mn;
+}
+
+// J0 of every tile row: the smallest tile column touched by the envelope of the
+// rows of the tile row (0 for the dense layout).
+__global__ void k_tile_j0(const BlockDesc *__restrict__ blk, int32_t nblk,
+                          const int32_t *__restrict__ rowmin, int dense,
+                          int32_t *__restrict__ j0) {
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  BlockDesc B = blk[b];
+  for (int I = threadIdx.x; I < B.nt; I += blockDim.x) {
+    int v = I;
+    if (!dense) {
+      int r1 = min((I + 1) * kTile, B.m);
+      for (int r = I * kTile; r < r1; ++r) v = min(v, rowmin[B.row0 + r] / kTile);
+    } else {
+      v = 0;
+    }
+    j0[B.trow0 + I] = v;
+  }
+}
+
+// Write the lower triangle of G_b into the tiles of its factor (zeroing the tile
+// row first); padded rows beyond m get a unit diagonal.
+template <typename W>
+__global__ void k_gram_scatter(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
+                               const TileRow *__restrict__ trow, const int64_t *__restrict__ brp,
+                               const int32_t *__restrict__ bci, const double *__restrict__ bcv,
+                               W *__restrict__ fac) {
+  const int b = blist[blockIdx.x];
+  const BlockDesc B = blk[b];
+  const int mp = B.nt * kTile;
+  for (int r = threadIdx.x; r < mp; r += blockDim.x) {
+    const int I = r / kTile, rr = r % kTile;
+    const TileRow T = trow[B.trow0 + I];
+    W *rowbase = fac + T.off + (int64_t)rr * kTile;
+    const int ntiles = I - T.j0 + 1;
+    for (int t = 0; t < ntiles; ++t)
+      for (int c = 0; c < kTile; ++c) rowbase[(int64_t)t * kTile * kTile + c] = W(0);
+    if (r >= B.m) {
+      rowbase[(int64_t)(I - T.j0) * kTile * kTile + rr] = W(1);
+      continue;
+    }
+    const int64_t gi = B.row0 + r;
+    for (int64_t q = brp[gi]; q < brp[gi + 1]; ++q) {
+      int j = bci[q];
+      if (j > r) break;  // columns sorted: only the lower triangle is stored
+      int J = j / kTile;
+      rowbase[(int64_t)(J - T.j0) * kTile * kTile + (j % kTile)] = W(bcv[q]);
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================ launchers
+void launch_validate_csr(const int64_t *rp, const int32_t *ci, int64_t n, int64_t nnz,
+                         int32_t *flag, cudaStream_t s) {
+  k_validate_csr<<<grid_for(n + 1, kThreads), kThreads, 0, s>>>(rp, ci, n, nnz, flag);
+}
+
+int64_t scan_tmp_len(int64_t n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
+
+void launch_scan_counts(const int64_t *counts, int64_t *out, int64_t n, int64_t *tmp,
+                        int64_t tmp_len, cudaStream_t s) {
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  if (nb < 1) nb = 1;
+  (void)tmp_len;
+  k_scan_chunks<<<(unsigned)nb, kThreads, 0, s>>>(counts, out, n, tmp);
+  k_scan_totals<<<1, kThreads, 0, s>>>(tmp, nb);
+  k_scan_add<<<(unsigned)nb, kThreads, 0, s>>>(out, n, tmp);
+}
+
+void launch_permuted_lengths(const int64_t *rp0, const int32_t *perm, int64_t N, int64_t *len,
+                             cudaStream_t s) {
+  k_permuted_lengths<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp0, perm, N, len);
+}
+
+void launch_scale_permute(const int64_t *rp0, const int32_t *ci0, const double *v0,
+                          const int32_t *perm, const int64_t *rp, int64_t N, int32_t *ci,
+                          double *va, double *d, int32_t *flag, cudaStream_t s) {
+  k_scale_permute<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp0, ci0, v0, perm, rp, N, ci, va,
+                                                             d, flag);
+}
+
+void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, int64_t N,
+                      int64_t nnz, int64_t *cp, int32_t *ri, double *cv, int64_t *work,
+                      int64_t *tmp, int64_t tmp_len, cudaStream_t s) {
+  // work: 2*N int64 (column counts, then fill cursors)
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(work);
+  unsigned long long *cur = cnt + N;
+  cudaMemsetAsync(cnt, 0, sizeof(int64_t) * N, s);
+  k_col_count<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp, ci, N, cnt);
+  launch_scan_counts(reinterpret_cast<int64_t *>(cnt), cp, N, tmp, tmp_len, s);
+  cudaMemcpyAsync(cur, cp, sizeof(int64_t) * N, cudaMemcpyDeviceToDevice, s);
+  k_col_fill<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp, ci, va, N, cur, ri, cv);
+  k_col_sort<<<grid_for(N, kThreads), kThreads, 0, s>>>(cp, N, ri, cv);
+  (void)nnz;
+}
+
+void spgemm_count(const int64_t *rp, const int32_t *ci, const int64_t *cp, const int32_t *ri,
+                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s) {
+  cudaMemsetAsync(ovf_n, 0, sizeof(int32_t), s);
+  k_spgemm_count_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(rp, ci, cp, ri, N,
+                                                                             cnt, ovf, ovf_n);
+}
+
+void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
+                     const int32_t *ri, const int32_t *ovf, int32_t novf, int64_t *cnt,
+                     const int64_t *crp, int32_t *cci, double *ccv, int32_t *flag,
+                     cudaStream_t s) {
+  if (novf <= 0) return;
+  size_t smem = sizeof(int32_t) * kSpgemmCtaCap;
+  k_spgemm_cta<<<(unsigned)novf, kThreads, smem, s>>>(rp, ci, va, cp, ri, ovf, cnt, crp, cci,
+                                                      ccv, flag);
+}
+
+void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
+                 const int32_t *ri, int64_t N, const int64_t *crp, int32_t *cci, double *ccv,
+                 cudaStream_t s) {
+  k_spgemm_fill_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(rp, ci, va, cp, ri,
+                                                                            N, crp, cci, ccv);
+}
+
+void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s) {
+  if (nblk > 0) k_row_block_ids<<<(unsigned)nblk, kThreads, 0, s>>>(blk, nblk, rowblk);
+}
+
+void bd_count(const int64_t *crp, const int32_t *cci, const BlockDesc *blk, const int32_t *rowblk,
+              int64_t N, int64_t *cnt, cudaStream_t s) {
+  k_bd_count<<<grid_for(N, kThreads), kThreads, 0, s>>>(crp, cci, blk, rowblk, N, cnt);
+}
+
+void bd_fill(const int64_t *crp, const int32_t *cci, const double *ccv, const BlockDesc *blk,
+             const int32_t *rowblk, int64_t N, const int64_t *brp, int32_t *bci, double *bcv,
+             int32_t *rowmin, cudaStream_t s) {
+  k_bd_fill<<<grid_for(N, kThreads), kThreads, 0, s>>>(crp, cci, ccv, blk, rowblk, N, brp, bci,
+                                                       bcv, rowmin);
+}
+
+void launch_tile_j0(const BlockDesc *blk, int32_t nblk, const int32_t *rowmin, int dense,
+                    int32_t *j0, cudaStream_t s) {
+  if (nblk > 0) k_tile_j0<<<(unsigned)nblk, 64, 0, s>>>(blk, nblk, rowmin, dense, j0);
+}
+
+void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                         const TileRow *trow, const int64_t *brp, const int32_t *bci,
+                         const double *bcv, void *fac, int prec64, cudaStream_t s) {
+  if (nlist <= 0) return;
+  if (prec64)
+    k_gram_scatter<double><<<(unsigned)nlist, kThreads, 0, s>>>(
+        blk, blist, trow, brp, bci, bcv, static_cast<double *>(fac));
+  else
+    k_gram_scatter<float><<<(unsigned)nlist, kThreads, 0, s>>>(
+        blk, blist, trow, brp, bci, bcv, static_cast<float *>(fac));
+}
+
+}  // namespace cimmino

@@ -1,0 +1,596 @@
+// Per-iteration kernels of Algorithm 2 (CG on H x = xi, Section 1.1):
+//   k_spmv_res   u = A p (projection input) and the true residual of the current x
+//                (||f - A x||_2 through the scaled system: (f - A x)_orig = D (f_s - A_s x))
+//   k_proj       y_i = G_i^{-1} u_i per block: forward / backward solves with the tiled
+//                factor (inverted diagonal tiles) and, for FP32 factors, FP64 iterative
+//                refinement against the exact Gram block G_i (sparse, FP64)
+//   k_spmv_t     psi = A^T y = sum_i A_i^T y_i (gather over the transpose: no atomics)
+//                fused with p^T psi
+//   k_update_xr  x += alpha p, r -= alpha psi, fused with r^T r
+//   k_update_p   p = r + beta p
+// Reductions are deterministic: every CTA covers rows of one system only, writes
+// its partial sums, and the last CTA to arrive (threadfence + counter) sums the
+// partials of its system in a fixed order and updates the per-lane CG state.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cimmino {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int T = kTile;
+constexpr int kWarps = kThreads / 32;
+
+// partial-sum kinds
+enum { kPartRes = 0, kPartPq = 1, kPartRr = 2, kPartMisc = 3, kNumParts = 4 };
+
+__device__ __forceinline__ double *part_ptr(const IterArgs &a, int kind) {
+  return a.part + (int64_t)kind * a.ncta * a.nrhs;
+}
+
+// Returns true in the last CTA (of the system's CTAs) to finish.
+__device__ __forceinline__ bool arrive_last(int32_t *counter, int ncta) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int prev = atomicAdd(counter, 1);
+    s_last = (prev == ncta - 1);
+    if (s_last) *counter = 0;  // reset for the next launch (all CTAs have arrived)
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Sum of the partials of one system for rhs k, fixed order; valid in warp 0.
+__device__ __forceinline__ double reduce_partials(const double *part, const SysDesc &S, int nrhs,
+                                                  int k) {
+  double v = 0.0;
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < S.ncta; c += 32) v += __ldcg(part + (int64_t)(S.cta0 + c) * nrhs + k);
+  return warp_sum(v);
+}
+
+__device__ __forceinline__ bool lane_running(const IterArgs &a, int sys, int k) {
+  return a.lane[sys * a.nrhs + k].status == CIMMINO_RUNNING;
+}
+
+// ----------------------------------------------------------------------------
+// right-hand side: fs[r][k] = F[k][perm(r)] / d[r]; ||f_k||^2 per lane
+__global__ void __launch_bounds__(kThreads)
+    k_rhs_scale(IterArgs a, const double *__restrict__ Fin, const int32_t *__restrict__ perm) {
+  __shared__ double red[32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t r = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  for (int k = 0; k < a.nrhs; ++k) {
+    double f2 = 0.0;
+    if (act) {
+      double fo = Fin[(int64_t)k * a.N + r];  // original order row r (same system range)
+      f2 = fo * fo;
+      a.fs[r * a.nrhs + k] = Fin[(int64_t)k * a.N + perm[r]] / a.d[r];
+    }
+    double s = block_sum(f2, red);
+    if (threadIdx.x == 0) part_ptr(a, kPartMisc)[(int64_t)blockIdx.x * a.nrhs + k] = s;
+  }
+  if (arrive_last(a.cnt + kPartMisc * a.nsys + C.sys, S.ncta)) {
+    if (threadIdx.x < 32)
+      for (int k = 0; k < a.nrhs; ++k) {
+        double f2 = reduce_partials(part_ptr(a, kPartMisc), S, a.nrhs, k);
+        if (threadIdx.x == 0) {
+          LaneState &L = a.lane[C.sys * a.nrhs + k];
+          L.fnorm2 = f2;
+          L.t = 0;
+          L.iters = 0;
+          L.relres = f2 > 0.0 ? 1.0 : 0.0;
+          L.status = f2 > 0.0 ? CIMMINO_RUNNING : CIMMINO_CONVERGED;
+        }
+      }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// u = A v (plain SpMV over the scaled permuted rows), for the projection hooks
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_plain(IterArgs a, const double *__restrict__ v, double *__restrict__ out) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  if (threadIdx.x >= C.rows) return;
+  const int64_t r = C.row0 + threadIdx.x;
+  for (int k = 0; k < a.nrhs; ++k) {
+    double s = 0.0;
+    for (int64_t q = a.rp[r]; q < a.rp[r + 1]; ++q) s = fma(a.va[q], v[(int64_t)a.ci[q] * a.nrhs + k], s);
+    out[r * a.nrhs + k] = s;
+  }
+}
+
+// u = A p and the residual of x (iteration step 1, convergence decision)
+__global__ void __launch_bounds__(kThreads) k_spmv_res(IterArgs a) {
+  __shared__ double red[32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t r = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  for (int k = 0; k < a.nrhs; ++k) {
+    if (!lane_running(a, C.sys, k)) continue;  // uniform across the CTA
+    double e2 = 0.0;
+    if (act) {
+      double su = 0.0, sx = 0.0;
+      for (int64_t q = a.rp[r]; q < a.rp[r + 1]; ++q) {
+        const double av = a.va[q];
+        const int64_t c = (int64_t)a.ci[q] * a.nrhs + k;
+        su = fma(av, a.p[c], su);
+        sx = fma(av, a.x[c], sx);
+      }
+      a.u[r * a.nrhs + k] = su;
+      double e = a.d[r] * (a.fs[r * a.nrhs + k] - sx);
+      e2 = e * e;
+    }
+    double s = block_sum(e2, red);
+    if (threadIdx.x == 0) part_ptr(a, kPartRes)[(int64_t)blockIdx.x * a.nrhs + k] = s;
+  }
+  if (arrive_last(a.cnt + kPartRes * a.nsys + C.sys, S.ncta)) {
+    if (threadIdx.x < 32)
+      for (int k = 0; k < a.nrhs; ++k) {
+        LaneState &L = a.lane[C.sys * a.nrhs + k];
+        if (L.status != CIMMINO_RUNNING) continue;
+        double e2 = reduce_partials(part_ptr(a, kPartRes), S, a.nrhs, k);
+        if (threadIdx.x == 0) {
+          double rel = sqrt(e2 / L.fnorm2);
+          L.relres = rel;
+          if (rel <= a.tol) {
+            L.status = CIMMINO_CONVERGED;
+            L.iters = L.t;
+          } else if (L.t >= a.max_iter) {
+            L.status = CIMMINO_ENOCONV;
+            L.iters = L.t;
+          }
+        }
+      }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// projection kernel: one CTA per block
+
+struct ProjSmem {
+  double *u, *y, *res;
+  void *w;   // working-precision vector (mp entries, sized for double)
+  void *bI;  // T entries
+  void *part;  // 2 x kWarps x T entries
+  double *red;
+};
+
+__device__ __forceinline__ ProjSmem proj_smem(int mp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ProjSmem s;
+  double *p = reinterpret_cast<double *>(smem_raw);
+  s.u = p;
+  s.y = p + mp;
+  s.res = p + 2 * mp;
+  s.w = p + 3 * mp;
+  s.bI = p + 4 * mp;
+  s.part = p + 4 * mp + T;
+  s.red = p + 4 * mp + T + 2 * kWarps * T;
+  return s;
+}
+
+template <typename W>
+__device__ __forceinline__ W pick8(const W (&acc)[8], int lane) {
+  W v = W(0);
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr)
+    if (lane == rr) v = acc[rr];
+  return v;
+}
+
+// w <- L^{-1} w  (tile rows in order; inverted diagonal tiles)
+template <typename W>
+__device__ void tile_forward(const W *__restrict__ fac, const TileRow *__restrict__ tr,
+                             const W *__restrict__ dinv, int nt, W *w, W *bI) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int I = 0; I < nt; ++I) {
+    const TileRow TI = tr[I];
+    const W *base = fac + TI.off;
+    W acc[8];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = W(0);
+#pragma unroll 2
+    for (int J = TI.j0; J < I; ++J) {
+      const W *t = base + (int64_t)(J - TI.j0) * T * T + (warp * 8) * T;
+      const W z0 = w[J * T + lane], z1 = w[J * T + lane + 32];
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        acc[rr] = fma(t[rr * T + lane], z0, acc[rr]);
+        acc[rr] = fma(t[rr * T + lane + 32], z1, acc[rr]);
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = warp_sum(acc[rr]);
+    if (lane < 8) bI[warp * 8 + lane] = w[I * T + warp * 8 + lane] - pick8(acc, lane);
+    __syncthreads();
+    const W *D = dinv + (int64_t)I * T * T + (warp * 8) * T;
+    const W b0 = bI[lane], b1 = bI[lane + 32];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      W s = D[rr * T + lane] * b0;
+      s = fma(D[rr * T + lane + 32], b1, s);
+      acc[rr] = warp_sum(s);
+    }
+    if (lane < 8) w[I * T + warp * 8 + lane] = pick8(acc, lane);
+    __syncthreads();
+  }
+}
+
+// w <- L^{-T} w  (tile rows in reverse order)
+template <typename W>
+__device__ void tile_backward(const W *__restrict__ fac, const TileRow *__restrict__ tr,
+                              const W *__restrict__ dinv, int nt, W *w, W *part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int I = nt - 1; I >= 0; --I) {
+    const TileRow TI = tr[I];
+    // y_I = inv(L_II)^T w_I
+    {
+      const W *D = dinv + (int64_t)I * T * T + (warp * 8) * T;
+      W p0 = W(0), p1 = W(0);
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const W wr = w[I * T + warp * 8 + rr];
+        p0 = fma(D[rr * T + lane], wr, p0);
+        p1 = fma(D[rr * T + lane + 32], wr, p1);
+      }
+      part[warp * T + lane] = p0;
+      part[warp * T + lane + 32] = p1;
+      __syncthreads();
+      if (threadIdx.x < T) {
+        W s = W(0);
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s += part[q * T + threadIdx.x];
+        w[I * T + threadIdx.x] = s;
+      }
+      __syncthreads();
+    }
+    // w_J -= L_IJ^T y_I for the stored tiles left of the diagonal
+    W yr[8];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) yr[rr] = w[I * T + warp * 8 + rr];
+    const W *base = fac + TI.off;
+    int buf = 0;
+    for (int J = I - 1; J >= TI.j0; --J) {
+      const W *t = base + (int64_t)(J - TI.j0) * T * T + (warp * 8) * T;
+      W p0 = W(0), p1 = W(0);
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        p0 = fma(t[rr * T + lane], yr[rr], p0);
+        p1 = fma(t[rr * T + lane + 32], yr[rr], p1);
+      }
+      W *pb = part + buf * kWarps * T;
+      pb[warp * T + lane] = p0;
+      pb[warp * T + lane + 32] = p1;
+      __syncthreads();
+      if (threadIdx.x < T) {
+        W s = W(0);
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s += pb[q * T + threadIdx.x];
+        w[J * T + threadIdx.x] -= s;
+      }
+      buf ^= 1;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename W>
+__device__ void proj_block(const IterArgs &a, const BlockDesc &B, const W *fac, const W *dinv,
+                           const double *__restrict__ u, double *__restrict__ y, int k,
+                           int refine_steps, const ProjSmem &sm) {
+  const int mp = B.nt * T;
+  const int tid = threadIdx.x;
+  W *w = reinterpret_cast<W *>(sm.w);
+  for (int r = tid; r < mp; r += kThreads) {
+    sm.u[r] = r < B.m ? u[(B.row0 + r) * a.nrhs + k] : 0.0;
+    sm.y[r] = 0.0;
+    sm.res[r] = 0.0;
+  }
+  __syncthreads();
+  double un2 = 0.0;
+  if (refine_steps > 0) {
+    for (int r = tid; r < B.m; r += kThreads) un2 += sm.u[r] * sm.u[r];
+    un2 = block_sum(un2, sm.red);
+  }
+  const double *rhs = sm.u;
+  const TileRow *tr = a.trow + B.trow0;
+  const W *dblk = dinv + B.dinv_off;
+  int s = 0;
+  for (;;) {
+    for (int r = tid; r < mp; r += kThreads) w[r] = W(rhs[r]);
+    __syncthreads();
+    tile_forward<W>(fac, tr, dblk, B.nt, w, reinterpret_cast<W *>(sm.bI));
+    tile_backward<W>(fac, tr, dblk, B.nt, w, reinterpret_cast<W *>(sm.part));
+    for (int r = tid; r < mp; r += kThreads) sm.y[r] += double(w[r]);
+    __syncthreads();
+    if (s >= refine_steps) break;
+    // FP64 residual of the inner system: res = u - G_i y with the exact Gram block
+    double e2 = 0.0;
+    for (int r = tid; r < B.m; r += kThreads) {
+      const int64_t gr = B.row0 + r;
+      double acc = sm.u[r];
+      for (int64_t q = a.brp[gr]; q < a.brp[gr + 1]; ++q) acc = fma(-a.bcv[q], sm.y[a.bci[q]], acc);
+      sm.res[r] = acc;
+      e2 += acc * acc;
+    }
+    e2 = block_sum(e2, sm.red);
+    if (e2 <= a.refine_tol * a.refine_tol * un2) break;
+    ++s;
+    rhs = sm.res;
+  }
+  for (int r = tid; r < B.m; r += kThreads) y[(B.row0 + r) * a.nrhs + k] = sm.y[r];
+  if (tid == 0 && refine_steps > 0) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(a.refine_total), (unsigned long long)s);
+    atomicMax(a.refine_max, s);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_proj(IterArgs a, const double *__restrict__ u, double *__restrict__ y, int check_lane) {
+  const BlockDesc B = a.blk[blockIdx.x];
+  const ProjSmem sm = proj_smem(a.max_mp);
+  for (int k = 0; k < a.nrhs; ++k) {
+    if (check_lane && !lane_running(a, B.sys, k)) continue;
+    if (B.prec64)
+      proj_block<double>(a, B, a.fac64, a.dinv64, u, y, k, 0, sm);
+    else
+      proj_block<float>(a, B, a.fac32, a.dinv32, u, y, k, a.refine_steps, sm);
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// psi = A^T y (column gather over the transpose); MODE 1 also reduces p^T psi -> alpha
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_t(IterArgs a, const double *__restrict__ yin, double *__restrict__ out) {
+  __shared__ double red[32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;  // column index (square systems)
+  const bool act = threadIdx.x < C.rows;
+  for (int k = 0; k < a.nrhs; ++k) {
+    if (MODE == 1 && !lane_running(a, C.sys, k)) continue;
+    double pq = 0.0;
+    if (act) {
+      double s = 0.0;
+      for (int64_t q = a.cp[j]; q < a.cp[j + 1]; ++q)
+        s = fma(a.cv[q], yin[(int64_t)a.ri[q] * a.nrhs + k], s);
+      out[j * a.nrhs + k] = s;
+      if (MODE == 1) pq = a.p[j * a.nrhs + k] * s;
+    }
+    if (MODE == 1) {
+      double t = block_sum(pq, red);
+      if (threadIdx.x == 0) part_ptr(a, kPartPq)[(int64_t)blockIdx.x * a.nrhs + k] = t;
+    }
+  }
+  if (MODE == 1 && arrive_last(a.cnt + kPartPq * a.nsys + C.sys, S.ncta)) {
+    if (threadIdx.x < 32)
+      for (int k = 0; k < a.nrhs; ++k) {
+        LaneState &L = a.lane[C.sys * a.nrhs + k];
+        if (L.status != CIMMINO_RUNNING) continue;
+        double pq = reduce_partials(part_ptr(a, kPartPq), S, a.nrhs, k);
+        if (threadIdx.x == 0) {
+          L.pq = pq;
+          if (!(pq > 0.0) || !isfinite(pq)) {
+            L.status = CIMMINO_EBREAKDOWN;
+            L.iters = L.t;
+            L.alpha = 0.0;
+          } else {
+            L.alpha = L.rho[L.t & 1] / pq;
+          }
+        }
+      }
+  }
+}
+
+// r = p = xi, x = 0, rho_0 = r^T r
+__global__ void __launch_bounds__(kThreads) k_cg_init(IterArgs a) {
+  __shared__ double red[32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  for (int k = 0; k < a.nrhs; ++k) {
+    double rr = 0.0;
+    if (act) {
+      const int64_t o = j * a.nrhs + k;
+      const double v = a.psi[o];
+      a.r[o] = v;
+      a.p[o] = v;
+      a.x[o] = 0.0;
+      rr = v * v;
+    }
+    double t = block_sum(rr, red);
+    if (threadIdx.x == 0) part_ptr(a, kPartRr)[(int64_t)blockIdx.x * a.nrhs + k] = t;
+  }
+  if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
+    if (threadIdx.x < 32)
+      for (int k = 0; k < a.nrhs; ++k) {
+        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k);
+        if (threadIdx.x == 0) {
+          LaneState &L = a.lane[C.sys * a.nrhs + k];
+          L.rho[0] = rr;
+          L.rho[1] = rr;
+        }
+      }
+  }
+}
+
+// x += alpha p, r -= alpha psi, rho_{t+1} = r^T r, beta
+__global__ void __launch_bounds__(kThreads) k_update_xr(IterArgs a) {
+  __shared__ double red[32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  for (int k = 0; k < a.nrhs; ++k) {
+    const LaneState &L = a.lane[C.sys * a.nrhs + k];
+    if (L.status != CIMMINO_RUNNING) continue;
+    const double alpha = L.alpha;
+    double rr = 0.0;
+    if (act) {
+      const int64_t o = j * a.nrhs + k;
+      a.x[o] = fma(alpha, a.p[o], a.x[o]);
+      const double rn = fma(-alpha, a.psi[o], a.r[o]);
+      a.r[o] = rn;
+      rr = rn * rn;
+    }
+    double t = block_sum(rr, red);
+    if (threadIdx.x == 0) part_ptr(a, kPartRr)[(int64_t)blockIdx.x * a.nrhs + k] = t;
+  }
+  if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
+    if (threadIdx.x < 32)
+      for (int k = 0; k < a.nrhs; ++k) {
+        LaneState &L = a.lane[C.sys * a.nrhs + k];
+        if (L.status != CIMMINO_RUNNING) continue;
+        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k);
+        if (threadIdx.x == 0) {
+          const int par = L.t & 1;
+          L.rho[par ^ 1] = rr;
+          L.beta = rr / L.rho[par];
+        }
+      }
+  }
+}
+
+// p = r + beta p, then t += 1
+__global__ void __launch_bounds__(kThreads) k_update_p(IterArgs a) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  for (int k = 0; k < a.nrhs; ++k) {
+    const LaneState &L = a.lane[C.sys * a.nrhs + k];
+    if (L.status != CIMMINO_RUNNING) continue;
+    if (threadIdx.x < C.rows) {
+      const int64_t o = j * a.nrhs + k;
+      a.p[o] = fma(L.beta, a.p[o], a.r[o]);
+    }
+  }
+  // one CTA per system advances the iteration counters of its running lanes
+  if (blockIdx.x == (unsigned)S.cta0) {
+    __syncthreads();
+    if (threadIdx.x < (unsigned)a.nrhs) {
+      LaneState &L = a.lane[C.sys * a.nrhs + threadIdx.x];
+      if (L.status == CIMMINO_RUNNING) L.t += 1;
+    }
+  }
+}
+
+// final statistics: per CTA partial max |D(f_s - A_s x)|, sum |x|, max |f|, max row abs-sum
+__global__ void __launch_bounds__(kThreads)
+    k_final_stats(IterArgs a, const double *__restrict__ Fin, const double *__restrict__ rowabs,
+                  double *__restrict__ out) {
+  __shared__ double sred[3][kWarps];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const int64_t r = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < a.nrhs; ++k) {
+    double rmax = 0.0, x1 = 0.0, fmax_ = 0.0;
+    if (act) {
+      double sx = 0.0;
+      for (int64_t q = a.rp[r]; q < a.rp[r + 1]; ++q) sx = fma(a.va[q], a.x[(int64_t)a.ci[q] * a.nrhs + k], sx);
+      rmax = fabs(a.d[r] * (a.fs[r * a.nrhs + k] - sx));
+      x1 = fabs(a.x[r * a.nrhs + k]);
+      fmax_ = fabs(Fin[(int64_t)k * a.N + r]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+      fmax_ = fmax(fmax_, __shfl_xor_sync(0xffffffffu, fmax_, o));
+    }
+    if (lane == 0) {
+      sred[0][warp] = rmax;
+      sred[1][warp] = x1;
+      sred[2][warp] = fmax_;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m0 = 0, s1 = 0, m2 = 0;
+      for (int q = 0; q < kWarps; ++q) {
+        m0 = fmax(m0, sred[0][q]);
+        s1 += sred[1][q];
+        m2 = fmax(m2, sred[2][q]);
+      }
+      double *o = out + ((int64_t)blockIdx.x * a.nrhs + k) * 4;
+      o[0] = m0;
+      o[1] = s1;
+      o[2] = m2;
+      double am = 0.0;
+      for (int q = 0; q < C.rows; ++q) am = fmax(am, rowabs[C.row0 + q]);
+      o[3] = am;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_row_abs(const int64_t *__restrict__ rp, const double *__restrict__ va,
+                          const double *__restrict__ d, int64_t N, double *__restrict__ rowabs) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double s = 0.0;
+  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) s += fabs(va[q]);
+  rowabs[r] = s * d[r];
+}
+
+}  // namespace
+
+// ============================================================================ launchers
+int proj_smem_bytes(int max_mp) {
+  return (int)(sizeof(double) * (4 * (size_t)max_mp + T + 2 * kWarps * T + 32));
+}
+
+void set_proj_smem_attr(int bytes) {
+  cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_rhs_scale(const IterArgs &a, const double *Fin, const int32_t *perm, cudaStream_t s) {
+  k_rhs_scale<<<a.ncta, kThreads, 0, s>>>(a, Fin, perm);
+}
+
+void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStream_t s) {
+  k_spmv_plain<<<a.ncta, kThreads, 0, s>>>(a, v, out);
+}
+
+void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
+  k_proj<<<a.nblk, kThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+}
+
+void launch_spmv_t(const IterArgs &a, const double *y, double *out, cudaStream_t s) {
+  k_spmv_t<0><<<a.ncta, kThreads, 0, s>>>(a, y, out);
+}
+
+void launch_cg_init(const IterArgs &a, cudaStream_t s) {
+  k_cg_init<<<a.ncta, kThreads, 0, s>>>(a);
+}
+
+void launch_iteration(const IterArgs &a, cudaStream_t s) {
+  k_spmv_res<<<a.ncta, kThreads, 0, s>>>(a);
+  k_proj<<<a.nblk, kThreads, a.proj_smem, s>>>(a, a.u, a.y, 1);
+  k_spmv_t<1><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
+  k_update_xr<<<a.ncta, kThreads, 0, s>>>(a);
+  k_update_p<<<a.ncta, kThreads, 0, s>>>(a);
+}
+
+void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,
+                        cudaStream_t s) {
+  k_final_stats<<<a.ncta, kThreads, 0, s>>>(a, Fin, rowabs, out);
+}
+
+void launch_row_abs(const int64_t *rp, const double *va, const double *d, int64_t N,
+                    double *rowabs, cudaStream_t s) {
+  k_row_abs<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rp, va, d, N, rowabs);
+}
+
+}  // namespace cimmino

@@ -1,0 +1,245 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated requirements of the method's implementation):
+  * pattern of C = A A^T: bit-exact; values of C: 1e-12 relative;
+  * FP64 factors L_i: 1e-12 relative (Frobenius) against the oracle's L_i;
+  * FP64 projections H v: 1e-12 relative (2-norm);
+  * solves: relative residual <= 1e-10 and the oracle's iteration count +-1;
+  * FP32+refinement: inner solves refined to ||G y - u|| <= 1e-13 ||u||, so H v
+    agrees to 1e-11 relative and the iteration count to +-1 as well.
+Sizes span several 64-row tiles with ragged tails and 1-row blocks.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+g = pytest.importorskip("paper_1710_07769_gb300")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def csr_from_dense(D):
+    n = D.shape[0]
+    rp = np.zeros(n + 1, np.int64)
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        cols.append(nz)
+        vals.append(D[i, nz])
+        rp[i + 1] = rp[i] + len(nz)
+    return inputs.CSR(n, rp, np.concatenate(cols).astype(np.int32), np.concatenate(vals))
+
+
+RAGGED = np.array([0, 1, 65, 200, 329, 330, 700], np.int64)  # m = 1, 64, 135, 129, 1, 370
+
+
+@pytest.fixture(scope="module")
+def sys_small():
+    A = inputs.random_dd(700, 5, 11)
+    rng = np.random.default_rng(5)
+    perm = rng.permutation(700).astype(np.int32)
+    xt = rng.uniform(-1, 1, 700)
+    return A, perm, inputs.matvec(A, xt)
+
+
+# ------------------------------------------------------------------ SpGEMM (Section 2.3)
+
+@pytest.mark.parametrize("which", ["random", "stencil2d", "stencil3d"])
+def test_aat_standalone_bitexact(which):
+    A = {"random": lambda: inputs.random_dd(3000, 8, 3),
+         "stencil2d": lambda: inputs.convdiff2d(40, 20.0),
+         "stencil3d": lambda: inputs.convdiff3d(12, 11, 10, (30, 20, 10))}[which]()
+    rp, ci, v = g.aat(A)
+    orp, oci, ov = oracle.aat_plain(A)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)      # pattern bit-exact
+    np.testing.assert_allclose(v, ov, rtol=1e-12, atol=0)
+    assert np.array_equal(v, ov)                                   # same sum order: bitwise
+
+
+def test_aat_dense_column_overflow_path():
+    """A column with 1500 entries gives rows with more than 1024 candidates (CTA path)."""
+    n = 2000
+    D = np.zeros((n, n))
+    D[np.arange(n), np.arange(n)] = 3.0
+    D[:1500, 7] += np.linspace(0.5, 1.5, 1500)
+    A = csr_from_dense(D)
+    rp, ci, v = g.aat(A)
+    orp, oci, ov = oracle.aat_plain(A)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    np.testing.assert_allclose(v, ov, rtol=1e-12)
+
+
+def test_setup_scaled_and_aat_match_oracle(sys_small):
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, keep_aat=True)
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    rp, ci, v, d = s.scaled_csr(A.nnz)
+    orp, oci, ov, od = o.scaled()
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    np.testing.assert_allclose(v, ov, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(d, od, rtol=1e-15)
+    crp, cci, cv = s.aat()
+    ocrp, occi, ocv = o.aat()
+    assert np.array_equal(crp, ocrp) and np.array_equal(cci, occi)
+    np.testing.assert_allclose(cv, ocv, rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------ Cholesky of G_i
+
+@pytest.mark.parametrize("layout", ["dense", "skyline"])
+def test_fp64_factors_match_oracle(sys_small, layout):
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, layout=layout)
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    for b in range(len(RAGGED) - 1):
+        Lg, is64 = s.factor(b)
+        assert is64
+        assert rel(Lg, o.factor(b)) <= 1e-12, b
+
+
+def test_fp64_factors_stencil_skyline_envelope():
+    """Contiguous blocks of a 3D stencil: G_i is banded, the skyline layout stores only
+    the envelope, and the factor still equals the oracle's dense Cholesky factor."""
+    A = inputs.convdiff3d(16, 16, 6, (30, 20, 10))
+    bp = inputs.contiguous_blocks(A.n, 700)
+    s = g.Solver(A, bp, layout="skyline")
+    o = oracle.Oracle(A, bp)
+    for b in [0, len(bp) - 2]:
+        Lg, _ = s.factor(b)
+        assert rel(Lg, o.factor(b)) <= 1e-12
+
+
+def test_fp32_factors_close_to_oracle(sys_small):
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, precision="fp32_refine")
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    for b in range(len(RAGGED) - 1):
+        Lg, is64 = s.factor(b)
+        tol = 1e-12 if is64 else 2e-5
+        assert rel(Lg, o.factor(b)) <= tol, b
+
+
+# ------------------------------------------------------------------ projections (Eq. 1.5)
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-11)])
+def test_projection_matches_oracle(sys_small, precision, tol):
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, precision=precision)
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    v = np.random.default_rng(1).standard_normal(A.n)
+    assert rel(s.project(v), o.project(v)) <= tol
+    assert rel(s.project_rhs(f), o.project_rhs(f)) <= tol
+
+
+# ------------------------------------------------------------------ Algorithm 2
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("layout", ["dense", "skyline"])
+def test_config1_solve_matches_oracle(precision, layout):
+    w = inputs.workload(1)
+    o = oracle.Oracle(w.A, w.block_ptr)
+    xo, ito, rro, go, sto = o.solve(w.F[0])
+    s = g.Solver(w.A, w.block_ptr, precision=precision, layout=layout)
+    x, st, code = s.solve(w.F[0], tol=1e-10)
+    assert code == 0 and st[0]["status"] == 0
+    assert abs(st[0]["iters"] - ito) <= 1, (st[0]["iters"], ito)
+    assert st[0]["rel_res"] <= 1e-10
+    r = np.linalg.norm(w.F[0] - inputs.matvec(w.A, x)) / np.linalg.norm(w.F[0])
+    assert r <= 1.01e-10
+    # both solutions are within kappa * 1e-10 of the truth; kappa(A) of config 1 is < 50
+    assert rel(x, xo) <= 1e-8
+
+
+def test_solve_ragged_permuted_matches_oracle(sys_small):
+    A, perm, f = sys_small
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    xo, ito, *_ = o.solve(f)
+    for precision in ("fp64", "fp32_refine"):
+        s = g.Solver(A, RAGGED, perm=perm, precision=precision)
+        x, st, code = s.solve(f)
+        assert code == 0 and abs(st[0]["iters"] - ito) <= 1
+        assert rel(x, xo) <= 1e-8
+
+
+def test_K1_one_iteration():
+    A = inputs.convdiff2d(50, 20.0)
+    f = inputs.matvec(A, inputs.uniform_x(A.n, 1, 3)[0])
+    s = g.Solver(A, np.array([0, A.n]))
+    x, st, code = s.solve(f)
+    assert code == 0 and st[0]["iters"] == 1
+
+
+def test_zero_rhs_gives_zero():
+    w = inputs.workload(1)
+    s = g.Solver(w.A, w.block_ptr)
+    x, st, code = s.solve(np.zeros(w.A.n))
+    assert code == 0 and st[0]["iters"] == 0 and not np.any(x)
+
+
+def test_multi_rhs_matches_single(sys_small):
+    A, perm, f = sys_small
+    rng = np.random.default_rng(9)
+    F = np.stack([inputs.matvec(A, rng.uniform(-1, 1, A.n)) for _ in range(3)])
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    s = g.Solver(A, RAGGED, perm=perm, precision="fp32_refine")
+    X, st, code = s.solve(F)
+    assert code == 0
+    for k in range(3):
+        xo, ito, *_ = o.solve(F[k])
+        assert abs(st[k]["iters"] - ito) <= 1
+        assert rel(X[k], xo) <= 1e-8
+
+
+def test_deterministic_bitwise():
+    w = inputs.workload(1)
+    s = g.Solver(w.A, w.block_ptr, precision="fp32_refine")
+    x1, s1, _ = s.solve(w.F[0])
+    x2, s2, _ = s.solve(w.F[0])
+    assert np.array_equal(x1, x2) and s1[0]["iters"] == s2[0]["iters"]
+
+
+def test_graph_and_eager_agree():
+    w = inputs.workload(1)
+    x1, s1, _ = g.Solver(w.A, w.block_ptr, use_graph=True, check_every=5).solve(w.F[0])
+    x2, s2, _ = g.Solver(w.A, w.block_ptr, use_graph=False, check_every=1).solve(w.F[0])
+    assert s1[0]["iters"] == s2[0]["iters"]
+    assert np.array_equal(x1, x2)
+
+
+def test_batch_matches_individual_oracles():
+    systems = inputs.batch_workload(nsys=4, seed=4, max_nz=6)
+    bs = g.BatchSolver([w.A for w in systems], [w.block_ptr for w in systems])
+    X, st, code = bs.solve([w.F[0] for w in systems])
+    assert code == 0
+    for w, x, s in zip(systems, X, st):
+        xo, ito, *_ = oracle.Oracle(w.A, w.block_ptr).solve(w.F[0])
+        assert abs(s["iters"] - ito) <= 1
+        assert rel(x, xo) <= 1e-8
+
+
+# ------------------------------------------------------------------ errors
+
+def test_errors_reported():
+    w = inputs.workload(1)
+    bad = inputs.CSR(w.A.n, w.A.row_ptr.copy(), w.A.col_idx.copy(), w.A.val)
+    bad.col_idx[5] = w.A.n + 3
+    with pytest.raises(g.CimminoError) as e:
+        g.Solver(bad, w.block_ptr)
+    assert e.value.code == g.EINVAL
+    # rank-deficient block: two parallel rows in block 0
+    D = np.eye(8) * 2.0
+    D[1] = D[0] * 3.0
+    with pytest.raises(g.CimminoError) as e:
+        g.Solver(csr_from_dense(D), np.array([0, 4, 8]))
+    assert e.value.code == g.ESINGULAR
+    s = g.Solver(w.A, w.block_ptr, max_iter=3)
+    x, st, code = s.solve(w.F[0])
+    assert code == g.ENOCONV and st[0]["iters"] == 3
