@@ -197,6 +197,31 @@ int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t o
 int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
                 int32_t *col_idx, double *val);
 
+/* C = A A^T into caller-owned DEVICE buffers without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate, such
+ * as code running while a stream is captured into a CUDA graph (cudaMalloc is not
+ * allowed there), embedders whose device memory belongs to another allocator or a
+ * fixed budget, and latency-critical paths that must not block on the allocator.
+ * It computes the same result as cimmino_aat() (same kernels, bitwise equal).
+ *   A         device CSR (A->on_device must be 1), n <= 262,144 and nnz <= 2,097,152,
+ *             else CIMMINO_EUNSUPPORTED.
+ *   stream    cudaStream_t for the work (NULL: legacy default stream).
+ *   nnz       host out: nnz(C).
+ *   row_ptr   device out, n + 1 entries (always written).
+ *   col_idx, val  device out with room for `capacity` entries, or both NULL to only
+ *             count (first call of a two-call pattern); EINVAL if capacity < nnz(C).
+ * Memory: the working arrays (transpose of A, counts, scan partials) live in one
+ * static device array of about 33 MB that every GPU loading this library keeps until
+ * the process exits.  No cudaMalloc / cudaFree or allocating library call is made.
+ * The first call on each device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls share
+ * the array, so calls whose work overlaps on the GPU (other threads, other streams)
+ * race and must be serialised by the caller; each call clears what must start at
+ * zero.  The call synchronises `stream` before returning; the error message is
+ * available from cimmino_last_error(NULL). */
+int cimmino_aat_noalloc(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
+                        int32_t *col_idx, double *val, int64_t capacity);
+
 /* Benchmark hook: after a cimmino_solve() on a single-system context, launch each
  * per-iteration kernel `reps` times back to back on the context's stream, on the
  * vectors of the last solve, and write the average device time per launch in

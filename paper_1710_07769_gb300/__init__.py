@@ -33,8 +33,8 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV", -
 EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimmino_solve",
            "cimmino_solve_batch", "cimmino_free", "cimmino_last_error", "cimmino_get_aat_nnz",
            "cimmino_get_aat", "cimmino_get_scaled", "cimmino_block_rows", "cimmino_get_factor",
-           "cimmino_project", "cimmino_project_rhs", "cimmino_aat", "cimmino_time_kernels",
-           "cimmino_version"]
+           "cimmino_project", "cimmino_project_rhs", "cimmino_aat", "cimmino_aat_noalloc",
+           "cimmino_time_kernels", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_project_rhs.argtypes = [vp, vp, vp, i32]
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
+        L.cimmino_aat_noalloc.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp, i64]
         L.cimmino_version.restype = C.c_char_p
         for name in EXPORTS:
             if name not in ("cimmino_free", "cimmino_last_error", "cimmino_version",

@@ -706,6 +706,8 @@ int set_error(cimmino_ctx *c, const Error &e) {
 
 }  // namespace
 
+void cimmino::record_last_error(const std::string &msg) { g_last_error = msg; }
+
 // ====================================================================== C ABI
 extern "C" {
 

@@ -92,6 +92,9 @@ struct Error {
 
 inline void fail(int code, const std::string &msg) { throw Error{code, msg}; }
 
+// Sets the per-thread message returned by cimmino_last_error(NULL) (defined in api.cu).
+void record_last_error(const std::string &msg);
+
 // --------------------------------------------------------------------------
 // device helpers
 __device__ __forceinline__ double warp_sum(double v) {
