@@ -287,8 +287,21 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--layout", default="skyline", choices=["skyline", "dense"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--profile", default=None, choices=["fp64", "fp32_refine"],
+                    help="profiling target: one setup + 4 CG iterations, nothing timed")
     args = ap.parse_args()
     ws, rank, local = dist_env()
+    if args.profile:
+        import inputs
+        import paper_1710_07769_gb300 as g
+        w = inputs.workload(args.config)
+        s = g.Solver(w.A, w.block_ptr, perm=w.perm, precision=args.profile, layout=args.layout,
+                     max_iter=4, check_every=1)
+        x, st, code = s.solve(w.F[0], tol=TOL)
+        print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
+                          "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
+        s.close()
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0
