@@ -107,16 +107,22 @@ struct cimmino_ctx {
   std::vector<TileRow> htrow;
   std::vector<CtaDesc> hcta;
   int32_t max_mp = 0;
+  int32_t proj_slots = 0, proj_slot_bytes = 0, proj_smem = 0, proj_wbytes = 8;
   // matrices
   DBuf<int64_t> rp, cp, brp, crp;
   DBuf<int32_t> ci, ri, bci, cci, perm;
-  DBuf<double> va, cv, d, bcv, ccv, rowabs;
+  DBuf<double> va, cv, d, bcv, ccv, rowabs, sval;
+  DBuf<int64_t> soff;
+  DBuf<int16_t> scol;
   DBuf<BlockDesc> blk;
   DBuf<TileRow> trow;
   DBuf<SysDesc> sys;
   DBuf<CtaDesc> cta;
-  DBuf<float> fac32, dinv32;
-  DBuf<double> fac64, dinv64;
+  DBuf<float> fac32, dinv32, facT32, dinvT32;
+  DBuf<double> fac64, dinv64, facT64, dinvT64;
+  DBuf<TileRow> trowT;
+  std::vector<TileRow> htrowT;
+  int64_t pass_bytes = 0;  // factor bytes one forward + backward solve pass streams
   int64_t nnzc = 0, nnz_bd = 0, factor_bytes = 0;
   int32_t fallbacks = 0;
   int64_t setup_launches = 0;  // kernels launched by the setup
@@ -126,7 +132,7 @@ struct cimmino_ctx {
   int32_t nrhs = 0;
   DBuf<LaneState> lane;
   DBuf<double> fs, x, p, r, psi, u, y, part, Fin, stats4;
-  DBuf<int32_t> cnt, refine_max;
+  DBuf<int32_t> cnt, refine_max, err_flag;
   DBuf<int64_t> refine_total;
   cudaGraphExec_t graph = nullptr;
   int32_t graph_nrhs = 0, graph_iters = 0;
@@ -298,7 +304,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   }
   c->perm.alloc(N);
   h2d(c->perm.p, hperm.data(), N, s);
-  int32_t ntrow = 0;
+  int32_t ntrow = 0, nslice = 0;
   c->max_mp = 0;
   for (int32_t q = 0; q < nsys; ++q) {
     for (int32_t b = 0; b < K[q]; ++b) {
@@ -309,6 +315,8 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
       B.trow0 = ntrow;
       B.sys = q;
       B.prec64 = c->opts.precision == CIMMINO_FP64;
+      B.slice0 = nslice;
+      nslice += (B.m + 31) / 32;
       ntrow += B.nt;
       c->max_mp = std::max(c->max_mp, B.nt * kTile);
       c->hblk.push_back(B);
@@ -317,8 +325,8 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   const int32_t nblk = (int32_t)c->hblk.size();
   c->blk.alloc(nblk);
   h2d(c->blk.p, c->hblk.data(), nblk, s);
-  const int psm = proj_smem_bytes(c->max_mp);
-  if (psm > 227 * 1024) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
+  if (proj_smem_bytes(c->max_mp, 2, kTile * kTile * 8, 8) > kProjSmemMax)
+    fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
 
   // ---- scale and permute rows (Sections 2.1, 2.2)
   DBuf<int64_t> len, tmp;
@@ -397,6 +405,21 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   bd_fill(c->crp.p, c->cci.p, c->ccv.p, c->blk.p, rowblk.p, N, c->brp.p, c->bci.p, c->bcv.p,
           rowmin.p, s);
   c->setup_launches += 2;  // fill, tile envelope
+  // sliced-ELL copy of the Gram blocks for the refinement residual
+  {
+    DBuf<int64_t> scnt;
+    scnt.alloc(nslice);
+    c->soff.alloc(nslice + 1);
+    sell_width(c->blk.p, nblk, c->brp.p, scnt.p, s);
+    launch_scan_counts(scnt.p, c->soff.p, nslice, tmp.p, tl, s);
+    int64_t sn = 0;
+    d2h(&sn, c->soff.p + nslice, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    c->scol.alloc(sn);
+    c->sval.alloc(sn);
+    sell_fill(c->blk.p, nblk, c->brp.p, c->bci.p, c->bcv.p, c->soff.p, c->scol.p, c->sval.p, s);
+    c->setup_launches += 5;  // widths, 3-pass scan, fill
+  }
 
   // ---- tile envelope and factor layout
   DBuf<int32_t> dj0;
@@ -498,6 +521,43 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                       " is not positive definite in FP64 (A_i is rank deficient)");
     }
   }
+  // ---- transposed copy of every factor, read row-wise by the backward solves
+  {
+    c->htrowT.resize(ntrow);
+    int64_t oT32 = 0, oT64 = 0, ntiles = 0;
+    for (const auto &B : c->hblk) {
+      for (int32_t I = 0; I < B.nt; ++I) {
+        int32_t j1 = I;
+        for (int32_t J = I + 1; J < B.nt; ++J)
+          if (c->htrow[B.trow0 + J].j0 <= I) j1 = J;
+        TileRow &U = c->htrowT[B.trow0 + I];
+        U.j0 = j1;
+        int64_t &o = B.prec64 ? oT64 : oT32;
+        U.off = o;
+        o += (int64_t)(j1 - I) * TT;
+        // streamed per solve pass: N row, NT row, inv(L_II), inv(L_II)^T
+        ntiles += (I - c->htrow[B.trow0 + I].j0) + (j1 - I) + 2;
+      }
+    }
+    c->pass_bytes = 0;
+    for (const auto &B : c->hblk) {
+      int64_t t = 0;
+      for (int32_t I = 0; I < B.nt; ++I)
+        t += (I - c->htrow[B.trow0 + I].j0) + (c->htrowT[B.trow0 + I].j0 - I) + 2;
+      c->pass_bytes += t * TT * (B.prec64 ? 8 : 4);
+    }
+    (void)ntiles;
+    c->trowT.alloc(ntrow);
+    h2d(c->trowT.p, c->htrowT.data(), ntrow, s);
+    if (oT32) c->facT32.alloc(oT32);
+    if (oT64) c->facT64.alloc(oT64);
+    if (c->dinv32.p) c->dinvT32.alloc(c->dinv32.n);
+    if (c->dinv64.p) c->dinvT64.alloc(c->dinv64.n);
+    FactorPtrs f{c->fac32.p, c->dinv32.p, c->facT32.p, c->dinvT32.p,
+                 c->fac64.p, c->dinv64.p, c->facT64.p, c->dinvT64.p};
+    launch_transpose_factor(c->blk.p, nblk, c->trow.p, c->trowT.p, f, s);
+    c->setup_launches += 1;
+  }
   c->t_factor_ms = tfac.stop_ms(s);
   if (!c->opts.keep_aat) {
     c->crp.release();
@@ -525,7 +585,19 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   c->rowabs.alloc(N);
   launch_row_abs(c->rp.p, c->va.p, c->d.p, N, c->rowabs.p, s);
   c->setup_launches += 1;
-  set_proj_smem_attr(psm);
+  // projection ring: as many factor-tile slots as fit beside the block vectors
+  bool any64 = false;
+  for (const auto &B : c->hblk) any64 |= B.prec64 != 0;
+  c->proj_slot_bytes = kTile * kTile * (any64 ? 8 : 4);
+  c->proj_wbytes = any64 ? 8 : 4;
+  c->proj_slots =
+      std::min(kMaxProjSlots, (kProjSmemMax - proj_smem_bytes(c->max_mp, 0, 0, c->proj_wbytes)) /
+                                  c->proj_slot_bytes);
+  if (c->proj_slots < 2) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
+  c->proj_smem = proj_smem_bytes(c->max_mp, c->proj_slots, c->proj_slot_bytes, c->proj_wbytes);
+  set_proj_smem_attr(c->proj_smem);
+  c->err_flag.alloc(1);
+  CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
 }
@@ -561,12 +633,20 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.brp = c->brp.p;
   a.bci = c->bci.p;
   a.bcv = c->bcv.p;
+  a.soff = c->soff.p;
+  a.scol = c->scol.p;
+  a.sval = c->sval.p;
   a.blk = c->blk.p;
   a.trow = c->trow.p;
+  a.trowT = c->trowT.p;
   a.fac32 = c->fac32.p;
   a.dinv32 = c->dinv32.p;
+  a.facT32 = c->facT32.p;
+  a.dinvT32 = c->dinvT32.p;
   a.fac64 = c->fac64.p;
   a.dinv64 = c->dinv64.p;
+  a.facT64 = c->facT64.p;
+  a.dinvT64 = c->dinvT64.p;
   a.sys = c->sys.p;
   a.cta = c->cta.p;
   a.lane = c->lane.p;
@@ -590,7 +670,11 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.refine_tol = c->opts.refine_tol;
   a.max_iter = c->opts.max_iter;
   a.max_mp = c->max_mp;
-  a.proj_smem = proj_smem_bytes(c->max_mp);
+  a.proj_smem = c->proj_smem;
+  a.proj_slots = c->proj_slots;
+  a.proj_slot_bytes = c->proj_slot_bytes;
+  a.proj_wbytes = c->proj_wbytes;
+  a.err = c->err_flag.p;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -655,8 +739,11 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   int32_t rmax = 0;
   d2h(&rtot, c->refine_total.p, 1, s);
   d2h(&rmax, c->refine_max.p, 1, s);
+  int32_t herr = 0;
+  d2h(&herr, c->err_flag.p, 1, s);
   const double tms = tsolve.stop_ms(s);
   CUDA_TRY(cudaGetLastError());
+  if (herr) fail(CIMMINO_ETIMEOUT, "a bounded wait in the projection kernel ran out");
   int ret = CIMMINO_OK;
   for (int32_t q = 0; q < c->nsys; ++q) {
     const SysDesc &S = c->hsys[q];
@@ -687,6 +774,7 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.t_solve_ms = tms;
         o.nnz_aat = c->nnzc;
         o.factor_bytes = c->factor_bytes;
+        o.pass_bytes = c->pass_bytes;
         // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
         o.kernel_launches = c->setup_launches + 5 + 5 * launched + (nrhs > 1 ? 1 : 0);
       }
@@ -905,10 +993,22 @@ int cimmino_get_factor(cimmino_ctx *ctx, int32_t b, double *L, int32_t *is_fp64)
     CUDA_TRY(cudaStreamSynchronize(s));
     const int m = B.m;
     std::memset(L, 0, sizeof(double) * (size_t)m * m);
+    // stored: diagonal tiles L_II and N_IJ = inv(L_II) L_IJ; rebuild L_IJ = L_II N_IJ
+    std::vector<double> tmp(TT);
     for (int32_t I = 0; I < B.nt; ++I) {
       const TileRow &R = ctx->htrow[B.trow0 + I];
+      const double *dI = buf.data() + (R.off - first.off) + (int64_t)(I - R.j0) * TT;
       for (int32_t J = R.j0; J <= I; ++J) {
         const double *t = buf.data() + (R.off - first.off) + (int64_t)(J - R.j0) * TT;
+        if (J < I) {
+          for (int rr = 0; rr < kTile; ++rr)
+            for (int cc = 0; cc < kTile; ++cc) {
+              double acc = 0.0;
+              for (int kk = 0; kk <= rr; ++kk) acc += dI[rr * kTile + kk] * t[kk * kTile + cc];
+              tmp[rr * kTile + cc] = acc;
+            }
+          t = tmp.data();
+        }
         for (int rr = 0; rr < kTile; ++rr) {
           int gr = I * kTile + rr;
           if (gr >= m) break;

@@ -6,6 +6,9 @@
 //   3. L_IK = G_IK * inv(L_KK)^T for the stored tiles below the diagonal;
 //   4. G_IJ -= L_IK * L_JK^T for K < J <= I (only tiles inside the envelope exist,
 //      and the fill of a Cholesky factor never leaves the envelope of G).
+// Once row K is final (after step 2 of step K), its off-diagonal tiles are replaced by
+// N_KJ = inv(L_KK) L_KJ, i.e. the factor is stored as L = diag(L_II) (I + N): the
+// diagonal tiles keep L_II and dinv keeps inv(L_II).
 // Pivot monitoring: min_j of the pivots L_jj^2 (G_jj = 1 after the unit row
 // scaling) and a failure flag for a non-positive or non-finite pivot; a failed
 // pivot is replaced by 1 so that the block finishes without NaNs and can be
@@ -133,6 +136,30 @@ __global__ void __launch_bounds__(kThreads)
       gKK[e] = c <= r ? S[r * LDS + c] : W(0);
       dK[e] = c <= r ? Di[r * LDS + c] : W(0);
     }
+    // Row K is final now: store N_KJ = inv(L_KK) L_KJ in place of L_KJ (J < K), so that
+    // the solves see L = diag(L_II) (I + N) and their sequential chains need no
+    // diagonal solve.  At[k][r] = Di(r, k), Bt[k][c] = L_KJ(k, c).
+    for (int e = tid; e < T * T; e += kThreads) {
+      int k = e / T, r = e % T;
+      At[k * LD + r] = Di[r * LDS + k];
+    }
+    for (int J = TK.j0; J < K; ++J) {
+      W *gKJ = tile_ptr(fac, TK, J);
+      __syncthreads();  // At ready / previous use of Bt finished
+      for (int e = tid; e < T * T; e += kThreads) Bt[(e / T) * LD + (e % T)] = gKJ[e];
+      __syncthreads();
+      W acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = W(0);
+      mma_4x4(At, Bt, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gKJ[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+    }
+    __syncthreads();
     // Bt[k][c] = Di(c, k) for the TRSM below
     for (int e = tid; e < T * T; e += kThreads) {
       int k = e / T, c = e % T;
@@ -194,6 +221,49 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Transposed copy of a factor for the backward solves: upper tile row I holds
+// NT_IJ = N_JI^T for J = I+1..J1(I) (J1(I) = last tile row whose envelope reaches
+// column I; tiles with J0(J) > I are zero), and dinvT_I = inv(L_II)^T.
+template <typename W>
+__device__ void transpose_block(const BlockDesc &B, const TileRow *__restrict__ tr,
+                                const TileRow *__restrict__ trT, const W *__restrict__ fac,
+                                const W *__restrict__ dinv, W *__restrict__ facT,
+                                W *__restrict__ dinvT, W *sm) {
+  constexpr int LDS = T + 1;
+  auto tile_t = [&](const W *src, W *dst) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T; e += kThreads) sm[(e / T) * LDS + (e % T)] = src[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T; e += kThreads) dst[e] = sm[(e % T) * LDS + (e / T)];
+  };
+  for (int I = 0; I < B.nt; ++I) {
+    tile_t(dinv + B.dinv_off + (int64_t)I * T * T, dinvT + B.dinv_off + (int64_t)I * T * T);
+    const TileRow U = trT[I];
+    for (int J = I + 1; J <= U.j0; ++J) {
+      W *dst = facT + U.off + (int64_t)(J - I - 1) * T * T;
+      const TileRow R = tr[J];
+      if (R.j0 <= I) {
+        tile_t(fac + R.off + (int64_t)(I - R.j0) * T * T, dst);
+      } else {
+        for (int e = threadIdx.x; e < T * T; e += kThreads) dst[e] = W(0);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_transpose_factor(const BlockDesc *__restrict__ blk, const TileRow *__restrict__ trow,
+                       const TileRow *__restrict__ trowT, FactorPtrs f) {
+  __shared__ double sm[T * (T + 1)];
+  const BlockDesc B = blk[blockIdx.x];
+  if (B.prec64)
+    transpose_block<double>(B, trow + B.trow0, trowT + B.trow0, f.fac64, f.dinv64, f.facT64,
+                            f.dinvT64, sm);
+  else
+    transpose_block<float>(B, trow + B.trow0, trowT + B.trow0, f.fac32, f.dinv32, f.facT32,
+                           f.dinvT32, reinterpret_cast<float *>(sm));
+}
+
 template <typename W>
 int chol_smem() {
   return (int)(sizeof(W) * (2 * T * (T + Pad<W>::v) + 2 * T * (T + 1)));
@@ -218,6 +288,11 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
         blk, blist, trow, static_cast<float *>(fac), static_cast<float *>(dinv), pivmin,
         pivfail);
   }
+}
+
+void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
+                             const TileRow *trowT, const FactorPtrs &f, cudaStream_t s) {
+  if (nblk > 0) k_transpose_factor<<<(unsigned)nblk, kThreads, 0, s>>>(blk, trow, trowT, f);
 }
 
 }  // namespace cimmino

@@ -25,6 +25,8 @@ constexpr int kTile = 64;          // tile edge T of the factor layout
 constexpr int kMaxBlockRows = 4096;
 constexpr int kSpgemmWarpCap = 1024;   // candidates per row handled by one warp
 constexpr int kSpgemmCtaCap = 8192;    // candidates per row handled by one CTA
+constexpr int kMaxProjSlots = 16;      // factor-tile slots of the projection kernel's ring
+constexpr int kProjSmemMax = 231424;   // dynamic shared memory budget of one projection CTA
 
 struct BlockDesc {
   int64_t row0;      // first global (permuted, concatenated) row
@@ -34,7 +36,7 @@ struct BlockDesc {
   int32_t trow0;     // first entry of this block in the tile-row table
   int32_t sys;       // system index
   int32_t prec64;    // 1: factor stored in FP64 arrays, 0: FP32 arrays
-  int32_t pad;
+  int32_t slice0;    // first 32-row slice of this block in the sliced-ELL Gram copy
 };
 
 struct TileRow {
@@ -160,11 +162,31 @@ void bd_fill(const int64_t *crp, const int32_t *cci, const double *ccv, const Bl
              int32_t *rowmin, cudaStream_t s);
 void launch_tile_j0(const BlockDesc *blk, int32_t nblk, const int32_t *rowmin, int dense,
                     int32_t *j0, cudaStream_t s);
+void sell_width(const BlockDesc *blk, int32_t nblk, const int64_t *brp, int64_t *cnt,
+                cudaStream_t s);
+void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int32_t *bci,
+               const double *bcv, const int64_t *soff, int16_t *scol, double *sval,
+               cudaStream_t s);
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, const int64_t *brp, const int32_t *bci,
                          const double *bcv, void *fac, int prec64, cudaStream_t s);
 
+// factor arrays of both precisions (a context may hold FP64 fallback blocks beside
+// FP32 blocks): forward tiles (L_II, N_IJ), inv(L_II), and their transposed copies
+struct FactorPtrs {
+  const float *fac32;
+  const float *dinv32;
+  float *facT32;
+  float *dinvT32;
+  const double *fac64;
+  const double *dinv64;
+  double *facT64;
+  double *dinvT64;
+};
+
 // chol_kernels.cu
+void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
+                             const TileRow *trowT, const FactorPtrs &f, cudaStream_t s);
 void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                      const TileRow *trow, void *fac, void *dinv, int prec64, double *pivmin,
                      int32_t *pivfail, cudaStream_t s);
@@ -181,12 +203,20 @@ struct IterArgs {
   const int64_t *brp;
   const int32_t *bci;
   const double *bcv;
+  const int64_t *soff;   // sliced-ELL Gram blocks: slice offsets (entries)
+  const int16_t *scol;   //   block-local columns
+  const double *sval;    //   values
   const BlockDesc *blk;
   const TileRow *trow;
+  const TileRow *trowT;  // upper (transposed) tile rows: off, j0 field = J1(I)
   const float *fac32;
   const float *dinv32;
+  const float *facT32;
+  const float *dinvT32;
   const double *fac64;
   const double *dinv64;
+  const double *facT64;
+  const double *dinvT64;
   const SysDesc *sys;
   const CtaDesc *cta;
   LaneState *lane;
@@ -209,12 +239,16 @@ struct IterArgs {
   int32_t refine_steps;  // refinement steps allowed per inner solve of FP32 blocks
   int32_t max_mp;        // largest padded block (rows), sizes the projection smem
   int32_t proj_smem;     // dynamic shared memory bytes of the projection kernel
+  int32_t proj_slots;    // factor-tile slots in the projection kernel's ring
+  int32_t proj_slot_bytes;
+  int32_t proj_wbytes;   // bytes per entry of the projection's working vectors (4 or 8)
+  int32_t *err;          // device error word: bounded waits that ran out
   int32_t max_iter;
   double refine_tol;
   double tol;
 };
 
-int proj_smem_bytes(int max_mp);
+int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
 void set_proj_smem_attr(int bytes);
 void launch_rhs_scale(const IterArgs &a, const double *Fin, const int32_t *perm, cudaStream_t s);
 void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStream_t s);

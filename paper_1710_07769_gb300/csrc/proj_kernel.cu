@@ -1,0 +1,473 @@
+// Projection kernel: y_i = G_i^{-1} u_i for every block i (the inner solves of
+// Algorithm 2 step 5, with G_i = A_i A_i^T = L_i L_i^T), one CTA per block.
+//
+// The factor is stored as L = diag(L_II) (I + N) with N_IJ = inv(L_II) L_IJ, together
+// with inv(L_II) and transposed copies NT_IJ = N_JI^T, inv(L_II)^T.  Then
+//   L z = b    <=>  c_I = inv(L_II) b_I (all I),  z_I = c_I - sum_{J<I} N_IJ z_J
+//   L^T y = z  <=>  v_I = z_I - sum_{J>I} NT_IJ v_J,     y_I = inv(L_II)^T v_I (all I)
+// so all four phases are row products of 64 x 64 tiles with a vector, and the two
+// sequential chains (one step per tile row) need one reduction and one barrier per step.
+//
+// CTA = 8 consumer warps + 1 producer warp.
+//  * The producer streams the tiles (16 or 32 KB) with cp.async.bulk into a ring of
+//    shared-memory slots in the consumers' order.  full[s] completes when a copy lands,
+//    empty[s] when all 8 consumer warps have passed the slot.  Every wait is bounded; a
+//    wait that runs out sets the error flag and the kernel finishes without waiting again.
+//  * inv(L_II) and its transpose (independent tile rows): one warp computes a tile, a
+//    lane per two rows, no reduction.  Every consumer warp waits for and releases every
+//    slot in order, so a warp never waits on a slot more than one use ahead (which would
+//    make the mbarrier phase parity ambiguous).
+//  * Chain steps: thread (rg, cg) owns rows 4rg..4rg+3 and four columns of each tile
+//    (4 x 4 register block: 16 FMAs per tile from 4 or 8 16-byte loads of the tile and
+//    1 or 2 of the vector); a quarter-warp's 16-byte loads cover 8 distinct bank groups.
+//    The 16 column groups of a row meet in a 5-shuffle butterfly.
+//  * FP32 blocks are refined in FP64 against the exact Gram block (sliced-ELL copy):
+//    res = u - G_i y, y += L^{-T} L^{-1} res, until ||res|| <= refine_tol ||u||.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cimmino {
+
+namespace {
+
+constexpr int T = kTile;
+constexpr int kConsumers = 256;
+constexpr int kProjThreads = kConsumers + 32;
+constexpr uint32_t kWaitSpins = 1u << 30;
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits give up after ~2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: try_wait suspends the thread in hardware until the phase completes (or
+// its own time slice ends), so no sleep is added; give up after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitSpins; ++i) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// consumer-only barrier (8 warps) and whole-CTA barrier (consumers + producer)
+__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void allsync() { asm volatile("bar.sync 2, 288;" ::: "memory"); }
+
+struct Ring {
+  unsigned char *base;
+  uint64_t *full;
+  uint64_t *empty;
+  uint32_t slots;
+  uint32_t slot_bytes;
+  int *abort;
+};
+
+// consumer side: wait for tile t, return its slot
+__device__ __forceinline__ const void *slot_acquire(const Ring &R, uint32_t t, int32_t *err) {
+  const uint32_t s = t % R.slots;
+  if (!*(volatile int *)R.abort) {
+    if (!mbar_wait(&R.full[s], (t / R.slots) & 1u)) {
+      *(volatile int *)R.abort = 1;
+      atomicOr(err, 1);
+    }
+  }
+  return R.base + (size_t)s * R.slot_bytes;
+}
+__device__ __forceinline__ void slot_release(const Ring &R, uint32_t t) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&R.empty[t % R.slots]);
+}
+
+
+// 16 FMAs: row r of a tile times 64 entries of z, chunks of quarter q in rotated order
+// 4 x 4 register block of a row product: a[i] += sum over the thread's 4 columns of
+// L(4rg+i, c) v(c).  FP32: columns 4cg..4cg+3.  FP64: columns 2cg, 2cg+1, 32+2cg, 33+2cg.
+__device__ __forceinline__ void tile_rows(const float *L, const float *v, int rg, int cg,
+                                          float (&a)[4]) {
+  const float4 x = *reinterpret_cast<const float4 *>(v + 4 * cg);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 l = *reinterpret_cast<const float4 *>(L + (4 * rg + i) * T + 4 * cg);
+    a[i] = fma(l.x, x.x, a[i]);
+    a[i] = fma(l.y, x.y, a[i]);
+    a[i] = fma(l.z, x.z, a[i]);
+    a[i] = fma(l.w, x.w, a[i]);
+  }
+}
+__device__ __forceinline__ void tile_rows(const double *L, const double *v, int rg, int cg,
+                                          double (&a)[4]) {
+  const double2 x0 = *reinterpret_cast<const double2 *>(v + 2 * cg);
+  const double2 x1 = *reinterpret_cast<const double2 *>(v + 32 + 2 * cg);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double *Lr = L + (4 * rg + i) * T;
+    const double2 l0 = *reinterpret_cast<const double2 *>(Lr + 2 * cg);
+    const double2 l1 = *reinterpret_cast<const double2 *>(Lr + 32 + 2 * cg);
+    a[i] = fma(l0.x, x0.x, a[i]);
+    a[i] = fma(l0.y, x0.y, a[i]);
+    a[i] = fma(l1.x, x1.x, a[i]);
+    a[i] = fma(l1.y, x1.y, a[i]);
+  }
+}
+
+// Whole tile times v by one warp: lane l owns rows l and l+32 and walks the 16-byte
+// chunks of its rows in the order (k + l) mod (chunks per row), so the 8 lanes of a
+// quarter-warp always touch 8 distinct bank groups; no reduction is needed.
+__device__ __forceinline__ void tile_rows_warp(const double *D, const double *v, double *o,
+                                               int lane) {
+  const double2 *R0 = reinterpret_cast<const double2 *>(D + lane * T);
+  const double2 *R1 = reinterpret_cast<const double2 *>(D + (lane + 32) * T);
+  const double2 *V = reinterpret_cast<const double2 *>(v);
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll 8
+  for (int k = 0; k < T / 2; ++k) {
+    const int ch = (k + lane) & (T / 2 - 1);
+    const double2 x = V[ch], p = R0[ch], q = R1[ch];
+    a0 = fma(p.x, x.x, a0);
+    a1 = fma(p.y, x.y, a1);
+    b0 = fma(q.x, x.x, b0);
+    b1 = fma(q.y, x.y, b1);
+  }
+  o[lane] = a0 + a1;
+  o[lane + 32] = b0 + b1;
+}
+__device__ __forceinline__ void tile_rows_warp(const float *D, const float *v, float *o, int lane) {
+  const float4 *R0 = reinterpret_cast<const float4 *>(D + lane * T);
+  const float4 *R1 = reinterpret_cast<const float4 *>(D + (lane + 32) * T);
+  const float4 *V = reinterpret_cast<const float4 *>(v);
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < T / 4; ++k) {
+    const int ch = (k + lane) & (T / 4 - 1);
+    const float4 x = V[ch], p = R0[ch], q = R1[ch];
+    a0 = fma(p.x, x.x, a0);
+    a1 = fma(p.y, x.y, a1);
+    a0 = fma(p.z, x.z, a0);
+    a1 = fma(p.w, x.w, a1);
+    b0 = fma(q.x, x.x, b0);
+    b1 = fma(q.y, x.y, b1);
+    b0 = fma(q.z, x.z, b0);
+    b1 = fma(q.w, x.w, b1);
+  }
+  o[lane] = a0 + a1;
+  o[lane + 32] = b0 + b1;
+}
+
+// Sum of a[0..3] over the 16 column groups of a half-warp (5 shuffles, fixed order).
+// Returns the sum of row 4rg + row, where row = 2 * lane bit 3 + lane bit 2; all four
+// lanes that share those bits hold it.
+template <typename W>
+__device__ __forceinline__ W reduce_rows(const W (&a)[4], int lane, int &row) {
+  const bool hi = (lane & 8) != 0, h2 = (lane & 4) != 0;
+  const W s0 = __shfl_xor_sync(0xffffffffu, hi ? a[0] : a[2], 8);
+  const W s1 = __shfl_xor_sync(0xffffffffu, hi ? a[1] : a[3], 8);
+  const W b0 = (hi ? a[2] : a[0]) + s0;
+  const W b1 = (hi ? a[3] : a[1]) + s1;
+  const W s2 = __shfl_xor_sync(0xffffffffu, h2 ? b0 : b1, 4);
+  W c = (h2 ? b1 : b0) + s2;
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  row = (hi ? 2 : 0) + (h2 ? 1 : 0);
+  return c;
+}
+
+// Deterministic sum over the 256 consumer threads (fixed order).
+__device__ __forceinline__ double csum(double v, double *red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  csync();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) s += red[w];
+  csync();
+  return s;
+}
+
+// One forward + backward solve: right-hand side in w (overwritten), result in out.
+template <typename W>
+__device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
+                              const TileRow *__restrict__ trT, int nt, W *w, W *out, uint32_t &t,
+                              int32_t *err) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int rg = tid >> 4, cg = tid & 15;
+  const bool writer = (lane & 3) == 0;
+  int row;
+  const int warp = tid >> 5;
+  // F0: out_I = inv(L_II) w_I (independent tile rows, one warp per tile); every warp still
+  // waits for and releases every tile in order, which keeps the slots' phases unambiguous
+  for (int I = 0; I < nt; ++I) {
+    const W *D = static_cast<const W *>(slot_acquire(R, t, err));
+    if ((I & 7) == warp) tile_rows_warp(D, w + I * T, out + I * T, lane);
+    slot_release(R, t);
+    ++t;
+  }
+  csync();
+  // F1: w_I = out_I - sum_{J<I} N_IJ w_J (sequential over I)
+  for (int I = 0; I < nt; ++I) {
+    W a[4] = {W(0), W(0), W(0), W(0)};
+    for (int J = tr[I].j0; J < I; ++J) {
+      tile_rows(static_cast<const W *>(slot_acquire(R, t, err)), w + J * T, rg, cg, a);
+      slot_release(R, t);
+      ++t;
+    }
+    const W c = reduce_rows(a, lane, row);
+    const int o = I * T + 4 * rg + row;
+    if (writer) w[o] = out[o] - c;
+    csync();
+  }
+  // B1: w_I = w_I - sum_{J>I} NT_IJ w_J (sequential over I descending)
+  for (int I = nt - 1; I >= 0; --I) {
+    W a[4] = {W(0), W(0), W(0), W(0)};
+    const int j1 = trT[I].j0;
+    for (int J = I + 1; J <= j1; ++J) {
+      tile_rows(static_cast<const W *>(slot_acquire(R, t, err)), w + J * T, rg, cg, a);
+      slot_release(R, t);
+      ++t;
+    }
+    const W c = reduce_rows(a, lane, row);
+    if (writer) w[I * T + 4 * rg + row] -= c;
+    csync();
+  }
+  // B2: out_I = inv(L_II)^T w_I (independent tile rows, one warp per tile); every warp still
+  // waits for and releases every tile in order, which keeps the slots' phases unambiguous
+  for (int I = 0; I < nt; ++I) {
+    const W *D = static_cast<const W *>(slot_acquire(R, t, err));
+    if ((I & 7) == warp) tile_rows_warp(D, w + I * T, out + I * T, lane);
+    slot_release(R, t);
+    ++t;
+  }
+  csync();
+}
+
+// Producer side of one pass: same tile order as consumer_pass.
+__device__ void producer_pass(const Ring &R, const TileRow *__restrict__ tr,
+                              const TileRow *__restrict__ trT, int nt, const unsigned char *fac,
+                              const unsigned char *dinv, const unsigned char *facT,
+                              const unsigned char *dinvT, uint32_t tile_bytes, uint32_t &t,
+                              int32_t *err) {
+  auto issue = [&](const unsigned char *src) {
+    const uint32_t s = t % R.slots;
+    if (!*(volatile int *)R.abort) {
+      if (t >= R.slots && !mbar_wait(&R.empty[s], ((t / R.slots) - 1u) & 1u)) {
+        *(volatile int *)R.abort = 1;
+        atomicOr(err, 2);
+      } else {
+        mbar_expect_tx(&R.full[s], tile_bytes);
+        bulk_g2s(R.base + (size_t)s * R.slot_bytes, src, tile_bytes, &R.full[s]);
+      }
+    }
+    ++t;
+  };
+  const size_t TB = tile_bytes;
+  const size_t esz = TB / (T * T);
+  for (int I = 0; I < nt; ++I) issue(dinv + (size_t)I * TB);
+  for (int I = 0; I < nt; ++I) {
+    const TileRow TI = tr[I];
+    const unsigned char *row = fac + (size_t)TI.off * esz;
+    for (int J = TI.j0; J < I; ++J) issue(row + (size_t)(J - TI.j0) * TB);
+  }
+  for (int I = nt - 1; I >= 0; --I) {
+    const TileRow U = trT[I];
+    const unsigned char *row = facT + (size_t)U.off * esz;
+    for (int J = I + 1; J <= U.j0; ++J) issue(row + (size_t)(J - I - 1) * TB);
+  }
+  for (int I = 0; I < nt; ++I) issue(dinvT + (size_t)I * TB);
+}
+
+struct Vecs {
+  double *y;  // FP64 solution being refined
+  void *w;    // working-precision right-hand side / workspace of a solve pass
+  void *out;  // working-precision result of a solve pass
+};
+
+template <typename W>
+__device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring &R, const Vecs &V,
+                               const double *__restrict__ u, double *__restrict__ y, int k,
+                               int refine_steps, uint32_t &t, double *red, int *s_again) {
+  const int mp = B.nt * T;
+  const int tid = threadIdx.x;
+  W *w = static_cast<W *>(V.w);
+  W *out = static_cast<W *>(V.out);
+  const double *ub = u + B.row0 * a.nrhs + k;  // u of this block (stride nrhs), global
+  double un2 = 0.0;
+  for (int r = tid; r < mp; r += kConsumers) {
+    const double ur = r < B.m ? ub[(int64_t)r * a.nrhs] : 0.0;
+    V.y[r] = 0.0;
+    w[r] = W(ur);
+    un2 += ur * ur;
+  }
+  if (refine_steps > 0)
+    un2 = csum(un2, red);  // also orders the writes above
+  else
+    csync();
+  const TileRow *tr = a.trow + B.trow0;
+  const TileRow *trT = a.trowT + B.trow0;
+  int s = 0;
+  for (;;) {
+    consumer_pass<W>(R, tr, trT, B.nt, w, out, t, a.err);
+    for (int r = tid; r < mp; r += kConsumers) V.y[r] += double(out[r]);
+    csync();
+    int again = 0;
+    if (s < refine_steps) {
+      // res = u - G_i y straight into w; a warp covers whole 32-row slices (coalesced)
+      double e2 = 0.0;
+      for (int r = tid; r < mp; r += kConsumers) {
+        if (r >= B.m) {
+          w[r] = W(0);
+          continue;
+        }
+        const int sl = B.slice0 + (r >> 5), l = r & 31;
+        const int64_t o = a.soff[sl];
+        const int wd = (int)((a.soff[sl + 1] - o) >> 5);
+        const double *sv = a.sval + o + l;
+        const int16_t *sc = a.scol + o + l;
+        double acc = ub[(int64_t)r * a.nrhs];
+#pragma unroll 4
+        for (int kk = 0; kk < wd; ++kk) acc = fma(-sv[32 * kk], V.y[sc[32 * kk]], acc);
+        w[r] = W(acc);
+        e2 += acc * acc;
+      }
+      e2 = csum(e2, red);
+      again = e2 > a.refine_tol * a.refine_tol * un2;
+    }
+    if (tid == 0) *s_again = again;
+    allsync();
+    if (!*(volatile int *)s_again) break;
+    ++s;
+  }
+  for (int r = tid; r < B.m; r += kConsumers) y[(B.row0 + r) * a.nrhs + k] = V.y[r];
+  if (tid == 0 && refine_steps > 0) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(a.refine_total), (unsigned long long)s);
+    atomicMax(a.refine_max, s);
+  }
+  csync();
+}
+
+__device__ void producer_block(const IterArgs &a, const BlockDesc &B, const Ring &R, uint32_t &t,
+                               int *s_again) {
+  const bool leader = (threadIdx.x & 31) == 0;
+  const bool p64 = B.prec64 != 0;
+  const unsigned char *fac = p64 ? reinterpret_cast<const unsigned char *>(a.fac64)
+                                 : reinterpret_cast<const unsigned char *>(a.fac32);
+  const unsigned char *facT = p64 ? reinterpret_cast<const unsigned char *>(a.facT64)
+                                  : reinterpret_cast<const unsigned char *>(a.facT32);
+  const unsigned char *dinv = p64 ? reinterpret_cast<const unsigned char *>(a.dinv64 + B.dinv_off)
+                                  : reinterpret_cast<const unsigned char *>(a.dinv32 + B.dinv_off);
+  const unsigned char *dinvT = p64
+                                   ? reinterpret_cast<const unsigned char *>(a.dinvT64 + B.dinv_off)
+                                   : reinterpret_cast<const unsigned char *>(a.dinvT32 + B.dinv_off);
+  const uint32_t tb = (uint32_t)(T * T * (p64 ? 8 : 4));
+  for (;;) {
+    if (leader)
+      producer_pass(R, a.trow + B.trow0, a.trowT + B.trow0, B.nt, fac, dinv, facT, dinvT, tb, t,
+                    a.err);
+    __syncwarp();
+    allsync();
+    if (!*(volatile int *)s_again) break;
+  }
+}
+
+__global__ void __launch_bounds__(kProjThreads, 1)
+    k_proj(IterArgs a, const double *__restrict__ u, double *__restrict__ y, int check_lane) {
+  __shared__ uint64_t full[kMaxProjSlots], empty[kMaxProjSlots];
+  __shared__ double red[8];
+  __shared__ int s_again, s_abort;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const BlockDesc B = a.blk[blockIdx.x];
+  const int mpmax = a.max_mp;
+  Ring R;
+  R.base = dsm;
+  R.full = full;
+  R.empty = empty;
+  R.slots = (uint32_t)a.proj_slots;
+  R.slot_bytes = (uint32_t)a.proj_slot_bytes;
+  R.abort = &s_abort;
+  Vecs V;
+  unsigned char *vb = dsm + (size_t)R.slots * R.slot_bytes;
+  const size_t wb = (size_t)a.proj_wbytes * mpmax;
+  V.y = reinterpret_cast<double *>(vb);
+  V.w = vb + 8 * (size_t)mpmax;
+  V.out = vb + 8 * (size_t)mpmax + wb;
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < R.slots; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers / 32);
+    }
+    s_abort = 0;
+    s_again = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t t = 0;  // tiles issued (producer) / consumed (consumers) so far
+  const bool producer = threadIdx.x >= kConsumers;
+  for (int k = 0; k < a.nrhs; ++k) {
+    if (check_lane && a.lane[B.sys * a.nrhs + k].status != CIMMINO_RUNNING) continue;
+    const int rs = B.prec64 ? 0 : a.refine_steps;
+    if (producer) {
+      producer_block(a, B, R, t, &s_again);
+    } else if (B.prec64) {
+      consumer_block<double>(a, B, R, V, u, y, k, 0, t, red, &s_again);
+    } else {
+      consumer_block<float>(a, B, R, V, u, y, k, rs, t, red, &s_again);
+    }
+  }
+  // the producer drains its own copies before the CTA exits (normally already landed)
+  if (producer && (threadIdx.x & 31) == 0) {
+    const uint32_t first = t > R.slots ? t - R.slots : 0u;
+    for (uint32_t v = first; v < t; ++v) mbar_wait(&R.full[v % R.slots], (v / R.slots) & 1u);
+  }
+}
+
+}  // namespace
+
+int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes) {
+  return slots * slot_bytes + 8 * max_mp + 2 * wbytes * max_mp;
+}
+
+void set_proj_smem_attr(int bytes) {
+  cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
+  k_proj<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+}
+
+}  // namespace cimmino

@@ -467,6 +467,47 @@ __global__ void k_tile_j0(const BlockDesc *__restrict__ blk, int32_t nblk,
   }
 }
 
+// Sliced-ELL copy of the Gram blocks (slices of 32 consecutive rows of a block,
+// entries stored [k][lane] so that a warp reads 32 consecutive values), used by the
+// FP64 refinement residual res = u - G_i y.  Width of a slice = its longest row.
+__global__ void k_sell_width(const BlockDesc *__restrict__ blk, int32_t nblk,
+                             const int64_t *__restrict__ brp, int64_t *__restrict__ cnt) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const BlockDesc B = blk[b];
+  const int ns = (B.m + 31) / 32;
+  for (int sl = threadIdx.x; sl < ns; sl += blockDim.x) {
+    int64_t w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int r = sl * 32 + l;
+      if (r < B.m) w = max(w, brp[B.row0 + r + 1] - brp[B.row0 + r]);
+    }
+    cnt[B.slice0 + sl] = 32 * w;
+  }
+}
+
+__global__ void k_sell_fill(const BlockDesc *__restrict__ blk, int32_t nblk,
+                            const int64_t *__restrict__ brp, const int32_t *__restrict__ bci,
+                            const double *__restrict__ bcv, const int64_t *__restrict__ soff,
+                            int16_t *__restrict__ scol, double *__restrict__ sval) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const BlockDesc B = blk[b];
+  const int ns = (B.m + 31) / 32;
+  for (int r = threadIdx.x; r < ns * 32; r += blockDim.x) {
+    const int sl = B.slice0 + r / 32, l = r % 32;
+    const int64_t o = soff[sl];
+    const int w = (int)((soff[sl + 1] - o) / 32);
+    const int64_t p0 = r < B.m ? brp[B.row0 + r] : 0;
+    const int len = r < B.m ? (int)(brp[B.row0 + r + 1] - p0) : 0;
+    for (int k = 0; k < w; ++k) {
+      const bool real = k < len;
+      scol[o + (int64_t)k * 32 + l] = real ? (int16_t)bci[p0 + k] : (int16_t)0;
+      sval[o + (int64_t)k * 32 + l] = real ? bcv[p0 + k] : 0.0;
+    }
+  }
+}
+
 // Write the lower triangle of G_b into the tiles of its factor (zeroing the tile
 // row first); padded rows beyond m get a unit diagonal.
 template <typename W>
@@ -588,6 +629,18 @@ void bd_fill(const int64_t *crp, const int32_t *cci, const double *ccv, const Bl
 void launch_tile_j0(const BlockDesc *blk, int32_t nblk, const int32_t *rowmin, int dense,
                     int32_t *j0, cudaStream_t s) {
   if (nblk > 0) k_tile_j0<<<(unsigned)nblk, 64, 0, s>>>(blk, nblk, rowmin, dense, j0);
+}
+
+void sell_width(const BlockDesc *blk, int32_t nblk, const int64_t *brp, int64_t *cnt,
+                cudaStream_t s) {
+  if (nblk > 0) k_sell_width<<<(unsigned)nblk, 64, 0, s>>>(blk, nblk, brp, cnt);
+}
+
+void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int32_t *bci,
+               const double *bcv, const int64_t *soff, int16_t *scol, double *sval,
+               cudaStream_t s) {
+  if (nblk > 0)
+    k_sell_fill<<<(unsigned)nblk, kThreads, 0, s>>>(blk, nblk, brp, bci, bcv, soff, scol, sval);
 }
 
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,

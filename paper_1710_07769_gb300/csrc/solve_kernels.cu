@@ -1,9 +1,7 @@
 // Per-iteration kernels of Algorithm 2 (CG on H x = xi, Section 1.1):
 //   k_spmv_res   u = A p (projection input) and the true residual of the current x
 //                (||f - A x||_2 through the scaled system: (f - A x)_orig = D (f_s - A_s x))
-//   k_proj       y_i = G_i^{-1} u_i per block: forward / backward solves with the tiled
-//                factor (inverted diagonal tiles) and, for FP32 factors, FP64 iterative
-//                refinement against the exact Gram block G_i (sparse, FP64)
+//   k_proj       y_i = G_i^{-1} u_i per block (proj_kernel.cu)
 //   k_spmv_t     psi = A^T y = sum_i A_i^T y_i (gather over the transpose: no atomics)
 //                fused with p^T psi
 //   k_update_xr  x += alpha p, r -= alpha psi, fused with r^T r
@@ -151,201 +149,6 @@ __global__ void __launch_bounds__(kThreads) k_spmv_res(IterArgs a) {
           }
         }
       }
-  }
-}
-
-// ----------------------------------------------------------------------------
-// projection kernel: one CTA per block
-
-struct ProjSmem {
-  double *u, *y, *res;
-  void *w;   // working-precision vector (mp entries, sized for double)
-  void *bI;  // T entries
-  void *part;  // 2 x kWarps x T entries
-  double *red;
-};
-
-__device__ __forceinline__ ProjSmem proj_smem(int mp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ProjSmem s;
-  double *p = reinterpret_cast<double *>(smem_raw);
-  s.u = p;
-  s.y = p + mp;
-  s.res = p + 2 * mp;
-  s.w = p + 3 * mp;
-  s.bI = p + 4 * mp;
-  s.part = p + 4 * mp + T;
-  s.red = p + 4 * mp + T + 2 * kWarps * T;
-  return s;
-}
-
-template <typename W>
-__device__ __forceinline__ W pick8(const W (&acc)[8], int lane) {
-  W v = W(0);
-#pragma unroll
-  for (int rr = 0; rr < 8; ++rr)
-    if (lane == rr) v = acc[rr];
-  return v;
-}
-
-// w <- L^{-1} w  (tile rows in order; inverted diagonal tiles)
-template <typename W>
-__device__ void tile_forward(const W *__restrict__ fac, const TileRow *__restrict__ tr,
-                             const W *__restrict__ dinv, int nt, W *w, W *bI) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int I = 0; I < nt; ++I) {
-    const TileRow TI = tr[I];
-    const W *base = fac + TI.off;
-    W acc[8];
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) acc[rr] = W(0);
-#pragma unroll 2
-    for (int J = TI.j0; J < I; ++J) {
-      const W *t = base + (int64_t)(J - TI.j0) * T * T + (warp * 8) * T;
-      const W z0 = w[J * T + lane], z1 = w[J * T + lane + 32];
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        acc[rr] = fma(t[rr * T + lane], z0, acc[rr]);
-        acc[rr] = fma(t[rr * T + lane + 32], z1, acc[rr]);
-      }
-    }
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) acc[rr] = warp_sum(acc[rr]);
-    if (lane < 8) bI[warp * 8 + lane] = w[I * T + warp * 8 + lane] - pick8(acc, lane);
-    __syncthreads();
-    const W *D = dinv + (int64_t)I * T * T + (warp * 8) * T;
-    const W b0 = bI[lane], b1 = bI[lane + 32];
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      W s = D[rr * T + lane] * b0;
-      s = fma(D[rr * T + lane + 32], b1, s);
-      acc[rr] = warp_sum(s);
-    }
-    if (lane < 8) w[I * T + warp * 8 + lane] = pick8(acc, lane);
-    __syncthreads();
-  }
-}
-
-// w <- L^{-T} w  (tile rows in reverse order)
-template <typename W>
-__device__ void tile_backward(const W *__restrict__ fac, const TileRow *__restrict__ tr,
-                              const W *__restrict__ dinv, int nt, W *w, W *part) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int I = nt - 1; I >= 0; --I) {
-    const TileRow TI = tr[I];
-    // y_I = inv(L_II)^T w_I
-    {
-      const W *D = dinv + (int64_t)I * T * T + (warp * 8) * T;
-      W p0 = W(0), p1 = W(0);
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        const W wr = w[I * T + warp * 8 + rr];
-        p0 = fma(D[rr * T + lane], wr, p0);
-        p1 = fma(D[rr * T + lane + 32], wr, p1);
-      }
-      part[warp * T + lane] = p0;
-      part[warp * T + lane + 32] = p1;
-      __syncthreads();
-      if (threadIdx.x < T) {
-        W s = W(0);
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += part[q * T + threadIdx.x];
-        w[I * T + threadIdx.x] = s;
-      }
-      __syncthreads();
-    }
-    // w_J -= L_IJ^T y_I for the stored tiles left of the diagonal
-    W yr[8];
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) yr[rr] = w[I * T + warp * 8 + rr];
-    const W *base = fac + TI.off;
-    int buf = 0;
-    for (int J = I - 1; J >= TI.j0; --J) {
-      const W *t = base + (int64_t)(J - TI.j0) * T * T + (warp * 8) * T;
-      W p0 = W(0), p1 = W(0);
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        p0 = fma(t[rr * T + lane], yr[rr], p0);
-        p1 = fma(t[rr * T + lane + 32], yr[rr], p1);
-      }
-      W *pb = part + buf * kWarps * T;
-      pb[warp * T + lane] = p0;
-      pb[warp * T + lane + 32] = p1;
-      __syncthreads();
-      if (threadIdx.x < T) {
-        W s = W(0);
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += pb[q * T + threadIdx.x];
-        w[J * T + threadIdx.x] -= s;
-      }
-      buf ^= 1;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename W>
-__device__ void proj_block(const IterArgs &a, const BlockDesc &B, const W *fac, const W *dinv,
-                           const double *__restrict__ u, double *__restrict__ y, int k,
-                           int refine_steps, const ProjSmem &sm) {
-  const int mp = B.nt * T;
-  const int tid = threadIdx.x;
-  W *w = reinterpret_cast<W *>(sm.w);
-  for (int r = tid; r < mp; r += kThreads) {
-    sm.u[r] = r < B.m ? u[(B.row0 + r) * a.nrhs + k] : 0.0;
-    sm.y[r] = 0.0;
-    sm.res[r] = 0.0;
-  }
-  __syncthreads();
-  double un2 = 0.0;
-  if (refine_steps > 0) {
-    for (int r = tid; r < B.m; r += kThreads) un2 += sm.u[r] * sm.u[r];
-    un2 = block_sum(un2, sm.red);
-  }
-  const double *rhs = sm.u;
-  const TileRow *tr = a.trow + B.trow0;
-  const W *dblk = dinv + B.dinv_off;
-  int s = 0;
-  for (;;) {
-    for (int r = tid; r < mp; r += kThreads) w[r] = W(rhs[r]);
-    __syncthreads();
-    tile_forward<W>(fac, tr, dblk, B.nt, w, reinterpret_cast<W *>(sm.bI));
-    tile_backward<W>(fac, tr, dblk, B.nt, w, reinterpret_cast<W *>(sm.part));
-    for (int r = tid; r < mp; r += kThreads) sm.y[r] += double(w[r]);
-    __syncthreads();
-    if (s >= refine_steps) break;
-    // FP64 residual of the inner system: res = u - G_i y with the exact Gram block
-    double e2 = 0.0;
-    for (int r = tid; r < B.m; r += kThreads) {
-      const int64_t gr = B.row0 + r;
-      double acc = sm.u[r];
-      for (int64_t q = a.brp[gr]; q < a.brp[gr + 1]; ++q) acc = fma(-a.bcv[q], sm.y[a.bci[q]], acc);
-      sm.res[r] = acc;
-      e2 += acc * acc;
-    }
-    e2 = block_sum(e2, sm.red);
-    if (e2 <= a.refine_tol * a.refine_tol * un2) break;
-    ++s;
-    rhs = sm.res;
-  }
-  for (int r = tid; r < B.m; r += kThreads) y[(B.row0 + r) * a.nrhs + k] = sm.y[r];
-  if (tid == 0 && refine_steps > 0) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(a.refine_total), (unsigned long long)s);
-    atomicMax(a.refine_max, s);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads)
-    k_proj(IterArgs a, const double *__restrict__ u, double *__restrict__ y, int check_lane) {
-  const BlockDesc B = a.blk[blockIdx.x];
-  const ProjSmem sm = proj_smem(a.max_mp);
-  for (int k = 0; k < a.nrhs; ++k) {
-    if (check_lane && !lane_running(a, B.sys, k)) continue;
-    if (B.prec64)
-      proj_block<double>(a, B, a.fac64, a.dinv64, u, y, k, 0, sm);
-    else
-      proj_block<float>(a, B, a.fac32, a.dinv32, u, y, k, a.refine_steps, sm);
-    __syncthreads();
   }
 }
 
@@ -547,24 +350,12 @@ __global__ void k_row_abs(const int64_t *__restrict__ rp, const double *__restri
 }  // namespace
 
 // ============================================================================ launchers
-int proj_smem_bytes(int max_mp) {
-  return (int)(sizeof(double) * (4 * (size_t)max_mp + T + 2 * kWarps * T + 32));
-}
-
-void set_proj_smem_attr(int bytes) {
-  cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 void launch_rhs_scale(const IterArgs &a, const double *Fin, const int32_t *perm, cudaStream_t s) {
   k_rhs_scale<<<a.ncta, kThreads, 0, s>>>(a, Fin, perm);
 }
 
 void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStream_t s) {
   k_spmv_plain<<<a.ncta, kThreads, 0, s>>>(a, v, out);
-}
-
-void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
-  k_proj<<<a.nblk, kThreads, a.proj_smem, s>>>(a, u, y, check_lane);
 }
 
 void launch_spmv_t(const IterArgs &a, const double *y, double *out, cudaStream_t s) {
@@ -577,7 +368,7 @@ void launch_cg_init(const IterArgs &a, cudaStream_t s) {
 
 void launch_iteration(const IterArgs &a, cudaStream_t s) {
   k_spmv_res<<<a.ncta, kThreads, 0, s>>>(a);
-  k_proj<<<a.nblk, kThreads, a.proj_smem, s>>>(a, a.u, a.y, 1);
+  launch_proj(a, a.u, a.y, 1, s);
   k_spmv_t<1><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
   k_update_xr<<<a.ncta, kThreads, 0, s>>>(a);
   k_update_p<<<a.ncta, kThreads, 0, s>>>(a);
