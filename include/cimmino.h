@@ -80,7 +80,7 @@ typedef struct cimmino_opts {
   int32_t tile;           /* tile edge T of the factor layout: 0 = default (64)      */
   int32_t refine_max;     /* refinement steps per inner solve (default 6)           */
   double refine_tol;      /* stop refining when ||G_i y - u_i||_2 <= refine_tol *   */
-                          /* ||u_i||_2 (default 1e-13)                               */
+                          /* ||u_i||_2 (default 1e-12)                               */
   double pivot_ratio_min; /* FP32 block refactored in FP64 when min_j L_jj^2 /      */
                           /* max_j G_jj < pivot_ratio_min (default 1e-4)            */
   int32_t max_iter;       /* CG iteration limit (default 10000, Section 3.1)        */

@@ -112,8 +112,10 @@ struct cimmino_ctx {
   DBuf<int64_t> rp, cp, brp, crp;
   DBuf<int32_t> ci, ri, bci, cci, perm;
   DBuf<double> va, cv, d, bcv, ccv, rowabs, sval;
-  DBuf<int64_t> soff;
+  DBuf<int64_t> soff, aoff, toff;
   DBuf<int16_t> scol;
+  DBuf<int32_t> acol, tcol;
+  DBuf<double> aval, tval;
   DBuf<BlockDesc> blk;
   DBuf<TileRow> trow;
   DBuf<SysDesc> sys;
@@ -152,7 +154,7 @@ void opts_default(cimmino_opts *o) {
   o->layout = CIMMINO_LAYOUT_SKYLINE;
   o->tile = 0;
   o->refine_max = 6;
-  o->refine_tol = 1e-13;
+  o->refine_tol = 1e-12;
   o->pivot_ratio_min = 1e-4;
   o->max_iter = 10000;
   o->use_graph = 1;
@@ -565,18 +567,52 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->ccv.release();
     c->have_aat = false;
   }
-  // ---- vector-kernel CTA table (256 rows per CTA, never straddling systems)
+  // ---- vector-kernel CTA table (256 rows per CTA, never straddling systems) and the
+  // 32-row slices of the sliced-ELL copies of A and A^T
+  std::vector<int64_t> hsrow0;
+  std::vector<int32_t> hsrows;
   for (int32_t q = 0; q < nsys; ++q) {
     SysDesc &S = c->hsys[q];
     S.cta0 = (int32_t)c->hcta.size();
     for (int64_t r = 0; r < S.n; r += 256) {
-      CtaDesc C;
+      CtaDesc C{};
       C.row0 = S.row0 + r;
       C.rows = (int32_t)std::min<int64_t>(256, S.n - r);
       C.sys = q;
+      C.slice0 = (int32_t)hsrow0.size();
+      for (int64_t r2 = r; r2 < r + C.rows; r2 += 32) {
+        hsrow0.push_back(S.row0 + r2);
+        hsrows.push_back((int32_t)std::min<int64_t>(32, S.n - r2));
+      }
       c->hcta.push_back(C);
     }
     S.ncta = (int32_t)c->hcta.size() - S.cta0;
+  }
+  {
+    const int32_t ns = (int32_t)hsrow0.size();
+    DBuf<int64_t> srow0, scnt;
+    DBuf<int32_t> srows;
+    srow0.alloc(ns);
+    srows.alloc(ns);
+    scnt.alloc(ns);
+    h2d(srow0.p, hsrow0.data(), ns, s);
+    h2d(srows.p, hsrows.data(), ns, s);
+    auto build = [&](const int64_t *ptr, const int32_t *idx, const double *val,
+                     DBuf<int64_t> &off, DBuf<int32_t> &col, DBuf<double> &vv) {
+      off.alloc(ns + 1);
+      sell_rows_width(ptr, srow0.p, srows.p, ns, scnt.p, s);
+      launch_scan_counts(scnt.p, off.p, ns, tmp.p, tl, s);
+      int64_t tot = 0;
+      d2h(&tot, off.p + ns, 1, s);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      col.alloc(tot);
+      vv.alloc(tot);
+      sell_rows_fill(ptr, idx, val, srow0.p, srows.p, ns, off.p, col.p, vv.p, s);
+      c->setup_launches += 5;  // widths, 3-pass scan, fill
+    };
+    build(c->rp.p, c->ci.p, c->va.p, c->aoff, c->acol, c->aval);
+    build(c->cp.p, c->ri.p, c->cv.p, c->toff, c->tcol, c->tval);
+    CUDA_TRY(cudaStreamSynchronize(s));
   }
   c->sys.alloc(nsys);
   h2d(c->sys.p, c->hsys.data(), nsys, s);
@@ -633,6 +669,12 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.brp = c->brp.p;
   a.bci = c->bci.p;
   a.bcv = c->bcv.p;
+  a.aoff = c->aoff.p;
+  a.acol = c->acol.p;
+  a.aval = c->aval.p;
+  a.toff = c->toff.p;
+  a.tcol = c->tcol.p;
+  a.tval = c->tval.p;
   a.soff = c->soff.p;
   a.scol = c->scol.p;
   a.sval = c->sval.p;

@@ -58,6 +58,8 @@ struct CtaDesc {
   int64_t row0;
   int32_t rows;
   int32_t sys;
+  int32_t slice0;  // first 32-row slice of the CTA in the sliced-ELL copies of A and A^T
+  int32_t pad;
 };
 
 // Per right-hand side of a system ("lane") CG state, written by the kernels.
@@ -167,6 +169,11 @@ void sell_width(const BlockDesc *blk, int32_t nblk, const int64_t *brp, int64_t 
 void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int32_t *bci,
                const double *bcv, const int64_t *soff, int16_t *scol, double *sval,
                cudaStream_t s);
+void sell_rows_width(const int64_t *ptr, const int64_t *srow0, const int32_t *srows,
+                     int32_t nslice, int64_t *cnt, cudaStream_t s);
+void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
+                    const int64_t *srow0, const int32_t *srows, int32_t nslice,
+                    const int64_t *off, int32_t *ocol, double *oval, cudaStream_t s);
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, const int64_t *brp, const int32_t *bci,
                          const double *bcv, void *fac, int prec64, cudaStream_t s);
@@ -203,6 +210,12 @@ struct IterArgs {
   const int64_t *brp;
   const int32_t *bci;
   const double *bcv;
+  const int64_t *aoff;   // sliced-ELL copy of A (32-row slices, [k][lane]): offsets
+  const int32_t *acol;   //   columns
+  const double *aval;    //   values
+  const int64_t *toff;   // sliced-ELL copy of A^T (32-column slices)
+  const int32_t *tcol;   //   rows
+  const double *tval;    //   values
   const int64_t *soff;   // sliced-ELL Gram blocks: slice offsets (entries)
   const int16_t *scol;   //   block-local columns
   const double *sval;    //   values

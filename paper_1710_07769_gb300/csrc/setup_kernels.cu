@@ -508,6 +508,41 @@ __global__ void k_sell_fill(const BlockDesc *__restrict__ blk, int32_t nblk,
   }
 }
 
+// Sliced-ELL copy of a CSR matrix (used for A and for A^T): slice k covers rows
+// srow0[k] .. srow0[k] + srows[k] - 1 (at most 32, never straddling systems); entry k
+// of lane l sits at off + 32 k + l.  Padding entries point at the slice's first row
+// with value 0, so they read a valid element and add nothing.
+__global__ void k_sell_rows_width(const int64_t *__restrict__ ptr, const int64_t *__restrict__ srow0,
+                                  const int32_t *__restrict__ srows, int32_t nslice,
+                                  int64_t *__restrict__ cnt) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nslice) return;
+  int64_t w = 0;
+  for (int l = 0; l < srows[k]; ++l) w = max(w, ptr[srow0[k] + l + 1] - ptr[srow0[k] + l]);
+  cnt[k] = 32 * w;
+}
+
+__global__ void k_sell_rows_fill(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                 const double *__restrict__ val, const int64_t *__restrict__ srow0,
+                                 const int32_t *__restrict__ srows, int32_t nslice,
+                                 const int64_t *__restrict__ off, int32_t *__restrict__ ocol,
+                                 double *__restrict__ oval) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = (int)(g >> 5), l = (int)(g & 31);
+  if (k >= nslice) return;
+  const int64_t o = off[k];
+  const int w = (int)((off[k + 1] - o) >> 5);
+  const int64_t r = srow0[k] + l;
+  const bool real = l < srows[k];
+  const int64_t p0 = real ? ptr[r] : 0;
+  const int len = real ? (int)(ptr[r + 1] - p0) : 0;
+  for (int e = 0; e < w; ++e) {
+    const bool in = e < len;
+    ocol[o + 32 * (int64_t)e + l] = in ? idx[p0 + e] : (int32_t)srow0[k];
+    oval[o + 32 * (int64_t)e + l] = in ? val[p0 + e] : 0.0;
+  }
+}
+
 // Write the lower triangle of G_b into the tiles of its factor (zeroing the tile
 // row first); padded rows beyond m get a unit diagonal.
 template <typename W>
@@ -641,6 +676,21 @@ void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int
                cudaStream_t s) {
   if (nblk > 0)
     k_sell_fill<<<(unsigned)nblk, kThreads, 0, s>>>(blk, nblk, brp, bci, bcv, soff, scol, sval);
+}
+
+void sell_rows_width(const int64_t *ptr, const int64_t *srow0, const int32_t *srows,
+                     int32_t nslice, int64_t *cnt, cudaStream_t s) {
+  if (nslice > 0)
+    k_sell_rows_width<<<grid_for(nslice, kThreads), kThreads, 0, s>>>(ptr, srow0, srows, nslice,
+                                                                      cnt);
+}
+
+void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
+                    const int64_t *srow0, const int32_t *srows, int32_t nslice,
+                    const int64_t *off, int32_t *ocol, double *oval, cudaStream_t s) {
+  if (nslice > 0)
+    k_sell_rows_fill<<<grid_for((int64_t)nslice * 32, kThreads), kThreads, 0, s>>>(
+        ptr, idx, val, srow0, srows, nslice, off, ocol, oval);
 }
 
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,

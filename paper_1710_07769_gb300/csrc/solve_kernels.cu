@@ -44,13 +44,15 @@ __device__ __forceinline__ bool arrive_last(int32_t *counter, int ncta) {
   return s_last != 0;
 }
 
-// Sum of the partials of one system for rhs k, fixed order; valid in warp 0.
+// Sum of the partials of one system for rhs k in a fixed order, by the whole CTA (each
+// thread loads a few partials, independent loads in flight, then a fixed tree); every
+// thread of the CTA must call it and gets the result.
 __device__ __forceinline__ double reduce_partials(const double *part, const SysDesc &S, int nrhs,
-                                                  int k) {
+                                                  int k, double *red) {
   double v = 0.0;
-  const int lane = threadIdx.x & 31;
-  for (int c = lane; c < S.ncta; c += 32) v += __ldcg(part + (int64_t)(S.cta0 + c) * nrhs + k);
-  return warp_sum(v);
+  for (int c = threadIdx.x; c < S.ncta; c += blockDim.x)
+    v += __ldcg(part + (int64_t)(S.cta0 + c) * nrhs + k);
+  return block_sum(v, red);
 }
 
 __device__ __forceinline__ bool lane_running(const IterArgs &a, int sys, int k) {
@@ -77,9 +79,8 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x == 0) part_ptr(a, kPartMisc)[(int64_t)blockIdx.x * a.nrhs + k] = s;
   }
   if (arrive_last(a.cnt + kPartMisc * a.nsys + C.sys, S.ncta)) {
-    if (threadIdx.x < 32)
-      for (int k = 0; k < a.nrhs; ++k) {
-        double f2 = reduce_partials(part_ptr(a, kPartMisc), S, a.nrhs, k);
+    for (int k = 0; k < a.nrhs; ++k) {
+        double f2 = reduce_partials(part_ptr(a, kPartMisc), S, a.nrhs, k, red);
         if (threadIdx.x == 0) {
           LaneState &L = a.lane[C.sys * a.nrhs + k];
           L.fnorm2 = f2;
@@ -117,12 +118,19 @@ __global__ void __launch_bounds__(kThreads) k_spmv_res(IterArgs a) {
     if (!lane_running(a, C.sys, k)) continue;  // uniform across the CTA
     double e2 = 0.0;
     if (act) {
+      // sliced-ELL: a warp's 32 rows read their k-th entries as one coalesced load
+      const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+      const int64_t o = a.aoff[sl];
+      const int wd = (int)((a.aoff[sl + 1] - o) >> 5);
+      const double *av = a.aval + o + l;
+      const int32_t *ac = a.acol + o + l;
       double su = 0.0, sx = 0.0;
-      for (int64_t q = a.rp[r]; q < a.rp[r + 1]; ++q) {
-        const double av = a.va[q];
-        const int64_t c = (int64_t)a.ci[q] * a.nrhs + k;
-        su = fma(av, a.p[c], su);
-        sx = fma(av, a.x[c], sx);
+#pragma unroll 4
+      for (int e = 0; e < wd; ++e) {
+        const double v = av[32 * e];
+        const int64_t c = (int64_t)ac[32 * e] * a.nrhs + k;
+        su = fma(v, a.p[c], su);
+        sx = fma(v, a.x[c], sx);
       }
       a.u[r * a.nrhs + k] = su;
       double e = a.d[r] * (a.fs[r * a.nrhs + k] - sx);
@@ -132,11 +140,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_res(IterArgs a) {
     if (threadIdx.x == 0) part_ptr(a, kPartRes)[(int64_t)blockIdx.x * a.nrhs + k] = s;
   }
   if (arrive_last(a.cnt + kPartRes * a.nsys + C.sys, S.ncta)) {
-    if (threadIdx.x < 32)
-      for (int k = 0; k < a.nrhs; ++k) {
+    for (int k = 0; k < a.nrhs; ++k) {
         LaneState &L = a.lane[C.sys * a.nrhs + k];
-        if (L.status != CIMMINO_RUNNING) continue;
-        double e2 = reduce_partials(part_ptr(a, kPartRes), S, a.nrhs, k);
+        if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+        double e2 = reduce_partials(part_ptr(a, kPartRes), S, a.nrhs, k, red);
         if (threadIdx.x == 0) {
           double rel = sqrt(e2 / L.fnorm2);
           L.relres = rel;
@@ -166,9 +173,14 @@ __global__ void __launch_bounds__(kThreads)
     if (MODE == 1 && !lane_running(a, C.sys, k)) continue;
     double pq = 0.0;
     if (act) {
+      const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+      const int64_t o = a.toff[sl];
+      const int wd = (int)((a.toff[sl + 1] - o) >> 5);
+      const double *tv = a.tval + o + l;
+      const int32_t *tc = a.tcol + o + l;
       double s = 0.0;
-      for (int64_t q = a.cp[j]; q < a.cp[j + 1]; ++q)
-        s = fma(a.cv[q], yin[(int64_t)a.ri[q] * a.nrhs + k], s);
+#pragma unroll 4
+      for (int e = 0; e < wd; ++e) s = fma(tv[32 * e], yin[(int64_t)tc[32 * e] * a.nrhs + k], s);
       out[j * a.nrhs + k] = s;
       if (MODE == 1) pq = a.p[j * a.nrhs + k] * s;
     }
@@ -178,11 +190,10 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   if (MODE == 1 && arrive_last(a.cnt + kPartPq * a.nsys + C.sys, S.ncta)) {
-    if (threadIdx.x < 32)
-      for (int k = 0; k < a.nrhs; ++k) {
+    for (int k = 0; k < a.nrhs; ++k) {
         LaneState &L = a.lane[C.sys * a.nrhs + k];
-        if (L.status != CIMMINO_RUNNING) continue;
-        double pq = reduce_partials(part_ptr(a, kPartPq), S, a.nrhs, k);
+        if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+        double pq = reduce_partials(part_ptr(a, kPartPq), S, a.nrhs, k, red);
         if (threadIdx.x == 0) {
           L.pq = pq;
           if (!(pq > 0.0) || !isfinite(pq)) {
@@ -218,9 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(IterArgs a) {
     if (threadIdx.x == 0) part_ptr(a, kPartRr)[(int64_t)blockIdx.x * a.nrhs + k] = t;
   }
   if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
-    if (threadIdx.x < 32)
-      for (int k = 0; k < a.nrhs; ++k) {
-        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k);
+    for (int k = 0; k < a.nrhs; ++k) {
+        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k, red);
         if (threadIdx.x == 0) {
           LaneState &L = a.lane[C.sys * a.nrhs + k];
           L.rho[0] = rr;
@@ -253,11 +263,10 @@ __global__ void __launch_bounds__(kThreads) k_update_xr(IterArgs a) {
     if (threadIdx.x == 0) part_ptr(a, kPartRr)[(int64_t)blockIdx.x * a.nrhs + k] = t;
   }
   if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
-    if (threadIdx.x < 32)
-      for (int k = 0; k < a.nrhs; ++k) {
+    for (int k = 0; k < a.nrhs; ++k) {
         LaneState &L = a.lane[C.sys * a.nrhs + k];
-        if (L.status != CIMMINO_RUNNING) continue;
-        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k);
+        if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+        double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k, red);
         if (threadIdx.x == 0) {
           const int par = L.t & 1;
           L.rho[par ^ 1] = rr;
