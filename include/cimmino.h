@@ -223,6 +223,26 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
 int cimmino_aat_noalloc(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
                         int32_t *col_idx, double *val, int64_t capacity);
 
+/* Block-row partition by the row inner-product graph G_RIP (Sections 2.1-2.3): vertices
+ * are rows, edge (i, j) carries cost |c_ij| / sqrt(c_ii c_jj), the cosine of rows i and j
+ * after unit 2-norm row scaling, for every nonzero c_ij of C = A A^T.  The K-way
+ * partition minimises the cutsize (Eq. 2.6 = sum of inter-block |inner products|) subject
+ * to at most `cap` rows per block (Eq. A.1 with unit vertex weights; cap = n / K gives
+ * exact balance).  Host-only, no GPU: multilevel heavy-edge coarsening, recursive
+ * bisection, balance-constrained k-way refinement; rows inside a block are ordered by
+ * reverse Cuthill-McKee (the order inside a block is free, Section 2.2).
+ *   C            host CSR of A A^T of the UNSCALED matrix with its diagonal (e.g. from
+ *                cimmino_aat); row i needs c_ii > 0.
+ *   K, cap       number of blocks (1 <= K <= n) and the row cap (cap * K >= n).
+ *   seed         random seed of the matching and bisection orders.
+ *   perm         out, n int32: block row order (permuted row r = original row perm[r]).
+ *   block_ptr    out, K+1 int64 offsets over the permuted rows.
+ *   cutsize      out (may be NULL): cut of the returned partition in cosine units.
+ * Errors: EINVAL, ENOMEM. */
+int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_t *cci, const double *ccv,
+                          int32_t K, int32_t cap, uint64_t seed, int32_t *perm,
+                          int64_t *block_ptr, double *cutsize);
+
 /* Benchmark hook: after a cimmino_solve() on a single-system context, launch each
  * per-iteration kernel `reps` times back to back on the context's stream, on the
  * vectors of the last solve, and write the average device time per launch in

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["FP64", "FP32_REFINE", "DENSE", "SKYLINE", "CimminoError", "Solver", "BatchSolver",
-           "aat", "load", "lib_path", "EXPORTS"]
+           "aat", "partition_rip", "load", "lib_path", "EXPORTS"]
 
 FP64, FP32_REFINE = 0, 1
 DENSE, SKYLINE = 0, 1
@@ -34,7 +34,7 @@ EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimm
            "cimmino_solve_batch", "cimmino_free", "cimmino_last_error", "cimmino_get_aat_nnz",
            "cimmino_get_aat", "cimmino_get_scaled", "cimmino_block_rows", "cimmino_get_factor",
            "cimmino_project", "cimmino_project_rhs", "cimmino_aat", "cimmino_aat_noalloc",
-           "cimmino_time_kernels", "cimmino_version"]
+           "cimmino_partition_rip", "cimmino_time_kernels", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = False):
         L.cimmino_project_rhs.argtypes = [vp, vp, vp, i32]
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
+        L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
+                                            C.POINTER(dbl)]
         L.cimmino_aat_noalloc.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp, i64]
         L.cimmino_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -365,3 +367,23 @@ def aat(A, stream=None):
     _check(L, L.cimmino_aat(C.byref(csr), stream, C.byref(nnz), rp.ctypes.data, ci.ctypes.data,
                             v.ctypes.data))
     return rp, ci[: nnz.value], v[: nnz.value]
+
+
+def partition_rip(n: int, aat_csr, K: int, cap: Optional[int] = None, eps: float = 0.0,
+                  seed: int = 0):
+    """Graph partition of the row inner-product graph of A (Section 2): aat_csr =
+    (row_ptr, col, val) of A A^T for the unscaled A (host arrays, e.g. from ``aat``).  cap
+    defaults to ceil(n/K * (1 + eps)).  Returns (perm, block_ptr, cutsize); host only."""
+    L = load()
+    crp, cci, ccv = (_host(aat_csr[0], np.int64), _host(aat_csr[1], np.int32),
+                     _host(aat_csr[2], np.float64))
+    if cap is None:
+        cap = int(np.ceil(n / K * (1.0 + eps)))
+    perm = np.empty(n, np.int32)
+    bp = np.empty(K + 1, np.int64)
+    cut = C.c_double(0.0)
+    _check(L, L.cimmino_partition_rip(int(n), crp.ctypes.data, cci.ctypes.data, ccv.ctypes.data,
+                                      int(K), int(cap), int(seed), perm.ctypes.data,
+                                      bp.ctypes.data, C.byref(cut)))
+    return perm, bp, float(cut.value)
+

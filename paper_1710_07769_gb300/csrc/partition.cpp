@@ -1,0 +1,490 @@
+// Host-side block-row partitioner on the row inner-product graph G_RIP (Section 2.1):
+// a vertex per row, an edge (i, j) for every nonzero c_ij = r_i . r_j of C = A A^T,
+// with cost |c_ij| / (||r_i|| ||r_j||), i.e. the cosine of the two rows after the unit
+// 2-norm prescaling.  A K-way partition minimising the cutsize (Eq. 2.6, the sum of the
+// inter-block inner products) under the balance constraint W_k <= cap (Eq. A.1, unit
+// vertex weights) is decoded into a row permutation and block offsets (Section 2.2).
+//
+// This is input plumbing, not the solver's hot path.  Multilevel scheme:
+//   coarsen by heavy-edge matching -> recursive bisection of the coarsest graph by
+//   greedy graph growing + FM-style refinement -> project back with balance-constrained
+//   greedy k-way boundary refinement at every level -> move vertices until every part
+//   satisfies the cap.  Inside every part the rows are ordered by reverse Cuthill-McKee
+//   on the part's subgraph (the order inside a block row is arbitrary, Section 2.2), which
+//   keeps the envelope of the Gram blocks, and hence the skyline factors, small.
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "../../include/cimmino.h"
+
+namespace {
+
+struct Graph {
+  int32_t n = 0;
+  std::vector<int64_t> xadj;
+  std::vector<int32_t> adj;
+  std::vector<double> w;
+  std::vector<int32_t> vw;
+  double total_vw() const {
+    double s = 0;
+    for (int32_t v : vw) s += v;
+    return s;
+  }
+};
+
+Graph build_rip(int64_t n, const int64_t *crp, const int32_t *cci, const double *ccv) {
+  Graph g;
+  g.n = (int32_t)n;
+  std::vector<double> d(n, 1.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
+      if (cci[q] == i && ccv[q] > 0) d[i] = std::sqrt(ccv[q]);
+  g.xadj.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
+      if (cci[q] != i && ccv[q] != 0.0) ++c;
+    g.xadj[i + 1] = g.xadj[i] + c;
+  }
+  g.adj.resize(g.xadj[n]);
+  g.w.resize(g.xadj[n]);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t o = g.xadj[i];
+    for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
+      if (cci[q] != i && ccv[q] != 0.0) {
+        g.adj[o] = cci[q];
+        g.w[o] = std::fabs(ccv[q]) / (d[i] * d[cci[q]]);
+        ++o;
+      }
+  }
+  g.vw.assign(n, 1);
+  return g;
+}
+
+// heavy-edge matching; cmap[v] = coarse vertex of v
+Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<int32_t> &cmap) {
+  const int32_t n = g.n;
+  std::vector<int32_t> order(n), match(n, -1);
+  std::iota(order.begin(), order.end(), 0);
+  std::shuffle(order.begin(), order.end(), rng);
+  for (int32_t v : order) {
+    if (match[v] != -1) continue;
+    int32_t best = -1;
+    double bw = -1.0;
+    for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+      const int32_t u = g.adj[q];
+      if (match[u] == -1 && u != v && g.vw[u] + g.vw[v] <= maxvw && g.w[q] > bw) {
+        bw = g.w[q];
+        best = u;
+      }
+    }
+    if (best >= 0) {
+      match[v] = best;
+      match[best] = v;
+    } else {
+      match[v] = v;
+    }
+  }
+  cmap.assign(n, -1);
+  int32_t nc = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (cmap[v] == -1) {
+      cmap[v] = nc;
+      cmap[match[v]] = nc;
+      ++nc;
+    }
+  Graph c;
+  c.n = nc;
+  c.vw.assign(nc, 0);
+  std::vector<int32_t> rep(nc, -1);
+  for (int32_t v = 0; v < n; ++v) {
+    c.vw[cmap[v]] += g.vw[v];
+    if (rep[cmap[v]] == -1) rep[cmap[v]] = v;
+  }
+  c.xadj.assign(nc + 1, 0);
+  std::vector<int32_t> mark(nc, -1), list;
+  std::vector<double> acc(nc, 0.0);
+  for (int32_t cv = 0; cv < nc; ++cv) {
+    list.clear();
+    const int32_t a = rep[cv], b = match[a];
+    for (int32_t v : {a, b}) {
+      if (v == b && b == a) continue;
+      for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+        const int32_t cu = cmap[g.adj[q]];
+        if (cu == cv) continue;
+        if (mark[cu] != cv) {
+          mark[cu] = cv;
+          acc[cu] = 0.0;
+          list.push_back(cu);
+        }
+        acc[cu] += g.w[q];
+      }
+    }
+    std::sort(list.begin(), list.end());
+    for (int32_t cu : list) {
+      c.adj.push_back(cu);
+      c.w.push_back(acc[cu]);
+    }
+    c.xadj[cv + 1] = (int64_t)c.adj.size();
+  }
+  return c;
+}
+
+// cut of a partition
+double cut_of(const Graph &g, const std::vector<int32_t> &part) {
+  double s = 0;
+  for (int32_t v = 0; v < g.n; ++v)
+    for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q)
+      if (g.adj[q] > v && part[g.adj[q]] != part[v]) s += g.w[q];
+  return s;
+}
+
+// Bisect the vertex subset `vs` (part ids p0 / p1) so that side 0 weighs about target0:
+// greedy growing from a pseudo-peripheral vertex, then FM-style passes of single moves.
+void bisect(const Graph &g, const std::vector<int32_t> &vs, double target0, int32_t p0, int32_t p1,
+            std::vector<int32_t> &part, std::mt19937_64 &rng) {
+  if (vs.empty()) return;
+  std::vector<int32_t> local(g.n, -1);
+  for (size_t i = 0; i < vs.size(); ++i) local[vs[i]] = (int32_t)i;
+  const size_t m = vs.size();
+  // pseudo-peripheral seed: farthest vertex (BFS) from a random start, twice
+  auto bfs_far = [&](int32_t s) {
+    std::vector<int32_t> dist(m, -1), q;
+    q.push_back(s);
+    dist[local[s]] = 0;
+    int32_t last = s;
+    for (size_t h = 0; h < q.size(); ++h) {
+      const int32_t v = q[h];
+      last = v;
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+        const int32_t u = g.adj[e];
+        if (local[u] >= 0 && dist[local[u]] < 0) {
+          dist[local[u]] = dist[local[v]] + 1;
+          q.push_back(u);
+        }
+      }
+    }
+    return last;
+  };
+  int32_t seed = vs[rng() % m];
+  seed = bfs_far(bfs_far(seed));
+  // greedy growing: add the frontier vertex with the largest (internal - external) gain
+  std::vector<char> in(m, 0);
+  std::vector<double> conn(m, 0.0);  // edge weight from a vertex to the grown region
+  double wgrown = 0;
+  std::vector<int32_t> frontier;
+  auto add = [&](int32_t v) {
+    in[local[v]] = 1;
+    wgrown += g.vw[v];
+    for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+      const int32_t u = g.adj[e];
+      if (local[u] >= 0 && !in[local[u]]) {
+        if (conn[local[u]] == 0.0) frontier.push_back(u);
+        conn[local[u]] += g.w[e];
+      }
+    }
+  };
+  add(seed);
+  size_t next_unvisited = 0;
+  while (wgrown < target0) {
+    int32_t best = -1;
+    double bg = -1e300;
+    size_t bi = 0;
+    for (size_t i = 0; i < frontier.size(); ++i) {
+      const int32_t u = frontier[i];
+      if (in[local[u]]) continue;
+      double tot = 0;
+      for (int64_t e = g.xadj[u]; e < g.xadj[u + 1]; ++e)
+        if (local[g.adj[e]] >= 0) tot += g.w[e];
+      const double gain = 2 * conn[local[u]] - tot;
+      if (gain > bg) {
+        bg = gain;
+        best = u;
+        bi = i;
+      }
+    }
+    if (best < 0) {  // disconnected remainder: restart from any vertex not yet grown
+      while (next_unvisited < m && in[next_unvisited]) ++next_unvisited;
+      if (next_unvisited >= m) break;
+      best = vs[next_unvisited];
+    } else {
+      frontier[bi] = frontier.back();
+      frontier.pop_back();
+    }
+    if (wgrown + g.vw[best] > target0 + 0.5 * g.vw[best] && wgrown > 0) break;
+    add(best);
+    if (frontier.size() > 4096) {  // keep the scan cheap: drop stale entries
+      std::vector<int32_t> f2;
+      for (int32_t u : frontier)
+        if (!in[local[u]]) f2.push_back(u);
+      frontier.swap(f2);
+    }
+  }
+  for (size_t i = 0; i < m; ++i) part[vs[i]] = in[i] ? p0 : p1;
+  // FM-style refinement: single moves with positive gain that keep the balance within 2%
+  double w0 = 0, wtot = 0;
+  for (int32_t v : vs) {
+    wtot += g.vw[v];
+    if (part[v] == p0) w0 += g.vw[v];
+  }
+  const double tol = std::max(2.0, 0.02 * wtot);
+  for (int pass = 0; pass < 6; ++pass) {
+    int moved = 0;
+    for (int32_t v : vs) {
+      double ext = 0, intw = 0;
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+        const int32_t u = g.adj[e];
+        if (local[u] < 0) continue;
+        (part[u] == part[v] ? intw : ext) += g.w[e];
+      }
+      if (ext <= intw) continue;
+      const bool to1 = part[v] == p0;
+      const double nw0 = w0 + (to1 ? -g.vw[v] : g.vw[v]);
+      if (std::fabs(nw0 - target0) > tol && std::fabs(nw0 - target0) >= std::fabs(w0 - target0))
+        continue;
+      part[v] = to1 ? p1 : p0;
+      w0 = nw0;
+      ++moved;
+    }
+    if (!moved) break;
+  }
+}
+
+void recursive_bisection(const Graph &g, const std::vector<int32_t> &vs, int32_t k0, int32_t K,
+                         std::vector<int32_t> &part, std::mt19937_64 &rng) {
+  if (K <= 1 || vs.empty()) {
+    for (int32_t v : vs) part[v] = k0;
+    return;
+  }
+  const int32_t K1 = K / 2;
+  double w = 0;
+  for (int32_t v : vs) w += g.vw[v];
+  bisect(g, vs, w * K1 / K, k0, k0 + K1, part, rng);
+  std::vector<int32_t> a, b;
+  for (int32_t v : vs) (part[v] == k0 ? a : b).push_back(v);
+  recursive_bisection(g, a, k0, K1, part, rng);
+  recursive_bisection(g, b, k0 + K1, K - K1, part, rng);
+}
+
+// balance-constrained greedy k-way refinement of the boundary
+void refine_kway(const Graph &g, std::vector<int32_t> &part, int32_t K, double cap,
+                 std::mt19937_64 &rng, int passes) {
+  std::vector<double> size(K, 0.0);
+  for (int32_t v = 0; v < g.n; ++v) size[part[v]] += g.vw[v];
+  std::vector<int32_t> order(g.n);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> conn(K, 0.0);
+  std::vector<int32_t> touched;
+  for (int pass = 0; pass < passes; ++pass) {
+    std::shuffle(order.begin(), order.end(), rng);
+    int moved = 0;
+    for (int32_t v : order) {
+      const int32_t pv = part[v];
+      touched.clear();
+      bool boundary = false;
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+        const int32_t p = part[g.adj[e]];
+        if (conn[p] == 0.0) touched.push_back(p);
+        conn[p] += g.w[e];
+        boundary |= p != pv;
+      }
+      if (boundary) {
+        int32_t best = -1;
+        double bgain = 0.0;
+        for (int32_t p : touched) {
+          if (p == pv || size[p] + g.vw[v] > cap) continue;
+          const double gain = conn[p] - conn[pv];
+          if (gain > bgain) {
+            bgain = gain;
+            best = p;
+          }
+        }
+        if (best >= 0) {
+          part[v] = best;
+          size[pv] -= g.vw[v];
+          size[best] += g.vw[v];
+          ++moved;
+        }
+      }
+      for (int32_t p : touched) conn[p] = 0.0;
+    }
+    if (!moved) break;
+  }
+}
+
+// move vertices out of parts above the cap, cheapest loss first, preferring parts they
+// touch; a part with no such neighbour sends its vertex to the lightest part
+void enforce_cap(const Graph &g, std::vector<int32_t> &part, int32_t K, int32_t cap) {
+  std::vector<int64_t> size(K, 0);
+  for (int32_t v = 0; v < g.n; ++v) size[part[v]] += 1;
+  std::vector<double> conn(K, 0.0);
+  std::vector<int32_t> touched;
+  for (int round = 0; round < 64; ++round) {
+    bool over = false;
+    for (int32_t k = 0; k < K; ++k) over |= size[k] > cap;
+    if (!over) return;
+    for (int32_t v = 0; v < g.n; ++v) {
+      const int32_t pv = part[v];
+      if (size[pv] <= cap) continue;
+      touched.clear();
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+        const int32_t p = part[g.adj[e]];
+        if (conn[p] == 0.0) touched.push_back(p);
+        conn[p] += g.w[e];
+      }
+      int32_t best = -1;
+      double bl = 1e300;
+      for (int32_t p : touched)
+        if (p != pv && size[p] < cap && conn[pv] - conn[p] < bl) {
+          bl = conn[pv] - conn[p];
+          best = p;
+        }
+      // only cheap moves in the early rounds, anything later
+      if (best >= 0 && (round >= 2 || bl <= 0.25 * (conn[pv] + 1e-300) + 1e-12)) {
+        part[v] = best;
+        --size[pv];
+        ++size[best];
+      }
+      for (int32_t p : touched) conn[p] = 0.0;
+    }
+  }
+  // last resort: fill the lightest parts
+  for (int32_t v = 0; v < g.n; ++v) {
+    const int32_t pv = part[v];
+    if (size[pv] <= cap) continue;
+    int32_t lo = (int32_t)(std::min_element(size.begin(), size.end()) - size.begin());
+    part[v] = lo;
+    --size[pv];
+    ++size[lo];
+  }
+}
+
+// reverse Cuthill-McKee order of the vertices of one part (on its induced subgraph)
+void rcm_order(const Graph &g, const std::vector<int32_t> &vs, std::vector<int32_t> &out,
+               std::vector<int32_t> &local) {
+  const size_t m = vs.size();
+  for (size_t i = 0; i < m; ++i) local[vs[i]] = (int32_t)i;
+  std::vector<int32_t> deg(m, 0);
+  for (size_t i = 0; i < m; ++i)
+    for (int64_t e = g.xadj[vs[i]]; e < g.xadj[vs[i] + 1]; ++e) deg[i] += local[g.adj[e]] >= 0;
+  std::vector<char> seen(m, 0);
+  std::vector<int32_t> order;
+  order.reserve(m);
+  std::vector<int32_t> nb;
+  for (size_t start = 0; order.size() < m;) {
+    // start of the next component: unseen vertex of minimum degree, then a BFS-far vertex
+    int32_t s = -1;
+    for (size_t i = 0; i < m; ++i)
+      if (!seen[i] && (s < 0 || deg[i] < deg[s])) s = (int32_t)i;
+    auto bfs = [&](int32_t root, bool commit) {
+      std::vector<int32_t> q{root};
+      std::vector<char> vis(m, 0);
+      vis[root] = 1;
+      for (size_t h = 0; h < q.size(); ++h) {
+        const int32_t v = q[h];
+        nb.clear();
+        for (int64_t e = g.xadj[vs[v]]; e < g.xadj[vs[v] + 1]; ++e) {
+          const int32_t u = local[g.adj[e]];
+          if (u >= 0 && !vis[u] && !seen[u]) {
+            vis[u] = 1;
+            nb.push_back(u);
+          }
+        }
+        std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+          return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+        });
+        q.insert(q.end(), nb.begin(), nb.end());
+      }
+      if (commit)
+        for (int32_t v : q) {
+          seen[v] = 1;
+          order.push_back(v);
+        }
+      return q.back();
+    };
+    const int32_t far = bfs(s, false);
+    bfs(far, true);
+    (void)start;
+  }
+  out.clear();
+  for (size_t i = m; i-- > 0;) out.push_back(vs[order[i]]);
+  for (size_t i = 0; i < m; ++i) local[vs[i]] = -1;
+}
+
+}  // namespace
+
+extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_t *cci,
+                                     const double *ccv, int32_t K, int32_t cap, uint64_t seed,
+                                     int32_t *perm, int64_t *block_ptr, double *cutsize) {
+  if (n <= 0 || !crp || !cci || !ccv || !perm || !block_ptr || K < 1 || K > n ||
+      (int64_t)cap * K < n)
+    return CIMMINO_EINVAL;
+  try {
+    std::mt19937_64 rng(seed);
+    std::vector<Graph> levels;
+    std::vector<std::vector<int32_t>> maps;
+    levels.push_back(build_rip(n, crp, cci, ccv));
+    // coarsen until a few dozen vertices per part remain
+    const int32_t maxvw = std::max(1, cap / 32);
+    while (levels.back().n > std::max<int64_t>(40LL * K, 2000)) {
+      std::vector<int32_t> cmap;
+      Graph c = coarsen(levels.back(), maxvw, rng, cmap);
+      if (c.n > 0.92 * levels.back().n) break;
+      maps.push_back(std::move(cmap));
+      levels.push_back(std::move(c));
+    }
+    // initial partition of the coarsest graph
+    const Graph &gc = levels.back();
+    std::vector<int32_t> part(gc.n, 0), all(gc.n);
+    std::iota(all.begin(), all.end(), 0);
+    recursive_bisection(gc, all, 0, K, part, rng);
+    // uncoarsen with refinement; the cap loosens toward the coarse levels
+    for (int lvl = (int)levels.size() - 1; lvl >= 0; --lvl) {
+      const Graph &g = levels[lvl];
+      const double slack = lvl == 0 ? 1.0 : 1.0 + 0.03 * lvl;
+      refine_kway(g, part, K, cap * slack, rng, 8);
+      if (lvl > 0) {
+        std::vector<int32_t> fine(levels[lvl - 1].n);
+        for (int32_t v = 0; v < levels[lvl - 1].n; ++v) fine[v] = part[maps[lvl - 1][v]];
+        part.swap(fine);
+      }
+    }
+    const Graph &g = levels.front();
+    enforce_cap(g, part, K, cap);
+    refine_kway(g, part, K, cap, rng, 4);
+    // every part must hold at least one row: borrow from the largest parts
+    std::vector<int64_t> size(K, 0);
+    for (int64_t v = 0; v < n; ++v) ++size[part[v]];
+    for (int32_t k = 0; k < K; ++k)
+      while (size[k] == 0) {
+        const int32_t big = (int32_t)(std::max_element(size.begin(), size.end()) - size.begin());
+        for (int64_t v = 0; v < n; ++v)
+          if (part[v] == big) {
+            part[v] = k;
+            --size[big];
+            ++size[k];
+            break;
+          }
+      }
+    if (cutsize) *cutsize = cut_of(g, part);
+    // decode: parts in order, RCM inside each part
+    std::vector<std::vector<int32_t>> members(K);
+    for (int64_t v = 0; v < n; ++v) members[part[v]].push_back((int32_t)v);
+    std::vector<int32_t> local(n, -1), ord;
+    int64_t o = 0;
+    block_ptr[0] = 0;
+    for (int32_t k = 0; k < K; ++k) {
+      rcm_order(g, members[k], ord, local);
+      for (int32_t v : ord) perm[o++] = v;
+      block_ptr[k + 1] = o;
+    }
+    return CIMMINO_OK;
+  } catch (...) {
+    return CIMMINO_ENOMEM;
+  }
+}
