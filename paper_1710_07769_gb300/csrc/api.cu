@@ -472,7 +472,14 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   void *dinv = fp64 ? (void *)c->dinv64.p : (void *)c->dinv32.p;
   launch_gram_scatter(c->blk.p, blist.p, nblk, c->trow.p, c->brp.p, c->bci.p, c->bcv.p, fac,
                       fp64, s);
-  launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, fac, dinv, fp64, pmin.p, pfail.p, s);
+  if (fp64) {
+    launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, fac, dinv, 1, pmin.p, pfail.p, s);
+  } else {
+    c->err_flag.alloc(1);
+    CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
+    launch_cholesky_tc(c->blk.p, blist.p, nblk, c->trow.p, c->fac32.p, c->dinv32.p, pmin.p,
+                       pfail.p, c->err_flag.p, s);
+  }
   c->setup_launches += 2;  // scatter, Cholesky
   CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> hfail(nblk);
@@ -632,7 +639,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   if (c->proj_slots < 2) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
   c->proj_smem = proj_smem_bytes(c->max_mp, c->proj_slots, c->proj_slot_bytes, c->proj_wbytes);
   set_proj_smem_attr(c->proj_smem);
-  c->err_flag.alloc(1);
+  if (!c->err_flag.p) c->err_flag.alloc(1);
   CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));

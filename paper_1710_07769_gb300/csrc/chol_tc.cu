@@ -1,0 +1,356 @@
+// Batched Cholesky of FP32 Gram blocks with the trailing update on the tensor cores.
+//
+// Same right-looking tile algorithm (and the same stored form L = diag(L_II)(I + N)) as
+// the CUDA-core kernel in chol_kernels.cu; only step 4, the trailing update
+//     G_IJ -= L_IK L_JK^T     for K < J <= I,
+// the one dense contraction of the method, runs as tcgen05 MMAs:
+//   * A = [L_{I0,K}; L_{I0+1,K}] (128 x 64, two tile rows), B = [L_{J0,K}; L_{J0+1,K}]
+//     (128 x 64, two tile columns), D = A B^T (128 x 128, FP32) in tensor memory;
+//   * 3xTF32 for FP32-level accuracy: x = hi + lo with hi = x rounded to TF32 and
+//     lo = x - hi, D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the TF32 operands are
+//     read from shared memory in the canonical no-swizzle K-major layout: 8-row x
+//     16-byte core matrices, 128 bytes apart along K, 2048 bytes apart along rows);
+//   * one thread issues the 24 MMAs (K = 8 each) and commits them to an mbarrier; the
+//     8 warps read D back with tcgen05.ld (warp w: lanes 32 (w mod 4).., half of the
+//     columns) and subtract it from the tiles in global memory.
+// Tiles outside the envelope read as zero and are never written.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace cimmino {
+
+namespace {
+
+constexpr int T = kTile;
+constexpr int kThreads = 256;
+constexpr int LDS = T + 1;  // padded row-major diagonal tile
+constexpr int LD = T + 4;   // k-major operand tiles of the CUDA-core steps
+constexpr uint32_t kCoreK = 128;    // bytes between core matrices along K
+constexpr uint32_t kCoreRow = 2048; // bytes between 8-row groups (16 core matrices of K = 64)
+constexpr uint32_t kTmemCols = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(kCoreK >> 4) << 16;    // leading (K) byte offset
+  d |= (uint64_t)(kCoreRow >> 4) << 32;  // stride (row) byte offset
+  d |= (uint64_t)1 << 46;                // descriptor version; no swizzle
+  return d;
+}
+// D f32, A/B tf32, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+// byte offset of element (r, k) of a 128 x 64 operand in the canonical layout
+__device__ __forceinline__ uint32_t canon(int r, int k) {
+  return (uint32_t)((r >> 3) * kCoreRow + (k >> 2) * kCoreK + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+// Fill rows [64 half, 64 half + 64) of a hi/lo operand pair from a row-major tile (or zeros).
+__device__ __forceinline__ void load_split(const float *__restrict__ g, unsigned char *hi,
+                                           unsigned char *lo, int half) {
+  for (int e = threadIdx.x; e < T * T; e += kThreads) {
+    const int r = e / T, k = e % T;
+    const float x = g ? g[e] : 0.f;
+    const float h = tf32_hi(x);
+    const uint32_t o = canon(64 * half + r, k);
+    *reinterpret_cast<float *>(hi + o) = h;
+    *reinterpret_cast<float *>(lo + o) = x - h;
+  }
+}
+
+__device__ __forceinline__ float *tile_ptr(float *fac, const TileRow &tr, int J) {
+  return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,"
+      "%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,"
+      "%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]),
+        "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]),
+        "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]),
+        "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// acc(r, c) for the thread's 4 x 4 block: sum_k At[k][r] * Bt[k][c] (CUDA cores)
+__device__ __forceinline__ void mma_4x4(const float *At, const float *Bt, float acc[4][4]) {
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+#pragma unroll 8
+  for (int k = 0; k < T; ++k) {
+    float a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = At[k * LD + tr * 4 + i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Bt[k * LD + tc * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_cholesky_tc(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
+                  const TileRow *__restrict__ trow, float *__restrict__ fac,
+                  float *__restrict__ dinv, double *__restrict__ pivmin,
+                  int32_t *__restrict__ pivfail, int32_t *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *Ahi = smem_raw;          // 128 x 64 TF32 operands, 32 KB each
+  unsigned char *Alo = Ahi + 32768;
+  unsigned char *Bhi = Alo + 32768;
+  unsigned char *Blo = Bhi + 32768;
+  float *At = reinterpret_cast<float *>(Blo + 32768);  // [T][LD]
+  float *Bt = At + T * LD;                             // [T][LD]
+  float *S = Bt + T * LD;                              // [T][LDS]
+  float *Di = S + T * LDS;                             // [T][LDS]
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ double s_pmin;
+  __shared__ int s_fail, s_err;
+
+  const int b = blist[blockIdx.x];
+  const BlockDesc B = blk[b];
+  const TileRow *tr = trow + B.trow0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tr4 = tid / 16, tc4 = tid % 16;
+  if (tid == 0) {
+    s_pmin = 1e300;
+    s_fail = 0;
+    s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+
+  for (int K = 0; K < B.nt && !s_err; ++K) {
+    const TileRow TK = tr[K];
+    float *gKK = tile_ptr(fac, TK, K);
+    // ---- 1. diagonal tile (CUDA cores)
+    for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
+    __syncthreads();
+    for (int j = 0; j < T; ++j) {
+      if (tid == 0) {
+        float dj = S[j * LDS + j];
+        if (K * T + j < B.m) s_pmin = fmin(s_pmin, (double)dj);
+        if (!(dj > 0.f) || !isfinite(dj)) {
+          s_fail = 1;
+          dj = 1.f;
+        }
+        S[j * LDS + j] = sqrtf(dj);
+      }
+      __syncthreads();
+      const float ljj = S[j * LDS + j];
+      for (int i = j + 1 + tid; i < T; i += kThreads) S[i * LDS + j] = S[i * LDS + j] / ljj;
+      __syncthreads();
+      const int w = T - j - 1;
+      for (int e = tid; e < w * w; e += kThreads) {
+        int i = j + 1 + e / w, k = j + 1 + e % w;
+        if (k <= i) S[i * LDS + k] = fmaf(-S[i * LDS + j], S[k * LDS + j], S[i * LDS + k]);
+      }
+      __syncthreads();
+    }
+    // ---- 2. inv(L_KK)
+    if (tid < T) {
+      const int c = tid;
+      for (int i = 0; i < c; ++i) Di[i * LDS + c] = 0.f;
+      Di[c * LDS + c] = 1.f / S[c * LDS + c];
+      for (int i = c + 1; i < T; ++i) {
+        float s = 0.f;
+        for (int k = c; k < i; ++k) s = fmaf(S[i * LDS + k], Di[k * LDS + c], s);
+        Di[i * LDS + c] = -s / S[i * LDS + i];
+      }
+    }
+    __syncthreads();
+    float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+    for (int e = tid; e < T * T; e += kThreads) {
+      int r = e / T, c = e % T;
+      gKK[e] = c <= r ? S[r * LDS + c] : 0.f;
+      dK[e] = c <= r ? Di[r * LDS + c] : 0.f;
+    }
+    // N_KJ = inv(L_KK) L_KJ for the final row K (CUDA cores)
+    for (int e = tid; e < T * T; e += kThreads) {
+      int k = e / T, r = e % T;
+      At[k * LD + r] = Di[r * LDS + k];
+    }
+    for (int J = TK.j0; J < K; ++J) {
+      float *gKJ = tile_ptr(fac, TK, J);
+      __syncthreads();
+      for (int e = tid; e < T * T; e += kThreads) Bt[(e / T) * LD + (e % T)] = gKJ[e];
+      __syncthreads();
+      float acc[4][4] = {};
+      mma_4x4(At, Bt, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gKJ[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+    }
+    __syncthreads();
+    // ---- 3. L_IK = G_IK inv(L_KK)^T (CUDA cores)
+    for (int e = tid; e < T * T; e += kThreads) {
+      int k = e / T, c = e % T;
+      Bt[k * LD + c] = Di[c * LDS + k];
+    }
+    __syncthreads();
+    for (int I = K + 1; I < B.nt; ++I) {
+      const TileRow TI = tr[I];
+      if (TI.j0 > K) continue;
+      float *gIK = tile_ptr(fac, TI, K);
+      for (int e = tid; e < T * T; e += kThreads) At[(e % T) * LD + (e / T)] = gIK[e];
+      __syncthreads();
+      float acc[4][4] = {};
+      mma_4x4(At, Bt, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gIK[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+      __syncthreads();
+    }
+    // ---- 4. trailing update on the tensor cores: pairs of tile rows x pairs of tile columns
+    for (int I0 = K + 1; I0 < B.nt && !s_err; I0 += 2) {
+      const int I1 = I0 + 1;
+      const bool has0 = tr[I0].j0 <= K;
+      const bool has1 = I1 < B.nt && tr[I1].j0 <= K;
+      if (!has0 && !has1) continue;
+      load_split(has0 ? tile_ptr(fac, tr[I0], K) : nullptr, Ahi, Alo, 0);
+      load_split(has1 ? tile_ptr(fac, tr[I1], K) : nullptr, Ahi, Alo, 1);
+      const int jmax = has1 ? I1 : I0;
+      for (int J0 = K + 1; J0 <= jmax && !s_err; J0 += 2) {
+        const int J1 = J0 + 1;
+        const bool hj0 = tr[J0].j0 <= K;
+        const bool hj1 = J1 <= jmax && J1 < B.nt && tr[J1].j0 <= K;
+        if (!hj0 && !hj1) continue;
+        load_split(hj0 ? tile_ptr(fac, tr[J0], K) : nullptr, Bhi, Blo, 0);
+        load_split(hj1 ? tile_ptr(fac, tr[J1], K) : nullptr, Bhi, Blo, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+          const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi),
+                         bl = smem_u32(Blo);
+          for (int s = 0; s < T / 8; ++s) {
+            const uint32_t ko = s * 2 * kCoreK;  // K = 8 per MMA: two core matrices
+            mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), s > 0);
+            mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), 1);
+            mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), 1);
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&mbar))
+              : "memory");
+        }
+        {  // bounded wait for the MMAs
+          uint32_t ok = 0;
+          const uint64_t t0 = global_ns();
+          while (!ok) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(smem_u32(&mbar)), "r"(phase)
+                : "memory");
+            if (!ok && global_ns() - t0 > kWaitNs) {
+              s_err = 1;
+              atomicOr(err, 4);
+              break;
+            }
+          }
+          phase ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads lanes 32 (w mod 4).., column half w / 4 (= tile column)
+        {
+          const int rowq = warp & 3, jh = warp >> 2;
+          const int rr = 32 * rowq + lane;            // row of D
+          const int I = rr < 64 ? I0 : I1, J = jh ? J1 : J0;
+          const bool hasI = rr < 64 ? has0 : has1, hasJ = jh ? hj1 : hj0;
+          float v[64];
+          tmem_ld64(tmem + ((uint32_t)(32 * rowq) << 16) + (uint32_t)(64 * jh), v);
+          if (hasI && hasJ && J <= I && !s_err) {
+            float *g = tile_ptr(fac, tr[I], J) + (rr & 63) * T;
+#pragma unroll
+            for (int c = 0; c < 64; ++c) g[c] -= v[c];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    pivmin[b] = s_pmin;
+    pivfail[b] = s_fail | s_err;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+constexpr int kTcSmem = 4 * 32768 + (int)sizeof(float) * (2 * T * LD + 2 * T * LDS);
+
+}  // namespace
+
+void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                        const TileRow *trow, float *fac, float *dinv, double *pivmin,
+                        int32_t *pivfail, int32_t *err, cudaStream_t s) {
+  if (nlist <= 0) return;
+  cudaFuncSetAttribute(k_cholesky_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  k_cholesky_tc<<<(unsigned)nlist, kThreads, kTcSmem, s>>>(blk, blist, trow, fac, dinv, pivmin,
+                                                           pivfail, err);
+}
+
+}  // namespace cimmino

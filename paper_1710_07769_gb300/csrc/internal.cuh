@@ -191,6 +191,11 @@ struct FactorPtrs {
   double *dinvT64;
 };
 
+// chol_tc.cu: FP32 blocks, trailing update on the tensor cores (tcgen05, 3xTF32)
+void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                        const TileRow *trow, float *fac, float *dinv, double *pivmin,
+                        int32_t *pivfail, int32_t *err, cudaStream_t s);
+
 // chol_kernels.cu
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
                              const TileRow *trowT, const FactorPtrs &f, cudaStream_t s);
