@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 rel. residual & HBM GB/s per CG iter; FP32+refine vs FP64 on GB300"
 TOL = 1e-10
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (recipe table); the FMA probe measured 1.196
+# DRAM bytes per k_proj launch from one ncu capture of the current kernel (ncu
+# --set full, 64^3 workload, CG iteration 1; profiles/k_proj_convdiff3d_64.md)
+PROJ_TRAFFIC = {"fp64": 785754112, "fp32": 856875008}
 
 
 def peaks():
@@ -99,10 +103,10 @@ class Clocks:
 def algorithmic_bytes(n, nnz, factor_bytes, w_factor, refine_mean, nnz_bd):
     """Minimum bytes one CG iteration must move (1 right-hand side).
 
-    projection: every stored factor tile (off-diagonal tiles + inverted diagonal
-      tiles = factor_bytes of the same precision) is read once by the forward and
-      once by the backward solve, times (1 + refinement steps); each refinement
-      step also reads the exact Gram block (12 B per entry); u read, y written.
+    projection: one solve pass streams pass_bytes = 2 x factor_bytes (N tiles and
+      inv(L_II) for the forward solve, their transposed copies for the backward
+      solve), times (1 + refinement steps); each refinement step also reads the
+      exact Gram block (12 B per entry); u read, y written.
     u = A p with the residual of x: CSR (12 B/entry + 8 B/row), p and x gathered,
       f_s and d read, u written.
     psi = A^T y with p^T psi: transpose (12 B/entry + 8 B/column), y gathered,
@@ -215,7 +219,7 @@ def run_ours(args, rank, local):
         refine_mean = st["refine_steps_total"] / max(1, nblk * (launches + 1))
         wf = 8 if st is st64 else 4
         # the exact Gram blocks have ~25 entries per row for the 7-point stencil
-        b = algorithmic_bytes(n, A.nnz, st["factor_bytes"], wf, refine_mean, 25 * n)
+        b = algorithmic_bytes(n, A.nnz, st["pass_bytes"] / 2, wf, refine_mean, 25 * n)
         it_ms = st["t_solve_ms"] / max(1, st["iters"] + 1)
         return {"time_to_solution_ms": sum(t_steps) / len(t_steps), "iters": st["iters"],
                 "rel_res": st["rel_res"], "backward_err": st["backward_err"],
@@ -225,18 +229,27 @@ def run_ours(args, rank, local):
                 "proj_ms": kt["proj_ms"], "proj_bytes": b["proj"],
                 "proj_gbps": b["proj"] / (kt["proj_ms"] * 1e-3) / 1e9,
                 "refine_steps_mean": refine_mean, "fallbacks": st["fallbacks"],
-                "factor_bytes": st["factor_bytes"], "kernel_launches": st["kernel_launches"]}
+                "factor_bytes": st["factor_bytes"], "pass_bytes": st["pass_bytes"],
+                "kernel_launches": st["kernel_launches"]}
 
     r64 = per_iter(st64, kt64, t64)
     r32 = per_iter(st32, kt32, t32)
     s64.close()
     s32.close()
-    dom = r64
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    roof = {"bound": "hbm", "achieved": round(dom["proj_gbps"], 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(dom["proj_gbps"] / hbm, 4), "traffic": None,
-            "kernel": "k_proj (FP64 tile solves)",
-            "peak_source": "measured" if "fallback" not in pk else "fallback"}
+    # FP64 projection: every streamed FP64 factor element feeds one FMA, so it is bound by
+    # GB300's FP64 pipe (ncu: FP64 pipe 75% / DRAM 35% busy); FP32 projection: HBM-bound.
+    flops64 = st64["pass_bytes"] / 4.0           # 2 flops per 8-byte element, one pass
+    tf64 = flops64 / (kt64["proj_ms"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": round(tf64 / FP64_PEAK_TFLOPS, 4),
+            "traffic": PROJ_TRAFFIC.get("fp64"), "kernel": "k_proj (FP64 tile solves)",
+            "peak_source": "nominal FP64 1.25 TFLOP/s (probe measured 1.196)",
+            "hbm_view": {"achieved_gbs": round(r64["proj_gbps"], 1), "frac": round(r64["proj_gbps"] / hbm, 4)}}
+    roof32 = {"bound": "hbm", "achieved": round(r32["proj_gbps"], 1), "peak": hbm, "unit": "GB/s",
+              "frac": round(r32["proj_gbps"] / hbm, 4), "traffic": PROJ_TRAFFIC.get("fp32"),
+              "kernel": "k_proj (FP32 tile solves + FP64 refinement)",
+              "peak_source": "measured" if "fallback" not in pk else "fallback"}
     out = {
         "metric": METRIC, "value": round(ms_step, 3), "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -249,6 +262,7 @@ def run_ours(args, rank, local):
         "fp64": r64, "fp32_refine": r32,
         "fp32_vs_fp64_time_ratio": round(r32["time_to_solution_ms"] / r64["time_to_solution_ms"], 4),
         "roofline": roof,
+        "roofline_fp32": roof32,
         "e2e": {"value": round(min(e2e_t), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(st64["kernel_launches"]) * args.steps,
@@ -274,6 +288,7 @@ def cpu_sample(config, nthreads=None, iters_sample=10, full_iters=None):
     full = full_iters if full_iters is not None else it
     est_ms = (t_setup + full * t_it) * 1e3
     return {"value": round(est_ms, 1), "unit": "ms", "cores": nthreads, "kind": "oracle",
+            "workload": w.name,
             "sample": f"{w.name}: full oracle setup ({t_setup:.1f} s) + {it} CG iterations "
                       f"({t_it * 1e3:.1f} ms each) extrapolated to {full} iterations"}
 
@@ -318,7 +333,8 @@ def main():
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": f"config {args.config}"},
+                          "config": {"workload": cb.pop("workload"), "partition": "contiguous",
+                                     "tol": TOL, "precision": "fp64"},
                           "cpu_baseline": cb,
                           "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
@@ -329,7 +345,9 @@ def main():
     out = run_ours(args, rank, local)
     if rank == 0:
         if not args.no_cpu:
-            out["cpu_baseline"] = cpu_sample(args.config, full_iters=out["fp64"]["iters"])
+            cb = cpu_sample(args.config, full_iters=out["fp64"]["iters"])
+            cb.pop("workload")
+            out["cpu_baseline"] = cb
         print(json.dumps(out))
     if args.gpus > 1:
         import torch

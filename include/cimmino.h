@@ -21,9 +21,10 @@
  *    the last failure of a context is available from cimmino_last_error().
  *  - Device pointers refer to the CUDA device that is current when
  *    cimmino_setup() is called; the context stays bound to that device.
- *  - All device work is ordered on opts.stream (a cudaStream_t; NULL selects
- *    the legacy default stream).  Every call returns after its results are
- *    complete, i.e. calls synchronise the stream before returning.
+ *  - All device work of a context is ordered on opts.stream (a cudaStream_t).
+ *    With opts.stream == NULL the context creates, and later destroys, a
+ *    non-blocking stream of its own.  Every call returns after its results are
+ *    complete, i.e. calls synchronise that stream before returning.
  *  - A context may be used by one host thread at a time.  There is no global
  *    mutable state: independent contexts may be used concurrently.
  */
@@ -87,7 +88,7 @@ typedef struct cimmino_opts {
   int32_t use_graph;      /* 1 (default): capture CG iterations as a CUDA graph     */
   int32_t check_every;    /* CG iterations between convergence read-backs (def. 8)  */
   int32_t keep_aat;       /* 1: keep C = A A^T for cimmino_get_aat() (default 0)    */
-  void *stream;           /* cudaStream_t for all device work (NULL: default)      */
+  void *stream;           /* cudaStream_t for all device work (NULL: own stream)   */
 } cimmino_opts;
 
 /* Statistics of one right-hand side of one system. */
