@@ -88,6 +88,9 @@ typedef struct cimmino_opts {
   int32_t use_graph;      /* 1 (default): capture CG iterations as a CUDA graph     */
   int32_t check_every;    /* CG iterations between convergence read-backs (def. 8)  */
   int32_t keep_aat;       /* 1: keep C = A A^T for cimmino_get_aat() (default 0)    */
+  int32_t multi_rhs;      /* 1 (default): with several right-hand sides, groups of  */
+                          /* 8 or 16 share every factor tile read; 0: one factor    */
+                          /* pass per right-hand side                               */
   void *stream;           /* cudaStream_t for all device work (NULL: own stream)   */
 } cimmino_opts;
 
@@ -184,13 +187,21 @@ int cimmino_block_rows(cimmino_ctx *ctx, int32_t b, int32_t *m);
  * converted to double; *is_fp64 tells which precision the block was factored in. */
 int cimmino_get_factor(cimmino_ctx *ctx, int32_t b, double *L, int32_t *is_fp64);
 
-/* One projection sum psi = H v = sum_i A_i^+ A_i v (Eq. 1.5) of a single-system
- * context, with the same kernels (and refinement) as the CG iterations; v and psi
- * are n-vectors in the original column order (host or device as on_device says). */
-int cimmino_project(cimmino_ctx *ctx, const double *v, double *psi, int32_t on_device);
+/* Projection sums psi_k = H v_k = sum_i A_i^+ A_i v_k (Eq. 1.5), k < nrhs, of a
+ * single-system context, with the same kernels (and refinement) as CG iterations
+ * with nrhs right-hand sides: for nrhs > 1 and opts.multi_rhs, groups of
+ * right-hand sides share every factor tile read.  v and psi are nrhs x n arrays
+ * (vector k at offset k * n) in the original column order, host or device memory
+ * (copies use unified addressing; on_device is informational).
+ * Errors: EINVAL (NULL pointer, nrhs < 1, batch context), ECUDA, ENOMEM. */
+int cimmino_project(cimmino_ctx *ctx, const double *v, int32_t nrhs, double *psi,
+                    int32_t on_device);
 
-/* xi = sum_i A_i^+ f_i (Section 1.1) for f in the original row order. */
-int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t on_device);
+/* xi_k = sum_i A_i^+ f_{k,i} (Section 1.1), k < nrhs, for right-hand sides f in the
+ * original row order (nrhs x n, vector k at offset k * n); xi is nrhs x n.
+ * Errors as cimmino_project. */
+int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, int32_t nrhs, double *xi,
+                        int32_t on_device);
 
 /* Standalone C = A A^T of a caller matrix (no scaling, no permutation) on the
  * GPU, e.g. to build the row inner-product graph for a partitioner.  Two calls:

@@ -47,7 +47,7 @@ class OptsStruct(C.Structure):
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_ratio_min", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("multi_rhs", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StatsStruct(C.Structure):
@@ -107,8 +107,8 @@ def load(build_if_missing: bool = False):
         L.cimmino_get_scaled.argtypes = [vp, vp, vp, vp, vp]
         L.cimmino_block_rows.argtypes = [vp, i32, C.POINTER(i32)]
         L.cimmino_get_factor.argtypes = [vp, i32, vp, C.POINTER(i32)]
-        L.cimmino_project.argtypes = [vp, vp, vp, i32]
-        L.cimmino_project_rhs.argtypes = [vp, vp, vp, i32]
+        L.cimmino_project.argtypes = [vp, vp, i32, vp, i32]
+        L.cimmino_project_rhs.argtypes = [vp, vp, i32, vp, i32]
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
@@ -143,7 +143,7 @@ def _check(L, code: int, ctx=None):
 
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
-          keep_aat=False, stream=None) -> OptsStruct:
+          keep_aat=False, multi_rhs=None, stream=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -161,6 +161,8 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
     if check_every is not None:
         o.check_every = int(check_every)
     o.keep_aat = int(bool(keep_aat))
+    if multi_rhs is not None:
+        o.multi_rhs = int(bool(multi_rhs))
     o.stream = stream
     return o
 
@@ -251,18 +253,22 @@ class Solver:
 
     # -- hooks
     def project(self, v) -> np.ndarray:
+        """H v for one n-vector or for each row of an (nrhs, n) array."""
         v = _host(v, np.float64)
-        out = np.empty(self.n)
-        _check(self._L, self._L.cimmino_project(self._h, v.ctypes.data, out.ctypes.data, 0),
-               self._h)
-        return out
+        V = np.ascontiguousarray(np.atleast_2d(v))
+        out = np.empty_like(V)
+        _check(self._L, self._L.cimmino_project(self._h, V.ctypes.data, V.shape[0],
+                                                 out.ctypes.data, 0), self._h)
+        return out.reshape(v.shape)
 
     def project_rhs(self, f) -> np.ndarray:
+        """xi = sum_i A_i^+ f_i for one n-vector or each row of an (nrhs, n) array."""
         f = _host(f, np.float64)
-        out = np.empty(self.n)
-        _check(self._L, self._L.cimmino_project_rhs(self._h, f.ctypes.data, out.ctypes.data, 0),
-               self._h)
-        return out
+        Fm = np.ascontiguousarray(np.atleast_2d(f))
+        out = np.empty_like(Fm)
+        _check(self._L, self._L.cimmino_project_rhs(self._h, Fm.ctypes.data, Fm.shape[0],
+                                                     out.ctypes.data, 0), self._h)
+        return out.reshape(f.shape)
 
     def aat(self):
         nnz = C.c_int64(0)

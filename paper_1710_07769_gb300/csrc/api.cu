@@ -92,6 +92,15 @@ __global__ void k_interleave_to_cols(const double *__restrict__ x, int64_t N, in
   out[(int64_t)k * N + j] = x[i];
 }
 
+__global__ void k_cols_to_interleaved(const double *__restrict__ v, int64_t N, int nrhs,
+                                      double *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * nrhs) return;
+  int64_t j = i / nrhs;
+  int k = (int)(i % nrhs);
+  out[i] = v[(int64_t)k * N + j];
+}
+
 }  // namespace
 
 struct cimmino_ctx {
@@ -160,6 +169,7 @@ void opts_default(cimmino_opts *o) {
   o->use_graph = 1;
   o->check_every = 8;
   o->keep_aat = 0;
+  o->multi_rhs = 1;
   o->stream = nullptr;
 }
 
@@ -638,7 +648,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                   c->proj_slot_bytes);
   if (c->proj_slots < 2) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
   c->proj_smem = proj_smem_bytes(c->max_mp, c->proj_slots, c->proj_slot_bytes, c->proj_wbytes);
-  set_proj_smem_attr(c->proj_smem);
+  CUDA_TRY(set_proj_smem_attr(c->proj_smem));
   if (!c->err_flag.p) c->err_flag.alloc(1);
   CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaGetLastError());
@@ -723,6 +733,26 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.proj_slots = c->proj_slots;
   a.proj_slot_bytes = c->proj_slot_bytes;
   a.proj_wbytes = c->proj_wbytes;
+  // several right-hand sides: groups of 16 (FP32 factors) or 8 share each factor tile,
+  // as long as the group's vectors and a ring of at least 2 slots fit in shared memory
+  a.proj_rg = 0;
+  a.proj_mr_slots = 0;
+  a.proj_mr_smem = 0;
+  if (nrhs > 1 && c->opts.multi_rhs) {
+    for (int rg = (c->proj_wbytes == 4 && nrhs > 8) ? 16 : 8; rg >= 8; rg /= 2) {
+      // the multi-RHS kernel has up to 2 KB of static shared memory besides this
+      const int budget = kProjSmemMax - 2048;
+      const int base = proj_mr_smem_bytes(c->max_mp, rg, 0, c->proj_slot_bytes, c->proj_wbytes);
+      const int slots = std::min(kMaxProjSlots, (budget - base) / c->proj_slot_bytes);
+      if (base < budget && slots >= 2) {
+        a.proj_rg = rg;
+        a.proj_mr_slots = slots;
+        a.proj_mr_smem = base + slots * c->proj_slot_bytes;
+        CUDA_TRY(set_proj_mr_smem_attr(rg, a.proj_mr_smem));
+        break;
+      }
+    }
+  }
   a.err = c->err_flag.p;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -1076,20 +1106,44 @@ int cimmino_get_factor(cimmino_ctx *ctx, int32_t b, double *L, int32_t *is_fp64)
   }
 }
 
-int cimmino_project(cimmino_ctx *ctx, const double *v, double *psi, int32_t on_device) {
+// [nrhs][N] (host or device) <-> [N][nrhs] device layout of the CG vectors
+static void cols_in(cimmino_ctx *c, const double *V, int32_t nrhs, double *dst, cudaStream_t s) {
+  const int64_t N = c->N;
+  if (nrhs == 1) {
+    h2d(dst, V, N, s);
+    return;
+  }
+  h2d(c->Fin.p, V, N * nrhs, s);
+  const int64_t tot = N * nrhs;
+  k_cols_to_interleaved<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c->Fin.p, N, nrhs, dst);
+}
+static void cols_out(cimmino_ctx *c, const double *src, int32_t nrhs, double *V, cudaStream_t s) {
+  const int64_t N = c->N;
+  if (nrhs == 1) {
+    d2h(V, src, N, s);
+    return;
+  }
+  const int64_t tot = N * nrhs;
+  k_interleave_to_cols<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, N, nrhs, c->Fin.p);
+  d2h(V, c->Fin.p, N * nrhs, s);
+}
+
+int cimmino_project(cimmino_ctx *ctx, const double *v, int32_t nrhs, double *psi,
+                    int32_t on_device) {
   if (!ctx || !v || !psi) return CIMMINO_EINVAL;
   try {
     if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_project needs a single-system context");
+    if (nrhs < 1) fail(CIMMINO_EINVAL, "nrhs must be >= 1");
     (void)on_device;
-    ensure_solve_buffers(ctx, 1);
+    ensure_solve_buffers(ctx, nrhs);
     cudaStream_t s = ctx->stream;
     CUDA_TRY(cudaMemsetAsync(ctx->refine_total.p, 0, sizeof(int64_t), s));
     CUDA_TRY(cudaMemsetAsync(ctx->refine_max.p, 0, sizeof(int32_t), s));
-    h2d(ctx->p.p, v, ctx->N, s);
+    cols_in(ctx, v, nrhs, ctx->p.p, s);
     launch_spmv_plain(ctx->args, ctx->p.p, ctx->u.p, s);
     launch_proj(ctx->args, ctx->u.p, ctx->y.p, 0, s);
     launch_spmv_t(ctx->args, ctx->y.p, ctx->psi.p, s);
-    d2h(psi, ctx->psi.p, ctx->N, s);
+    cols_out(ctx, ctx->psi.p, nrhs, psi, s);
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     return CIMMINO_OK;
@@ -1098,19 +1152,21 @@ int cimmino_project(cimmino_ctx *ctx, const double *v, double *psi, int32_t on_d
   }
 }
 
-int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, double *xi, int32_t on_device) {
+int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, int32_t nrhs, double *xi,
+                        int32_t on_device) {
   if (!ctx || !f || !xi) return CIMMINO_EINVAL;
   try {
     if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_project_rhs needs a single-system context");
+    if (nrhs < 1) fail(CIMMINO_EINVAL, "nrhs must be >= 1");
     (void)on_device;
-    ensure_solve_buffers(ctx, 1);
+    ensure_solve_buffers(ctx, nrhs);
     cudaStream_t s = ctx->stream;
     CUDA_TRY(cudaMemsetAsync(ctx->cnt.p, 0, sizeof(int32_t) * 4 * ctx->nsys, s));
-    h2d(ctx->Fin.p, f, ctx->N, s);
+    h2d(ctx->Fin.p, f, ctx->N * nrhs, s);
     launch_rhs_scale(ctx->args, ctx->Fin.p, ctx->perm.p, s);
     launch_proj(ctx->args, ctx->fs.p, ctx->y.p, 0, s);
     launch_spmv_t(ctx->args, ctx->y.p, ctx->psi.p, s);
-    d2h(xi, ctx->psi.p, ctx->N, s);
+    cols_out(ctx, ctx->psi.p, nrhs, xi, s);
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     return CIMMINO_OK;

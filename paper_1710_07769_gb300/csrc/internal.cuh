@@ -260,6 +260,9 @@ struct IterArgs {
   int32_t proj_slots;    // factor-tile slots in the projection kernel's ring
   int32_t proj_slot_bytes;
   int32_t proj_wbytes;   // bytes per entry of the projection's working vectors (4 or 8)
+  int32_t proj_rg;       // right-hand sides per group of the multi-RHS projection (0: off)
+  int32_t proj_mr_slots; // factor-tile slots of the multi-RHS projection's ring
+  int32_t proj_mr_smem;  // dynamic shared memory bytes of the multi-RHS projection
   int32_t *err;          // device error word: bounded waits that ran out
   int32_t max_iter;
   double refine_tol;
@@ -267,7 +270,12 @@ struct IterArgs {
 };
 
 int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
-void set_proj_smem_attr(int bytes);
+cudaError_t set_proj_smem_attr(int bytes);
+// proj_mr.cu: groups of rg right-hand sides share every factor tile read
+int proj_mr_smem_bytes(int max_mp, int rg, int slots, int slot_bytes, int wbytes);
+cudaError_t set_proj_mr_smem_attr(int rg, int bytes);
+void launch_proj_mr(const IterArgs &a, const double *u, double *y, int check_lane,
+                    cudaStream_t s);
 void launch_rhs_scale(const IterArgs &a, const double *Fin, const int32_t *perm, cudaStream_t s);
 void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStream_t s);
 void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s);

@@ -27,97 +27,14 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "proj_ring.cuh"
 
 namespace cimmino {
 
 namespace {
 
-constexpr int T = kTile;
-constexpr int kConsumers = 256;
-constexpr int kProjThreads = kConsumers + 32;
-constexpr uint32_t kWaitSpins = 1u << 30;
-constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits give up after ~2 s
+using namespace ring;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: try_wait suspends the thread in hardware until the phase completes (or
-// its own time slice ends), so no sleep is added; give up after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-  if (mbar_try_wait(b, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < kWaitSpins; ++i) {
-    if (mbar_try_wait(b, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// consumer-only barrier (8 warps) and whole-CTA barrier (consumers + producer)
-__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ void allsync() { asm volatile("bar.sync 2, 288;" ::: "memory"); }
-
-struct Ring {
-  unsigned char *base;
-  uint64_t *full;
-  uint64_t *empty;
-  uint32_t slots;
-  uint32_t slot_bytes;
-  int *abort;
-};
-
-// consumer side: wait for tile t, return its slot
-__device__ __forceinline__ const void *slot_acquire(const Ring &R, uint32_t t, int32_t *err) {
-  const uint32_t s = t % R.slots;
-  if (!*(volatile int *)R.abort) {
-    if (!mbar_wait(&R.full[s], (t / R.slots) & 1u)) {
-      *(volatile int *)R.abort = 1;
-      atomicOr(err, 1);
-    }
-  }
-  return R.base + (size_t)s * R.slot_bytes;
-}
-__device__ __forceinline__ void slot_release(const Ring &R, uint32_t t) {
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(&R.empty[t % R.slots]);
-}
-
-
-// 16 FMAs: row r of a tile times 64 entries of z, chunks of quarter q in rotated order
 // 4 x 4 register block of a row product: a[i] += sum over the thread's 4 columns of
 // L(4rg+i, c) v(c).  FP32: columns 4cg..4cg+3.  FP64: columns 2cg, 2cg+1, 32+2cg, 33+2cg.
 __device__ __forceinline__ void tile_rows(const float *L, const float *v, int rg, int cg,
@@ -283,19 +200,7 @@ __device__ void producer_pass(const Ring &R, const TileRow *__restrict__ tr,
                               const unsigned char *dinv, const unsigned char *facT,
                               const unsigned char *dinvT, uint32_t tile_bytes, uint32_t &t,
                               int32_t *err) {
-  auto issue = [&](const unsigned char *src) {
-    const uint32_t s = t % R.slots;
-    if (!*(volatile int *)R.abort) {
-      if (t >= R.slots && !mbar_wait(&R.empty[s], ((t / R.slots) - 1u) & 1u)) {
-        *(volatile int *)R.abort = 1;
-        atomicOr(err, 2);
-      } else {
-        mbar_expect_tx(&R.full[s], tile_bytes);
-        bulk_g2s(R.base + (size_t)s * R.slot_bytes, src, tile_bytes, &R.full[s]);
-      }
-    }
-    ++t;
-  };
+  auto issue = [&](const unsigned char *src) { slot_fill(R, t, src, tile_bytes, err); };
   const size_t TB = tile_bytes;
   const size_t esz = TB / (T * T);
   for (int I = 0; I < nt; ++I) issue(dinv + (size_t)I * TB);
@@ -427,13 +332,8 @@ __global__ void __launch_bounds__(kProjThreads, 1)
   V.w = vb + 8 * (size_t)mpmax;
   V.out = vb + 8 * (size_t)mpmax + wb;
   if (threadIdx.x == 0) {
-    for (uint32_t s = 0; s < R.slots; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumers / 32);
-    }
-    s_abort = 0;
+    ring_init(R);
     s_again = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   uint32_t t = 0;  // tiles issued (producer) / consumed (consumers) so far
@@ -450,10 +350,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     }
   }
   // the producer drains its own copies before the CTA exits (normally already landed)
-  if (producer && (threadIdx.x & 31) == 0) {
-    const uint32_t first = t > R.slots ? t - R.slots : 0u;
-    for (uint32_t v = first; v < t; ++v) mbar_wait(&R.full[v % R.slots], (v / R.slots) & 1u);
-  }
+  if (producer && (threadIdx.x & 31) == 0) ring_drain(R, t);
 }
 
 }  // namespace
@@ -462,12 +359,15 @@ int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes) {
   return slots * slot_bytes + 8 * max_mp + 2 * wbytes * max_mp;
 }
 
-void set_proj_smem_attr(int bytes) {
-  cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+cudaError_t set_proj_smem_attr(int bytes) {
+  return cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
-  k_proj<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+  if (a.nrhs > 1 && a.proj_rg > 0)
+    launch_proj_mr(a, u, y, check_lane, s);
+  else
+    k_proj<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
 }
 
 }  // namespace cimmino

@@ -244,3 +244,73 @@ def test_errors_reported():
     s = g.Solver(w.A, w.block_ptr, max_iter=3)
     x, st, code = s.solve(w.F[0])
     assert code == g.ENOCONV and st[0]["iters"] == 3
+
+
+# ------------------------------------------------------------------ several right-hand sides
+
+def envelope_matrix():
+    """640 rows, 2 blocks of 320 (5 tiles each): tridiagonal A gives a pentadiagonal G_i
+    with tile envelope J0 = [0, 0, 1, 2, .]; one long-range entry in row 261 (tile 4)
+    reaching column 74 couples tile 4 with tile 1, so J0(4) = 1 < J0(3) = 2 (a
+    non-monotone envelope: the backward chain of tile row 1 meets a zero tile at J = 3)."""
+    n = 640
+    D = np.zeros((n, n))
+    i = np.arange(n)
+    D[i, i] = 4.0
+    D[i[1:], i[:-1]] = -1.3
+    D[i[:-1], i[1:]] = -0.7
+    D[261, 74] = 0.9
+    D[320 + 261, 320 + 74] = -0.6
+    return csr_from_dense(D), np.array([0, 320, 640], np.int64)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-10)])
+@pytest.mark.parametrize("nrhs", [2, 8, 11, 16, 21])
+def test_projection_multi_rhs_matches_oracle(sys_small, precision, tol, nrhs):
+    """Groups of 8 or 16 right-hand sides share each factor tile (padded and partial
+    groups included); every column equals the oracle's H v."""
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, precision=precision)
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    V = np.random.default_rng(nrhs).standard_normal((nrhs, A.n))
+    P = s.project(V)
+    for k in range(nrhs):
+        assert rel(P[k], o.project(V[k])) <= tol, k
+    Fm = np.stack([inputs.matvec(A, V[k]) for k in range(nrhs)])
+    Xi = s.project_rhs(Fm)
+    for k in range(0, nrhs, 5):
+        assert rel(Xi[k], o.project_rhs(Fm[k])) <= tol, k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-10)])
+def test_projection_multi_rhs_nonmonotone_envelope(precision, tol):
+    A, bp = envelope_matrix()
+    o = oracle.Oracle(A, bp)
+    V = np.random.default_rng(3).standard_normal((16, A.n))
+    for multi in (True, False):
+        s = g.Solver(A, bp, precision=precision, multi_rhs=multi)
+        P = s.project(V)
+        for k in range(16):
+            assert rel(P[k], o.project(V[k])) <= tol, (multi, k)
+
+
+def test_solve_16_rhs_matches_oracle():
+    """16 independent CG lanes sharing the factors (the multi-right-hand-side reading):
+    each lane's iteration count and solution against its own oracle solve."""
+    w = inputs.workload(1)
+    rng = np.random.default_rng(21)
+    F = np.stack([inputs.matvec(w.A, rng.uniform(-1, 1, w.A.n)) for _ in range(16)])
+    s = g.Solver(w.A, w.block_ptr, precision="fp32_refine")
+    X, st, code = s.solve(F)
+    assert code == 0
+    o = oracle.Oracle(w.A, w.block_ptr)
+    for k in range(16):
+        xo, ito, *_ = o.solve(F[k])
+        assert st[k]["status"] == 0 and abs(st[k]["iters"] - ito) <= 1, (k, st[k]["iters"], ito)
+        assert st[k]["rel_res"] <= 1e-10
+        assert rel(X[k], xo) <= 1e-8
+    # the same lanes through one factor pass per right-hand side
+    X2, st2, _ = g.Solver(w.A, w.block_ptr, precision="fp32_refine", multi_rhs=False).solve(F)
+    for k in range(16):
+        assert abs(st2[k]["iters"] - st[k]["iters"]) <= 1
+        assert rel(X2[k], X[k]) <= 1e-8
