@@ -359,6 +359,17 @@ class BatchSolver:
             _check(self._L, st, self._h)
         return Xh, [s.as_dict() for s in stats], st
 
+    def factor(self, q: int, b: int):
+        """Dense copy of L of block b of system q, and whether it was factored in FP64."""
+        gb = sum(len(bp) - 1 for bp in self._bps[:q]) + int(b)
+        m = C.c_int32(0)
+        _check(self._L, self._L.cimmino_block_rows(self._h, gb, C.byref(m)), self._h)
+        Lb = np.empty((m.value, m.value), np.float64)
+        is64 = C.c_int32(0)
+        _check(self._L, self._L.cimmino_get_factor(self._h, gb, Lb.ctypes.data, C.byref(is64)),
+               self._h)
+        return Lb, bool(is64.value)
+
 
 def aat(A, stream=None):
     """C = A A^T of a host CSR matrix on the GPU (structural pattern, sorted columns)."""
