@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <queue>
 #include <random>
 #include <vector>
 
@@ -107,6 +108,8 @@ Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<i
     if (rep[cmap[v]] == -1) rep[cmap[v]] = v;
   }
   c.xadj.assign(nc + 1, 0);
+  c.adj.reserve(g.adj.size());
+  c.w.reserve(g.adj.size());
   std::vector<int32_t> mark(nc, -1), list;
   std::vector<double> acc(nc, 0.0);
   for (int32_t cv = 0; cv < nc; ++cv) {
@@ -125,7 +128,6 @@ Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<i
         acc[cu] += g.w[q];
       }
     }
-    std::sort(list.begin(), list.end());
     for (int32_t cu : list) {
       c.adj.push_back(cu);
       c.w.push_back(acc[cu]);
@@ -173,57 +175,47 @@ void bisect(const Graph &g, const std::vector<int32_t> &vs, double target0, int3
   };
   int32_t seed = vs[rng() % m];
   seed = bfs_far(bfs_far(seed));
-  // greedy growing: add the frontier vertex with the largest (internal - external) gain
+  // greedy growing: add the frontier vertex with the largest gain 2 conn - tot, where conn
+  // is its edge weight into the grown region and tot its edge weight inside vs; a lazy
+  // max-heap holds (gain, vertex) entries, stale ones are skipped when popped
   std::vector<char> in(m, 0);
-  std::vector<double> conn(m, 0.0);  // edge weight from a vertex to the grown region
+  std::vector<double> conn(m, 0.0), tot(m, 0.0);
+  for (size_t i = 0; i < m; ++i)
+    for (int64_t e = g.xadj[vs[i]]; e < g.xadj[vs[i] + 1]; ++e)
+      if (local[g.adj[e]] >= 0) tot[i] += g.w[e];
+  std::priority_queue<std::pair<double, int32_t>> heap;
   double wgrown = 0;
-  std::vector<int32_t> frontier;
-  auto add = [&](int32_t v) {
-    in[local[v]] = 1;
-    wgrown += g.vw[v];
-    for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
-      const int32_t u = g.adj[e];
-      if (local[u] >= 0 && !in[local[u]]) {
-        if (conn[local[u]] == 0.0) frontier.push_back(u);
-        conn[local[u]] += g.w[e];
+  auto add = [&](int32_t li) {
+    in[li] = 1;
+    wgrown += g.vw[vs[li]];
+    for (int64_t e = g.xadj[vs[li]]; e < g.xadj[vs[li] + 1]; ++e) {
+      const int32_t lu = local[g.adj[e]];
+      if (lu >= 0 && !in[lu]) {
+        conn[lu] += g.w[e];
+        heap.emplace(2 * conn[lu] - tot[lu], lu);
       }
     }
   };
-  add(seed);
+  add(local[seed]);
   size_t next_unvisited = 0;
   while (wgrown < target0) {
     int32_t best = -1;
-    double bg = -1e300;
-    size_t bi = 0;
-    for (size_t i = 0; i < frontier.size(); ++i) {
-      const int32_t u = frontier[i];
-      if (in[local[u]]) continue;
-      double tot = 0;
-      for (int64_t e = g.xadj[u]; e < g.xadj[u + 1]; ++e)
-        if (local[g.adj[e]] >= 0) tot += g.w[e];
-      const double gain = 2 * conn[local[u]] - tot;
-      if (gain > bg) {
-        bg = gain;
-        best = u;
-        bi = i;
+    while (!heap.empty()) {
+      const auto top = heap.top();
+      heap.pop();
+      if (!in[top.second] && top.first == 2 * conn[top.second] - tot[top.second]) {
+        best = top.second;
+        break;
       }
     }
     if (best < 0) {  // disconnected remainder: restart from any vertex not yet grown
       while (next_unvisited < m && in[next_unvisited]) ++next_unvisited;
       if (next_unvisited >= m) break;
-      best = vs[next_unvisited];
-    } else {
-      frontier[bi] = frontier.back();
-      frontier.pop_back();
+      best = (int32_t)next_unvisited;
     }
-    if (wgrown + g.vw[best] > target0 + 0.5 * g.vw[best] && wgrown > 0) break;
+    const int32_t vwb = g.vw[vs[best]];
+    if (wgrown + vwb > target0 + 0.5 * vwb && wgrown > 0) break;
     add(best);
-    if (frontier.size() > 4096) {  // keep the scan cheap: drop stale entries
-      std::vector<int32_t> f2;
-      for (int32_t u : frontier)
-        if (!in[local[u]]) f2.push_back(u);
-      frontier.swap(f2);
-    }
   }
   for (size_t i = 0; i < m; ++i) part[vs[i]] = in[i] ? p0 : p1;
   // FM-style refinement: single moves with positive gain that keep the balance within 2%
@@ -313,21 +305,29 @@ void refine_kway(const Graph &g, std::vector<int32_t> &part, int32_t K, double c
       }
       for (int32_t p : touched) conn[p] = 0.0;
     }
-    if (!moved) break;
+    if (moved <= g.n / 2000) break;  // converged: further passes gain little
   }
 }
 
-// move vertices out of parts above the cap, cheapest loss first, preferring parts they
-// touch; a part with no such neighbour sends its vertex to the lightest part
+// Move vertices out of parts above the cap.  Every round collects, for each vertex of an
+// over-full part, its best move into an under-full part it touches (loss = edge weight it
+// keeps minus edge weight it gains), then applies the moves cheapest first while both
+// parts still need them.  A part with no such neighbour sends vertices to the lightest part.
 void enforce_cap(const Graph &g, std::vector<int32_t> &part, int32_t K, int32_t cap) {
   std::vector<int64_t> size(K, 0);
   for (int32_t v = 0; v < g.n; ++v) size[part[v]] += 1;
   std::vector<double> conn(K, 0.0);
   std::vector<int32_t> touched;
-  for (int round = 0; round < 64; ++round) {
+  struct Move {
+    double loss;
+    int32_t v, to;
+  };
+  std::vector<Move> cand;
+  for (int round = 0; round < 16; ++round) {
     bool over = false;
     for (int32_t k = 0; k < K; ++k) over |= size[k] > cap;
     if (!over) return;
+    cand.clear();
     for (int32_t v = 0; v < g.n; ++v) {
       const int32_t pv = part[v];
       if (size[pv] <= cap) continue;
@@ -344,14 +344,22 @@ void enforce_cap(const Graph &g, std::vector<int32_t> &part, int32_t K, int32_t 
           bl = conn[pv] - conn[p];
           best = p;
         }
-      // only cheap moves in the early rounds, anything later
-      if (best >= 0 && (round >= 2 || bl <= 0.25 * (conn[pv] + 1e-300) + 1e-12)) {
-        part[v] = best;
-        --size[pv];
-        ++size[best];
-      }
+      if (best >= 0) cand.push_back({bl, v, best});
       for (int32_t p : touched) conn[p] = 0.0;
     }
+    if (cand.empty()) break;
+    std::stable_sort(cand.begin(), cand.end(),
+                     [](const Move &a, const Move &b) { return a.loss < b.loss; });
+    int64_t moved = 0;
+    for (const Move &m : cand) {
+      const int32_t pv = part[m.v];
+      if (size[pv] <= cap || size[m.to] >= cap) continue;
+      part[m.v] = m.to;
+      --size[pv];
+      ++size[m.to];
+      ++moved;
+    }
+    if (!moved) break;
   }
   // last resort: fill the lightest parts
   for (int32_t v = 0; v < g.n; ++v) {
