@@ -236,6 +236,7 @@ def run_ours(args, rank, local):
     r32 = per_iter(st32, kt32, t32)
     s64.close()
     s32.close()
+    gp = None if args.no_gp else gp_leg(w, dA, dF, dX, stream, args.layout)
     hbm = float(pk.get("hbm_gbs", 6800.0))
     # FP64 projection: every streamed FP64 factor element feeds one FMA, so it is bound by
     # GB300's FP64 pipe (ncu: FP64 pipe 75% / DRAM 35% busy); FP32 projection: HBM-bound.
@@ -261,6 +262,7 @@ def run_ours(args, rank, local):
                    "parallelism": "replicas" if args.gpus > 1 else "single"},
         "fp64": r64, "fp32_refine": r32,
         "fp32_vs_fp64_time_ratio": round(r32["time_to_solution_ms"] / r64["time_to_solution_ms"], 4),
+        "graph_partition": gp,
         "roofline": roof,
         "roofline_fp32": roof32,
         "e2e": {"value": round(min(e2e_t), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
@@ -269,6 +271,60 @@ def run_ours(args, rank, local):
         "clocks": clocks.summary(),
         "wall_s": round(wall, 3),
     }
+    return out
+
+
+def contiguous_cut(C, block_ptr):
+    """Cutsize (Eq. 2.6, cosine weights of the row-scaled A) of the partition into
+    consecutive row ranges, from C = A A^T of the unscaled A."""
+    rp, ci, v = C
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    d = np.zeros(n)
+    dg = rows == ci
+    d[rows[dg]] = np.sqrt(v[dg])
+    blk = np.searchsorted(block_ptr, np.arange(n), side="right") - 1
+    m = (ci > rows) & (blk[rows] != blk[ci])
+    return float(np.sum(np.abs(v[m]) / (d[rows[m]] * d[ci[m]])))
+
+
+def gp_leg(w, dA, dF, dX, stream, layout, eps=0.05):
+    """The graph-partitioned variant of the workload (Section 2): C = A A^T on the GPU, the
+    host multilevel partitioner on G_RIP with blocks of at most (1 + eps) n / K rows, then
+    both precisions solved with those blocks (one warm-up and one timed solve each)."""
+    import torch
+
+    import paper_1710_07769_gb300 as g
+    n = w.A.n
+    K = len(w.block_ptr) - 1
+    t0 = time.perf_counter()
+    C = g.aat(w.A)
+    t_aat = time.perf_counter() - t0
+    cap = int(np.floor((1.0 + eps) * n / K))
+    t0 = time.perf_counter()
+    perm, bp, cut = g.partition_rip(n, C, K, cap=cap, seed=0)
+    t_part = time.perf_counter() - t0
+    out = {"eps": eps, "cap": cap, "aat_s": round(t_aat, 3), "partition_s": round(t_part, 2),
+           "cutsize": round(cut, 2), "cutsize_contiguous": round(contiguous_cut(C, w.block_ptr), 2),
+           "block_rows_min": int(np.diff(bp).min()), "block_rows_max": int(np.diff(bp).max())}
+    for precision in ("fp64", "fp32_refine"):
+        times = []
+        for _ in range(2):
+            with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s = g.Solver(dA, bp, perm=perm, precision=precision, layout=layout)
+                x, st, code = s.solve(dF, tol=TOL, X=dX)
+                e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            s.close()
+        out[precision] = {"time_to_solution_ms": round(times[-1], 3), "iters": st[0]["iters"],
+                          "rel_res": st[0]["rel_res"], "status": code,
+                          "factor_ms": round(st[0]["t_factor_ms"], 3),
+                          "solve_ms": round(st[0]["t_solve_ms"], 3),
+                          "factor_bytes": st[0]["factor_bytes"]}
     return out
 
 
@@ -302,6 +358,7 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--layout", default="skyline", choices=["skyline", "dense"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--no-gp", action="store_true", help="skip the graph-partitioned leg")
     ap.add_argument("--profile", default=None, choices=["fp64", "fp32_refine"],
                     help="profiling target: one setup + 4 CG iterations, nothing timed")
     args = ap.parse_args()
