@@ -26,10 +26,12 @@ namespace {
 constexpr int T = kTile;
 constexpr int kThreads = 256;
 constexpr int LDS = T + 1;  // padded row-major diagonal tile
-constexpr int LD = T + 4;   // k-major operand tiles of the CUDA-core steps
+constexpr int LD = T + 1;   // k-major operand tiles of the CUDA-core steps (odd: the
+                            // transposed stores hit 32 distinct banks)
 constexpr uint32_t kCoreK = 128;    // bytes between core matrices along K
 constexpr uint32_t kCoreRow = 2048; // bytes between 8-row groups (16 core matrices of K = 64)
 constexpr uint32_t kTmemCols = 128;
+constexpr int kDstLd = 132;  // padded row of the epilogue staging area (floats)
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -62,17 +64,41 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(h);
 }
 
-// Fill rows [64 half, 64 half + 64) of a hi/lo operand pair from a row-major tile (or zeros).
-__device__ __forceinline__ void load_split(const float *__restrict__ g, unsigned char *hi,
-                                           unsigned char *lo, int half) {
-  for (int e = threadIdx.x; e < T * T; e += kThreads) {
-    const int r = e / T, k = e % T;
-    const float x = g ? g[e] : 0.f;
-    const float h = tf32_hi(x);
-    const uint32_t o = canon(64 * half + r, k);
-    *reinterpret_cast<float *>(hi + o) = h;
-    *reinterpret_cast<float *>(lo + o) = x - h;
+// Fill a 128 x 64 hi/lo operand pair from two row-major tiles (rows 0..63 from g0, rows
+// 64..127 from g1; a null tile reads as zeros).  A warp handles 8 rows x 4 16-byte chunks
+// per unit: lane l takes row 8 rg + (l & 7), chunk 4 cq + (l >> 3), so each quarter-warp
+// stores one whole 128-byte core matrix (conflict-free) and reads 8 rows x 64 contiguous
+// bytes from global memory.  All 8 loads of a lane are issued before the first store.
+__device__ __forceinline__ void load_split2(const float *__restrict__ g0,
+                                            const float *__restrict__ g1, unsigned char *hi,
+                                            unsigned char *lo) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int U = 32 / (kThreads / 32);  // units per warp and tile
+  float4 x[2][U];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float *g = h ? g1 : g0;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = warp + (kThreads / 32) * j;
+      const int r = 8 * (u >> 2) + (lane & 7), kc = 4 * (u & 3) + (lane >> 3);
+      x[h][j] = g ? *reinterpret_cast<const float4 *>(g + r * T + 4 * kc)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = warp + (kThreads / 32) * j;
+      const int r = 8 * (u >> 2) + (lane & 7), kc = 4 * (u & 3) + (lane >> 3);
+      const float4 v = x[h][j];
+      const float4 t = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+      const uint32_t o =
+          (uint32_t)(((64 * h + r) >> 3) * kCoreRow + kc * kCoreK + (r & 7) * 16);
+      *reinterpret_cast<float4 *>(hi + o) = t;
+      *reinterpret_cast<float4 *>(lo + o) = make_float4(v.x - t.x, v.y - t.y, v.z - t.z, v.w - t.w);
+    }
 }
 
 __device__ __forceinline__ float *tile_ptr(float *fac, const TileRow &tr, int J) {
@@ -141,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *Bt = At + T * LD;                             // [T][LD]
   float *S = Bt + T * LD;                              // [T][LDS]
   float *Di = S + T * LDS;                             // [T][LDS]
+  float *Dst = reinterpret_cast<float *>(Bhi);  // [128][kDstLd] epilogue staging (B, At)
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ double s_pmin;
@@ -174,42 +201,56 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int K = 0; K < B.nt && !s_err; ++K) {
     const TileRow TK = tr[K];
     float *gKK = tile_ptr(fac, TK, K);
-    // ---- 1. diagonal tile (CUDA cores)
+    // ---- 1. diagonal tile (CUDA cores), right-looking with the column scaling deferred:
+    // step j subtracts S_ij S_kj / d_j from the trailing triangle (one barrier per column);
+    // afterwards L_jj = sqrt(d_j) and L_ij = S_ij / sqrt(d_j)
     for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
     __syncthreads();
     for (int j = 0; j < T; ++j) {
-      if (tid == 0) {
-        float dj = S[j * LDS + j];
-        if (K * T + j < B.m) s_pmin = fmin(s_pmin, (double)dj);
-        if (!(dj > 0.f) || !isfinite(dj)) {
-          s_fail = 1;
-          dj = 1.f;
-        }
-        S[j * LDS + j] = sqrtf(dj);
+      float dj = S[j * LDS + j];
+      if (tid == 0 && K * T + j < B.m) s_pmin = fmin(s_pmin, (double)dj);
+      if (!(dj > 0.f) || !isfinite(dj)) {
+        if (tid == 0) s_fail = 1;
+        dj = 1.f;
       }
-      __syncthreads();
-      const float ljj = S[j * LDS + j];
-      for (int i = j + 1 + tid; i < T; i += kThreads) S[i * LDS + j] = S[i * LDS + j] / ljj;
-      __syncthreads();
-      const int w = T - j - 1;
-      for (int e = tid; e < w * w; e += kThreads) {
-        int i = j + 1 + e / w, k = j + 1 + e % w;
-        if (k <= i) S[i * LDS + k] = fmaf(-S[i * LDS + j], S[k * LDS + j], S[i * LDS + k]);
+      const float inv = 1.f / dj;
+      for (int i = j + 1 + tr4; i < T; i += 16) {
+        const float t = S[i * LDS + j] * inv;
+        for (int k = j + 1 + tc4; k <= i; k += 16) S[i * LDS + k] = fmaf(-t, S[k * LDS + j], S[i * LDS + k]);
       }
       __syncthreads();
     }
-    // ---- 2. inv(L_KK)
-    if (tid < T) {
-      const int c = tid;
-      for (int i = 0; i < c; ++i) Di[i * LDS + c] = 0.f;
-      Di[c * LDS + c] = 1.f / S[c * LDS + c];
-      for (int i = c + 1; i < T; ++i) {
-        float s = 0.f;
-        for (int k = c; k < i; ++k) s = fmaf(S[i * LDS + k], Di[k * LDS + c], s);
-        Di[i * LDS + c] = -s / S[i * LDS + i];
-      }
+    for (int e = tid; e < T * T; e += kThreads) {
+      const int i = e / T, j = e % T;
+      if (j > i) continue;
+      float dj = S[j * LDS + j];
+      if (!(dj > 0.f) || !isfinite(dj)) dj = 1.f;
+      Di[i * LDS + j] = i == j ? sqrtf(dj) : S[i * LDS + j] / sqrtf(dj);  // L_KK, staged in Di
     }
     __syncthreads();
+    for (int e = tid; e < T * T; e += kThreads) {
+      const int i = e / T, j = e % T;
+      S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.f;
+    }
+    __syncthreads();
+    // ---- 2. inv(L_KK) by rows: Di_ic = (delta_ic - sum_{c<=k<i} L_ik Di_kc) / L_ii; row i
+    // depends on rows < i only, so all columns c of a row run in parallel (4 threads per
+    // column split the sum, fixed-order shuffle reduction)
+    {
+      const int c = tid >> 2, q = tid & 3;
+      for (int i = 0; i < T; ++i) {
+        float acc = 0.f;
+        if (c < i)
+          for (int k = c + q; k < i; k += 4) acc = fmaf(S[i * LDS + k], Di[k * LDS + c], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (q == 0) {
+          const float lii = S[i * LDS + i];
+          Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.f / lii : 0.f);
+        }
+        __syncthreads();
+      }
+    }
     float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
     for (int e = tid; e < T * T; e += kThreads) {
       int r = e / T, c = e % T;
@@ -260,16 +301,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool has0 = tr[I0].j0 <= K;
       const bool has1 = I1 < B.nt && tr[I1].j0 <= K;
       if (!has0 && !has1) continue;
-      load_split(has0 ? tile_ptr(fac, tr[I0], K) : nullptr, Ahi, Alo, 0);
-      load_split(has1 ? tile_ptr(fac, tr[I1], K) : nullptr, Ahi, Alo, 1);
+      load_split2(has0 ? tile_ptr(fac, tr[I0], K) : nullptr,
+                  has1 ? tile_ptr(fac, tr[I1], K) : nullptr, Ahi, Alo);
       const int jmax = has1 ? I1 : I0;
       for (int J0 = K + 1; J0 <= jmax && !s_err; J0 += 2) {
         const int J1 = J0 + 1;
         const bool hj0 = tr[J0].j0 <= K;
         const bool hj1 = J1 <= jmax && J1 < B.nt && tr[J1].j0 <= K;
         if (!hj0 && !hj1) continue;
-        load_split(hj0 ? tile_ptr(fac, tr[J0], K) : nullptr, Bhi, Blo, 0);
-        load_split(hj1 ? tile_ptr(fac, tr[J1], K) : nullptr, Bhi, Blo, 1);
+        load_split2(hj0 ? tile_ptr(fac, tr[J0], K) : nullptr,
+                    hj1 ? tile_ptr(fac, tr[J1], K) : nullptr, Bhi, Blo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -307,18 +348,55 @@ __global__ void __launch_bounds__(kThreads, 1)
           phase ^= 1u;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads lanes 32 (w mod 4).., column half w / 4 (= tile column)
+        // epilogue: warp w reads lanes 32 (w mod 4).. and column half w / 4 of D into the
+        // staging area (the B operands, free once the MMAs completed; rows padded to 132
+        // floats so that a quarter-warp's 16-byte stores hit 8 distinct bank groups), then
+        // all threads update the four global tiles with coalesced 16-byte read-modify-writes
         {
           const int rowq = warp & 3, jh = warp >> 2;
-          const int rr = 32 * rowq + lane;            // row of D
-          const int I = rr < 64 ? I0 : I1, J = jh ? J1 : J0;
-          const bool hasI = rr < 64 ? has0 : has1, hasJ = jh ? hj1 : hj0;
+          const int rr = 32 * rowq + lane;  // row of D
           float v[64];
           tmem_ld64(tmem + ((uint32_t)(32 * rowq) << 16) + (uint32_t)(64 * jh), v);
-          if (hasI && hasJ && J <= I && !s_err) {
-            float *g = tile_ptr(fac, tr[I], J) + (rr & 63) * T;
+          float *st = Dst + rr * kDstLd + 64 * jh;
 #pragma unroll
-            for (int c = 0; c < 64; ++c) g[c] -= v[c];
+          for (int c = 0; c < 64; c += 4)
+            *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
+        __syncthreads();
+        if (!s_err) {
+          // tile (I, J) of quadrant q: q & 1 -> I1, q >> 1 -> J1; all 16 loads of a thread
+          // are in flight before the first subtraction
+          constexpr int R = T * T / 4 / kThreads;  // 16-byte chunks per thread and tile
+          float *gq[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int I = (q & 1) ? I1 : I0, J = (q >> 1) ? J1 : J0;
+            const bool ok = ((q & 1) ? has1 : has0) && ((q >> 1) ? hj1 : hj0) && J <= I;
+            gq[q] = ok ? tile_ptr(fac, tr[I], J) : nullptr;
+          }
+          float4 x[4][R];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const int e = tid + kThreads * j, r = e >> 4, c = 4 * (e & 15);
+              if (gq[q]) x[q][j] = *reinterpret_cast<const float4 *>(gq[q] + r * T + c);
+            }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!gq[q]) continue;
+            const float *src = Dst + 64 * (q & 1) * kDstLd + 64 * (q >> 1);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const int e = tid + kThreads * j, r = e >> 4, c = 4 * (e & 15);
+              const float4 d = *reinterpret_cast<const float4 *>(src + r * kDstLd + c);
+              float4 v = x[q][j];
+              v.x -= d.x;
+              v.y -= d.y;
+              v.z -= d.z;
+              v.w -= d.w;
+              *reinterpret_cast<float4 *>(gq[q] + r * T + c) = v;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -341,6 +419,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 constexpr int kTcSmem = 4 * 32768 + (int)sizeof(float) * (2 * T * LD + 2 * T * LDS);
+// the epilogue staging area (128 x kDstLd floats from Bhi) fits in Bhi, Blo and At
+static_assert(128 * kDstLd * 4 <= 2 * 32768 + (int)sizeof(float) * T * LD, "staging area");
 
 }  // namespace
 
