@@ -146,15 +146,16 @@ def run_ours(args, rank, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     torch.cuda.synchronize()
 
-    def step(precision):
+    def step(precision, relax=False):
         with torch.cuda.stream(stream):
-            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision=precision, layout=args.layout)
+            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision=precision, layout=args.layout,
+                         refine_relax=relax)
             x, st, code = s.solve(dF, tol=TOL, X=dX)
         return s, st[0], code
 
-    def timed(precision, k, w_):
+    def timed(precision, k, w_, relax=False):
         for _ in range(w_):
-            s, st, code = step(precision)
+            s, st, code = step(precision, relax)
             s.close()
         times, last = [], None
         for _ in range(k):
@@ -163,7 +164,7 @@ def run_ours(args, rank, local):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            s, st, code = step(precision)
+            s, st, code = step(precision, relax)
             with torch.cuda.stream(stream):
                 e1.record(stream)
             e1.synchronize()
@@ -193,10 +194,14 @@ def run_ours(args, rank, local):
     # FP32 + refinement on the same workload (fewer steps, same rules)
     t32, (s32, st32, code32) = timed("fp32_refine", max(1, min(args.steps, 2)), 1)
     kt32 = s32.time_kernels(reps=10)
+    # FP32 with the relaxed inner tolerance refine_tol / relres_t (an inexact-Krylov variant:
+    # same stopping test, a few more iterations, fewer second factor passes)
+    tr, (sr, str_, coder) = timed("fp32_refine", max(1, min(args.steps, 2)), 1, relax=True)
 
     if rank != 0:
         s64.close()
         s32.close()
+        sr.close()
         return None
 
     # e2e: host CSR and host f / x through the C ABI, copies inside the timed region
@@ -234,8 +239,13 @@ def run_ours(args, rank, local):
 
     r64 = per_iter(st64, kt64, t64)
     r32 = per_iter(st32, kt32, t32)
+    rrx = {"time_to_solution_ms": round(sum(tr) / len(tr), 3), "iters": str_["iters"],
+           "rel_res": str_["rel_res"], "status": coder, "solve_ms": round(str_["t_solve_ms"], 3),
+           "refine_steps_total": str_["refine_steps_total"],
+           "inner_solves": (len(w.block_ptr) - 1) * (str_["iters"] + 1)}
     s64.close()
     s32.close()
+    sr.close()
     gp = None if args.no_gp else gp_leg(w, dA, dF, dX, stream, args.layout)
     hbm = float(pk.get("hbm_gbs", 6800.0))
     # FP64 projection: every streamed FP64 factor element feeds one FMA, so it is bound by
@@ -260,7 +270,7 @@ def run_ours(args, rank, local):
                    "partition": "contiguous", "layout": args.layout, "tol": TOL,
                    "precision": "fp64", "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if args.gpus > 1 else "single"},
-        "fp64": r64, "fp32_refine": r32,
+        "fp64": r64, "fp32_refine": r32, "fp32_refine_relaxed": rrx,
         "fp32_vs_fp64_time_ratio": round(r32["time_to_solution_ms"] / r64["time_to_solution_ms"], 4),
         "graph_partition": gp,
         "roofline": roof,

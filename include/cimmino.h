@@ -88,6 +88,10 @@ typedef struct cimmino_opts {
   int32_t use_graph;      /* 1 (default): capture CG iterations as a CUDA graph     */
   int32_t check_every;    /* CG iterations between convergence read-backs (def. 8)  */
   int32_t keep_aat;       /* 1: keep C = A A^T for cimmino_get_aat() (default 0)    */
+  int32_t refine_relax;   /* 1: relaxed inner tolerance in CG iteration t:          */
+                          /* min(1e-6, refine_tol / relres_t), relres_t the true    */
+                          /* relative residual of the current x (inexact Krylov    */
+                          /* subspace methods); 0 (default): refine_tol throughout  */
   int32_t multi_rhs;      /* 1 (default): with several right-hand sides, groups of  */
                           /* 8 or 16 share every factor tile read; 0: one factor    */
                           /* pass per right-hand side                               */

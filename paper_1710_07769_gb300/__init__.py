@@ -47,7 +47,7 @@ class OptsStruct(C.Structure):
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_ratio_min", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
-                ("multi_rhs", C.c_int32), ("stream", C.c_void_p)]
+                ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StatsStruct(C.Structure):
@@ -143,7 +143,7 @@ def _check(L, code: int, ctx=None):
 
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
-          keep_aat=False, multi_rhs=None, stream=None) -> OptsStruct:
+          keep_aat=False, refine_relax=None, multi_rhs=None, stream=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -163,6 +163,8 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
     o.keep_aat = int(bool(keep_aat))
     if multi_rhs is not None:
         o.multi_rhs = int(bool(multi_rhs))
+    if refine_relax is not None:
+        o.refine_relax = int(bool(refine_relax))
     o.stream = stream
     return o
 

@@ -170,6 +170,7 @@ void opts_default(cimmino_opts *o) {
   o->check_every = 8;
   o->keep_aat = 0;
   o->multi_rhs = 1;
+  o->refine_relax = 0;
   o->stream = nullptr;
 }
 
@@ -727,6 +728,7 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.nrhs = nrhs;
   a.refine_steps = c->opts.precision == CIMMINO_FP32_REFINE ? c->opts.refine_max : 0;
   a.refine_tol = c->opts.refine_tol;
+  a.refine_relax = c->opts.refine_relax;
   a.max_iter = c->opts.max_iter;
   a.max_mp = c->max_mp;
   a.proj_smem = c->proj_smem;

@@ -266,8 +266,22 @@ struct IterArgs {
   int32_t *err;          // device error word: bounded waits that ran out
   int32_t max_iter;
   double refine_tol;
+  int32_t refine_relax;  // 1: inner tolerance min(1e-6, refine_tol / relres_t) in iterations
+  int32_t pad_relax;
   double tol;
 };
+
+// Inner-solve tolerance of lane `l` (relative ||G y - u|| / ||u||).  With refine_relax, a
+// projection inside CG iteration t may be as inexact as refine_tol / relres_t, where
+// relres_t is the true relative residual of the current iterate: the inexact-Krylov
+// bound lets the error of the operator application grow as the residual shrinks.  The
+// 1e-6 cap keeps it at the FP32 solve's own accuracy.  Outside iterations (check_lane 0:
+// the right-hand side projection and the inspection hooks) refine_tol applies.
+__device__ __forceinline__ double inner_tol(const IterArgs &a, int check_lane, int64_t l) {
+  if (!a.refine_relax || !check_lane) return a.refine_tol;
+  const double rr = a.lane[l].relres;
+  return fmin(1e-6, a.refine_tol / fmax(rr, 1e-300));
+}
 
 int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_smem_attr(int bytes);

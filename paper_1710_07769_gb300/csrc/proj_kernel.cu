@@ -22,7 +22,8 @@
 //    1 or 2 of the vector); a quarter-warp's 16-byte loads cover 8 distinct bank groups.
 //    The 16 column groups of a row meet in a 5-shuffle butterfly.
 //  * FP32 blocks are refined in FP64 against the exact Gram block (sliced-ELL copy):
-//    res = u - G_i y, y += L^{-T} L^{-1} res, until ||res|| <= refine_tol ||u||.
+//    res = u - G_i y, y += L^{-T} L^{-1} res, until ||res|| <= tol ||u|| (refine_tol, or
+//    the relaxed inner tolerance of the lane inside CG iterations).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -226,7 +227,8 @@ struct Vecs {
 template <typename W>
 __device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring &R, const Vecs &V,
                                const double *__restrict__ u, double *__restrict__ y, int k,
-                               int refine_steps, uint32_t &t, double *red, int *s_again) {
+                               int refine_steps, double tol, uint32_t &t, double *red,
+                               int *s_again) {
   const int mp = B.nt * T;
   const int tid = threadIdx.x;
   W *w = static_cast<W *>(V.w);
@@ -271,7 +273,7 @@ __device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring
         e2 += acc * acc;
       }
       e2 = csum(e2, red);
-      again = e2 > a.refine_tol * a.refine_tol * un2;
+      again = e2 > tol * tol * un2;
     }
     if (tid == 0) *s_again = again;
     allsync();
@@ -344,9 +346,11 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     if (producer) {
       producer_block(a, B, R, t, &s_again);
     } else if (B.prec64) {
-      consumer_block<double>(a, B, R, V, u, y, k, 0, t, red, &s_again);
+      consumer_block<double>(a, B, R, V, u, y, k, 0, 0.0, t, red, &s_again);
     } else {
-      consumer_block<float>(a, B, R, V, u, y, k, rs, t, red, &s_again);
+      consumer_block<float>(a, B, R, V, u, y, k, rs,
+                            inner_tol(a, check_lane, (int64_t)B.sys * a.nrhs + k), t, red,
+                            &s_again);
     }
   }
   // the producer drains its own copies before the CTA exits (normally already landed)

@@ -19,7 +19,8 @@
 //
 // FP32 blocks are refined in FP64 against the exact Gram block (sliced-ELL copy), with
 // y accumulated in the global output:  res = u - G_i y,  y += L^{-T} L^{-1} res,
-// until every active lane has ||res|| <= refine_tol ||u|| (or the step limit).
+// until every active lane has ||res|| <= tol ||u|| (refine_tol, or the lane's relaxed inner
+// tolerance inside CG iterations), or the step limit.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -298,7 +299,8 @@ template <typename W, int RG>
 __device__ void mr_block(const IterArgs &a, const BlockDesc &B, const Ring &R, W *Wv,
                          unsigned char *red,
                          const Small &sm, const double *__restrict__ u, double *__restrict__ y,
-                         int k0, uint32_t mask, int refine_steps, uint32_t &t, int *s_again) {
+                         int k0, uint32_t mask, int refine_steps, int check_lane, uint32_t &t,
+                         int *s_again) {
   const int mp = B.nt * T;
   const int tid = threadIdx.x;
   const int64_t ld = a.nrhs;
@@ -378,9 +380,11 @@ __device__ void mr_block(const IterArgs &a, const BlockDesc &B, const Ring &R, W
         sm.e2[tid] = v;
       }
       csync();
-      const double tol2 = a.refine_tol * a.refine_tol;
-      for (int g = 0; g < RG; ++g)
-        if (((mask >> g) & 1u) && sm.e2[g] > tol2 * sm.un2[g]) again = 1;
+      for (int g = 0; g < RG; ++g) {
+        if (!((mask >> g) & 1u)) continue;
+        const double tol = inner_tol(a, check_lane, (int64_t)B.sys * a.nrhs + k0 + g);
+        if (sm.e2[g] > tol * tol * sm.un2[g]) again = 1;
+      }
     }
     if (tid == 0) *s_again = again;
     allsync();
@@ -455,11 +459,11 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     if (producer) {
       mr_producer_block(a, B, R, t, &s_again);
     } else if (B.prec64) {
-      mr_block<double, RG>(a, B, R, static_cast<double *>(Wv), red, sm, u, y, k0, mask, 0, t,
-                           &s_again);
+      mr_block<double, RG>(a, B, R, static_cast<double *>(Wv), red, sm, u, y, k0, mask, 0,
+                           check_lane, t, &s_again);
     } else {
       mr_block<float, RG>(a, B, R, static_cast<float *>(Wv), red, sm, u, y, k0, mask,
-                          a.refine_steps, t, &s_again);
+                          a.refine_steps, check_lane, t, &s_again);
     }
   }
   if (producer && (threadIdx.x & 31) == 0) ring_drain(R, t);

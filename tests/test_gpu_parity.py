@@ -314,3 +314,23 @@ def test_solve_16_rhs_matches_oracle():
     for k in range(16):
         assert abs(st2[k]["iters"] - st[k]["iters"]) <= 1
         assert rel(X2[k], X[k]) <= 1e-8
+
+
+# ------------------------------------------------------------------ relaxed inner tolerance
+
+def test_relaxed_inner_tolerance_converges():
+    """refine_relax: inner solves to refine_tol / relres_t (capped at 1e-6) inside CG
+    iterations.  Same stopping test (true residual <= 1e-10); fewer refinement steps; the
+    iteration count stays within 1% (+1) of the exact-inner-solve count."""
+    w = inputs.workload(1)
+    ex = g.Solver(w.A, w.block_ptr, precision="fp32_refine")
+    x0, s0, c0 = ex.solve(w.F[0])
+    rx = g.Solver(w.A, w.block_ptr, precision="fp32_refine", refine_relax=True)
+    x1, s1, c1 = rx.solve(w.F[0])
+    assert c0 == 0 and c1 == 0
+    assert s1[0]["rel_res"] <= 1e-10
+    r = np.linalg.norm(w.F[0] - inputs.matvec(w.A, x1)) / np.linalg.norm(w.F[0])
+    assert r <= 1.01e-10
+    assert s1[0]["refine_steps_total"] < s0[0]["refine_steps_total"]
+    assert abs(s1[0]["iters"] - s0[0]["iters"]) <= 1 + s0[0]["iters"] // 100
+    assert rel(x1, x0) <= 1e-8
