@@ -251,6 +251,39 @@ __device__ void transpose_block(const BlockDesc &B, const TileRow *__restrict__ 
   }
 }
 
+// Packed copies of inv(L_II) (lower) and inv(L_II)^T (upper) for the single-vector solves
+// of FP64 blocks:
+// entry j of row pair p is (p, j) for j <= p and (63 - p, j - p - 1) for p < j <= 64 (lower),
+// (p, p + j) for j <= 63 - p and (63 - p, j - 1) for 63 - p < j <= 64 (upper); the rest 0.
+template <typename W>
+__device__ void pack_block(const BlockDesc &B, const W *__restrict__ dinv,
+                           const W *__restrict__ dinvT, W *__restrict__ P, W *__restrict__ PT) {
+  const int64_t o = B.dinv_off, op = B.dinv_off / (T * T) * kPackTile;
+  for (int64_t e = threadIdx.x; e < (int64_t)B.nt * kPackTile; e += kThreads) {
+    const int I = (int)(e / kPackTile), q = (int)(e % kPackTile);
+    const int p = q / kPackPair, j = q % kPackPair;
+    const W *D = dinv + o + (int64_t)I * T * T;
+    const W *DT = dinvT + o + (int64_t)I * T * T;
+    W lv = W(0), uv = W(0);
+    if (j <= p)
+      lv = D[p * T + j];
+    else if (j <= 64)
+      lv = D[(63 - p) * T + (j - p - 1)];
+    if (j <= 63 - p)
+      uv = DT[p * T + p + j];
+    else if (j <= 64)
+      uv = DT[(63 - p) * T + (j - 1)];
+    P[op + e] = lv;
+    PT[op + e] = uv;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_pack_diag(const BlockDesc *__restrict__ blk, FactorPtrs f) {
+  const BlockDesc B = blk[blockIdx.x];
+  if (B.prec64) pack_block<double>(B, f.dinv64, f.dinvT64, f.dinvP64, f.dinvTP64);
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_transpose_factor(const BlockDesc *__restrict__ blk, const TileRow *__restrict__ trow,
                        const TileRow *__restrict__ trowT, FactorPtrs f) {
@@ -293,6 +326,7 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
                              const TileRow *trowT, const FactorPtrs &f, cudaStream_t s) {
   if (nblk > 0) k_transpose_factor<<<(unsigned)nblk, kThreads, 0, s>>>(blk, trow, trowT, f);
+  if (nblk > 0) k_pack_diag<<<(unsigned)nblk, kThreads, 0, s>>>(blk, f);
 }
 
 }  // namespace cimmino

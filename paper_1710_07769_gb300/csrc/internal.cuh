@@ -27,6 +27,10 @@ constexpr int kSpgemmWarpCap = 1024;   // candidates per row handled by one warp
 constexpr int kSpgemmCtaCap = 8192;    // candidates per row handled by one CTA
 constexpr int kMaxProjSlots = 16;      // factor-tile slots of the projection kernel's ring
 constexpr int kProjSmemMax = 231424;   // dynamic shared memory budget of one projection CTA
+// Packed triangular tiles (rectangular full packed): row pair p = 0..31 holds the entries of
+// rows p and 63 - p of a lower (or upper) triangular 64 x 64 tile, 65 values, padded to 68.
+constexpr int kPackPair = 68;
+constexpr int kPackTile = 32 * kPackPair;  // 2176 entries instead of 4096
 
 struct BlockDesc {
   int64_t row0;      // first global (permuted, concatenated) row
@@ -189,6 +193,8 @@ struct FactorPtrs {
   const double *dinv64;
   double *facT64;
   double *dinvT64;
+  double *dinvP64;   // packed inv(L_II) (lower) and inv(L_II)^T (upper) of FP64 blocks,
+  double *dinvTP64;  // kPackTile entries per tile
 };
 
 // chol_tc.cu: FP32 blocks, trailing update on the tensor cores (tcgen05, 3xTF32)
@@ -235,6 +241,8 @@ struct IterArgs {
   const double *dinv64;
   const double *facT64;
   const double *dinvT64;
+  const double *dinvP64;  // packed triangular inv(L_II), inv(L_II)^T of FP64 blocks
+  const double *dinvTP64;
   const SysDesc *sys;
   const CtaDesc *cta;
   LaneState *lane;
@@ -265,9 +273,8 @@ struct IterArgs {
   int32_t proj_mr_smem;  // dynamic shared memory bytes of the multi-RHS projection
   int32_t *err;          // device error word: bounded waits that ran out
   int32_t max_iter;
-  double refine_tol;
   int32_t refine_relax;  // 1: inner tolerance min(1e-6, refine_tol / relres_t) in iterations
-  int32_t pad_relax;
+  double refine_tol;
   double tol;
 };
 

@@ -13,9 +13,10 @@
 //    shared-memory slots in the consumers' order.  full[s] completes when a copy lands,
 //    empty[s] when all 8 consumer warps have passed the slot.  Every wait is bounded; a
 //    wait that runs out sets the error flag and the kernel finishes without waiting again.
-//  * inv(L_II) and its transpose (independent tile rows): one warp computes a tile, a
-//    lane per two rows, no reduction.  Every consumer warp waits for and releases every
-//    slot in order, so a warp never waits on a slot more than one use ahead (which would
+//  * inv(L_II) and its transpose (independent tile rows): one warp computes a tile, no
+//    reduction.  FP64 blocks stream them as packed triangles (rectangular full packed,
+//    2176 of 4096 entries, a lane per row pair (p, 63 - p)); FP32 blocks as full tiles.
+//    Every consumer warp waits for and releases every slot in order, so a warp never waits on a slot more than one use ahead (which would
 //    make the mbarrier phase parity ambiguous).
 //  * Chain steps: thread (rg, cg) owns rows 4rg..4rg+3 and four columns of each tile
 //    (4 x 4 register block: 16 FMAs per tile from 4 or 8 16-byte loads of the tile and
@@ -66,27 +67,9 @@ __device__ __forceinline__ void tile_rows(const double *L, const double *v, int 
   }
 }
 
-// Whole tile times v by one warp: lane l owns rows l and l+32 and walks the 16-byte
-// chunks of its rows in the order (k + l) mod (chunks per row), so the 8 lanes of a
-// quarter-warp always touch 8 distinct bank groups; no reduction is needed.
-__device__ __forceinline__ void tile_rows_warp(const double *D, const double *v, double *o,
-                                               int lane) {
-  const double2 *R0 = reinterpret_cast<const double2 *>(D + lane * T);
-  const double2 *R1 = reinterpret_cast<const double2 *>(D + (lane + 32) * T);
-  const double2 *V = reinterpret_cast<const double2 *>(v);
-  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-#pragma unroll 8
-  for (int k = 0; k < T / 2; ++k) {
-    const int ch = (k + lane) & (T / 2 - 1);
-    const double2 x = V[ch], p = R0[ch], q = R1[ch];
-    a0 = fma(p.x, x.x, a0);
-    a1 = fma(p.y, x.y, a1);
-    b0 = fma(q.x, x.x, b0);
-    b1 = fma(q.y, x.y, b1);
-  }
-  o[lane] = a0 + a1;
-  o[lane + 32] = b0 + b1;
-}
+// Whole tile times v by one warp (FP32 blocks): lane l owns rows l and l+32 and walks the
+// 16-byte chunks of its rows in the order (k + l) mod 16, so the 8 lanes of a quarter-warp
+// always touch 8 distinct bank groups; four independent accumulators, no reduction.
 __device__ __forceinline__ void tile_rows_warp(const float *D, const float *v, float *o, int lane) {
   const float4 *R0 = reinterpret_cast<const float4 *>(D + lane * T);
   const float4 *R1 = reinterpret_cast<const float4 *>(D + (lane + 32) * T);
@@ -107,6 +90,62 @@ __device__ __forceinline__ void tile_rows_warp(const float *D, const float *v, f
   }
   o[lane] = a0 + a1;
   o[lane + 32] = b0 + b1;
+}
+
+// Packed triangular tile times v by one warp (FP64 blocks, where every FMA counts on
+// GB300's FP64 pipe).  Lane p owns row pair p (rows p and 63 - p,
+// kPackPair entries, the second row starting at entry sw): one accumulator runs over the
+// pair's entries and is handed over at sw, so every lane does 68 FMAs instead of 128.
+//   lower (inv(L_II)):   entry e < sw = p + 1 is (p, e), later (63 - p, e - p - 1)
+//   upper (inv(L_II)^T): entry e < sw = 64 - p is (p, p + e), later (63 - p, e - 1)
+// Pair stride 544 bytes: a quarter-warp's 16-byte loads hit 4 distinct bank groups.  The
+// three padding entries are zero, any in-range index serves.
+template <bool UPPER, typename W>
+__device__ __forceinline__ void packed_rows_warp(const W *P, const W *v, W *o, int p) {
+  constexpr int E = 16 / sizeof(W);
+  const W *R = P + p * kPackPair;
+  const int sw = UPPER ? 64 - p : p + 1;
+  W acc = W(0), first = W(0);
+#pragma unroll
+  for (int q = 0; q < kPackPair / E; ++q) {
+    W d[E];
+    if constexpr (E == 4) {
+      const float4 x = reinterpret_cast<const float4 *>(R)[q];
+      d[0] = x.x;
+      d[1] = x.y;
+      d[2] = x.z;
+      d[3] = x.w;
+    } else {
+      const double2 x = reinterpret_cast<const double2 *>(R)[q];
+      d[0] = x.x;
+      d[1] = x.y;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int e = E * q + j;
+      if (e == sw) {
+        first = acc;
+        acc = W(0);
+      }
+      int c = UPPER ? (e < sw ? p + e : e - 1) : (e < sw ? e : e - p - 1);
+      c = c < T ? c : T - 1;
+      acc = fma(d[j], v[c], acc);
+    }
+  }
+  o[p] = first;
+  o[T - 1 - p] = acc;
+}
+
+// Diagonal-tile products: FP32 blocks stream full tiles of inv(L_II) and inv(L_II)^T
+// (bandwidth-bound: the vectorised full-tile product is cheaper than unpacking), FP64
+// blocks stream the packed triangles (FP64-bound: 68 instead of 128 FMAs per lane).
+template <bool UPPER>
+__device__ __forceinline__ void diag_rows(const float *D, const float *v, float *o, int lane) {
+  tile_rows_warp(D, v, o, lane);
+}
+template <bool UPPER>
+__device__ __forceinline__ void diag_rows(const double *D, const double *v, double *o, int lane) {
+  packed_rows_warp<UPPER>(D, v, o, lane);
 }
 
 // Sum of a[0..3] over the 16 column groups of a half-warp (5 shuffles, fixed order).
@@ -149,11 +188,12 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
   const bool writer = (lane & 3) == 0;
   int row;
   const int warp = tid >> 5;
-  // F0: out_I = inv(L_II) w_I (independent tile rows, one warp per tile); every warp still
-  // waits for and releases every tile in order, which keeps the slots' phases unambiguous
+  // F0: out_I = inv(L_II) w_I (independent tile rows, one warp per packed tile); every warp
+  // still waits for and releases every tile in order, which keeps the slots' phases
+  // unambiguous
   for (int I = 0; I < nt; ++I) {
     const W *D = static_cast<const W *>(slot_acquire(R, t, err));
-    if ((I & 7) == warp) tile_rows_warp(D, w + I * T, out + I * T, lane);
+    if ((I & 7) == warp) diag_rows<false>(D, w + I * T, out + I * T, lane);
     slot_release(R, t);
     ++t;
   }
@@ -184,11 +224,10 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
     if (writer) w[I * T + 4 * rg + row] -= c;
     csync();
   }
-  // B2: out_I = inv(L_II)^T w_I (independent tile rows, one warp per tile); every warp still
-  // waits for and releases every tile in order, which keeps the slots' phases unambiguous
+  // B2: out_I = inv(L_II)^T w_I (packed upper triangles, one warp per tile)
   for (int I = 0; I < nt; ++I) {
     const W *D = static_cast<const W *>(slot_acquire(R, t, err));
-    if ((I & 7) == warp) tile_rows_warp(D, w + I * T, out + I * T, lane);
+    if ((I & 7) == warp) diag_rows<true>(D, w + I * T, out + I * T, lane);
     slot_release(R, t);
     ++t;
   }
@@ -199,12 +238,12 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
 __device__ void producer_pass(const Ring &R, const TileRow *__restrict__ tr,
                               const TileRow *__restrict__ trT, int nt, const unsigned char *fac,
                               const unsigned char *dinv, const unsigned char *facT,
-                              const unsigned char *dinvT, uint32_t tile_bytes, uint32_t &t,
-                              int32_t *err) {
+                              const unsigned char *dinvT, uint32_t tile_bytes, uint32_t diag_bytes,
+                              uint32_t &t, int32_t *err) {
   auto issue = [&](const unsigned char *src) { slot_fill(R, t, src, tile_bytes, err); };
   const size_t TB = tile_bytes;
   const size_t esz = TB / (T * T);
-  for (int I = 0; I < nt; ++I) issue(dinv + (size_t)I * TB);
+  for (int I = 0; I < nt; ++I) slot_fill(R, t, dinv + (size_t)I * diag_bytes, diag_bytes, err);
   for (int I = 0; I < nt; ++I) {
     const TileRow TI = tr[I];
     const unsigned char *row = fac + (size_t)TI.off * esz;
@@ -215,7 +254,7 @@ __device__ void producer_pass(const Ring &R, const TileRow *__restrict__ tr,
     const unsigned char *row = facT + (size_t)U.off * esz;
     for (int J = I + 1; J <= U.j0; ++J) issue(row + (size_t)(J - I - 1) * TB);
   }
-  for (int I = 0; I < nt; ++I) issue(dinvT + (size_t)I * TB);
+  for (int I = 0; I < nt; ++I) slot_fill(R, t, dinvT + (size_t)I * diag_bytes, diag_bytes, err);
 }
 
 struct Vecs {
@@ -224,11 +263,12 @@ struct Vecs {
   void *out;  // working-precision result of a solve pass
 };
 
-template <typename W>
+// RELAX: inner tolerance of the lane relaxed to min(1e-6, refine_tol / relres_t) (CG
+// iterations with refine_relax); otherwise refine_tol.
+template <typename W, bool RELAX>
 __device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring &R, const Vecs &V,
                                const double *__restrict__ u, double *__restrict__ y, int k,
-                               int refine_steps, double tol, uint32_t &t, double *red,
-                               int *s_again) {
+                               int refine_steps, uint32_t &t, double *red, int *s_again) {
   const int mp = B.nt * T;
   const int tid = threadIdx.x;
   W *w = static_cast<W *>(V.w);
@@ -273,6 +313,7 @@ __device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring
         e2 += acc * acc;
       }
       e2 = csum(e2, red);
+      const double tol = RELAX ? inner_tol(a, 1, (int64_t)B.sys * a.nrhs + k) : a.refine_tol;
       again = e2 > tol * tol * un2;
     }
     if (tid == 0) *s_again = again;
@@ -296,22 +337,28 @@ __device__ void producer_block(const IterArgs &a, const BlockDesc &B, const Ring
                                  : reinterpret_cast<const unsigned char *>(a.fac32);
   const unsigned char *facT = p64 ? reinterpret_cast<const unsigned char *>(a.facT64)
                                   : reinterpret_cast<const unsigned char *>(a.facT32);
-  const unsigned char *dinv = p64 ? reinterpret_cast<const unsigned char *>(a.dinv64 + B.dinv_off)
+  // diagonal tiles: packed triangles for FP64 blocks, full tiles for FP32 blocks
+  const int64_t po = B.dinv_off / (T * T) * kPackTile;
+  const unsigned char *dinv = p64 ? reinterpret_cast<const unsigned char *>(a.dinvP64 + po)
                                   : reinterpret_cast<const unsigned char *>(a.dinv32 + B.dinv_off);
   const unsigned char *dinvT = p64
-                                   ? reinterpret_cast<const unsigned char *>(a.dinvT64 + B.dinv_off)
+                                   ? reinterpret_cast<const unsigned char *>(a.dinvTP64 + po)
                                    : reinterpret_cast<const unsigned char *>(a.dinvT32 + B.dinv_off);
   const uint32_t tb = (uint32_t)(T * T * (p64 ? 8 : 4));
+  const uint32_t db = p64 ? (uint32_t)(kPackTile * 8) : tb;
   for (;;) {
     if (leader)
-      producer_pass(R, a.trow + B.trow0, a.trowT + B.trow0, B.nt, fac, dinv, facT, dinvT, tb, t,
-                    a.err);
+      producer_pass(R, a.trow + B.trow0, a.trowT + B.trow0, B.nt, fac, dinv, facT, dinvT, tb, db,
+                    t, a.err);
     __syncwarp();
     allsync();
     if (!*(volatile int *)s_again) break;
   }
 }
 
+// ANY64: the context holds FP64 blocks (FP64 precision or fallbacks).  An all-FP32 context
+// runs the instance without the FP64 path.  RELAX: CG iterations with refine_relax.
+template <bool ANY64, bool RELAX>
 __global__ void __launch_bounds__(kProjThreads, 1)
     k_proj(IterArgs a, const double *__restrict__ u, double *__restrict__ y, int check_lane) {
   __shared__ uint64_t full[kMaxProjSlots], empty[kMaxProjSlots];
@@ -345,12 +392,10 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     const int rs = B.prec64 ? 0 : a.refine_steps;
     if (producer) {
       producer_block(a, B, R, t, &s_again);
-    } else if (B.prec64) {
-      consumer_block<double>(a, B, R, V, u, y, k, 0, 0.0, t, red, &s_again);
+    } else if (ANY64 && B.prec64) {
+      consumer_block<double, false>(a, B, R, V, u, y, k, 0, t, red, &s_again);
     } else {
-      consumer_block<float>(a, B, R, V, u, y, k, rs,
-                            inner_tol(a, check_lane, (int64_t)B.sys * a.nrhs + k), t, red,
-                            &s_again);
+      consumer_block<float, RELAX>(a, B, R, V, u, y, k, rs, t, red, &s_again);
     }
   }
   // the producer drains its own copies before the CTA exits (normally already landed)
@@ -364,14 +409,25 @@ int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes) {
 }
 
 cudaError_t set_proj_smem_attr(int bytes) {
-  return cudaFuncSetAttribute(k_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void *fs[4] = {(const void *)k_proj<false, false>, (const void *)k_proj<false, true>,
+                       (const void *)k_proj<true, false>, (const void *)k_proj<true, true>};
+  for (const void *f : fs) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
   if (a.nrhs > 1 && a.proj_rg > 0)
     launch_proj_mr(a, u, y, check_lane, s);
-  else
-    k_proj<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+  else {
+    const bool any64 = a.proj_wbytes == 8, relax = a.refine_relax && check_lane;
+    auto k = any64 ? (relax ? k_proj<true, true> : k_proj<true, false>)
+                   : (relax ? k_proj<false, true> : k_proj<false, false>);
+    k<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+  }
 }
 
 }  // namespace cimmino
