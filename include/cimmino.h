@@ -259,6 +259,17 @@ int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_t *cci, con
                           int32_t K, int32_t cap, uint64_t seed, int32_t *perm,
                           int64_t *block_ptr, double *cutsize);
 
+/* Algorithm 1 (Section 1.1): the block Cimmino iteration with relaxation parameter
+ * omega, x^(t+1) = x^(t) + omega * sum_i A_i^+ (f_i - A_i x^(t)), from x^(0) = 0, for
+ * `sweeps` sweeps, on the same setup (scaling, factors, refinement) as the CG solve.
+ * f: nrhs x n right-hand sides in the original row order; x: nrhs x n result in the
+ * original column order (vector k at offset k * n); host or device memory.  Block
+ * Cimmino converges for 0 < omega < 2 / rho(H) (Section 1.1); no test is applied here.
+ * Errors: EINVAL (NULL pointer, nrhs < 1, sweeps < 0, omega not finite, batch
+ * context), ECUDA, ENOMEM. */
+int cimmino_sweeps(cimmino_ctx *ctx, const double *f, int32_t nrhs, double omega,
+                   int32_t sweeps, double *x, int32_t on_device);
+
 /* Benchmark hook: after a cimmino_solve() on a single-system context, launch each
  * per-iteration kernel `reps` times back to back on the context's stream, on the
  * vectors of the last solve, and write the average device time per launch in

@@ -33,7 +33,8 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV", -
 EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimmino_solve",
            "cimmino_solve_batch", "cimmino_free", "cimmino_last_error", "cimmino_get_aat_nnz",
            "cimmino_get_aat", "cimmino_get_scaled", "cimmino_block_rows", "cimmino_get_factor",
-           "cimmino_project", "cimmino_project_rhs", "cimmino_aat", "cimmino_aat_noalloc",
+           "cimmino_project", "cimmino_project_rhs", "cimmino_sweeps", "cimmino_aat",
+           "cimmino_aat_noalloc",
            "cimmino_partition_rip", "cimmino_time_kernels", "cimmino_version"]
 
 
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_get_factor.argtypes = [vp, i32, vp, C.POINTER(i32)]
         L.cimmino_project.argtypes = [vp, vp, i32, vp, i32]
         L.cimmino_project_rhs.argtypes = [vp, vp, i32, vp, i32]
+        L.cimmino_sweeps.argtypes = [vp, vp, i32, dbl, i32, vp, i32]
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
@@ -270,6 +272,17 @@ class Solver:
         out = np.empty_like(Fm)
         _check(self._L, self._L.cimmino_project_rhs(self._h, Fm.ctypes.data, Fm.shape[0],
                                                      out.ctypes.data, 0), self._h)
+        return out.reshape(f.shape)
+
+    def sweeps(self, f, omega: float, sweeps: int) -> np.ndarray:
+        """Algorithm 1 from x = 0: `sweeps` block Cimmino sweeps with relaxation omega, for
+        one n-vector or each row of an (nrhs, n) array of right-hand sides."""
+        f = _host(f, np.float64)
+        Fm = np.ascontiguousarray(np.atleast_2d(f))
+        out = np.empty_like(Fm)
+        _check(self._L, self._L.cimmino_sweeps(self._h, Fm.ctypes.data, Fm.shape[0],
+                                                float(omega), int(sweeps), out.ctypes.data, 0),
+               self._h)
         return out.reshape(f.shape)
 
     def aat(self):

@@ -591,17 +591,17 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->ccv.release();
     c->have_aat = false;
   }
-  // ---- vector-kernel CTA table (256 rows per CTA, never straddling systems) and the
-  // 32-row slices of the sliced-ELL copies of A and A^T
+  // ---- vector-kernel CTA table (kVecRows rows per CTA, never straddling systems) and
+  // the 32-row slices of the sliced-ELL copies of A and A^T
   std::vector<int64_t> hsrow0;
   std::vector<int32_t> hsrows;
   for (int32_t q = 0; q < nsys; ++q) {
     SysDesc &S = c->hsys[q];
     S.cta0 = (int32_t)c->hcta.size();
-    for (int64_t r = 0; r < S.n; r += 256) {
+    for (int64_t r = 0; r < S.n; r += kVecRows) {
       CtaDesc C{};
       C.row0 = S.row0 + r;
-      C.rows = (int32_t)std::min<int64_t>(256, S.n - r);
+      C.rows = (int32_t)std::min<int64_t>(kVecRows, S.n - r);
       C.sys = q;
       C.slice0 = (int32_t)hsrow0.size();
       for (int64_t r2 = r; r2 < r + C.rows; r2 += 32) {
@@ -832,7 +832,9 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   d2h(&herr, c->err_flag.p, 1, s);
   const double tms = tsolve.stop_ms(s);
   CUDA_TRY(cudaGetLastError());
-  if (herr) fail(CIMMINO_ETIMEOUT, "a bounded wait in the projection kernel ran out");
+  if (herr)
+    fail(CIMMINO_ETIMEOUT, "a bounded wait ran out (error word " + std::to_string(herr) +
+                               ": 1/2 projection ring, 4 Cholesky MMA)");
   int ret = CIMMINO_OK;
   for (int32_t q = 0; q < c->nsys; ++q) {
     const SysDesc &S = c->hsys[q];
@@ -1177,6 +1179,33 @@ int cimmino_project_rhs(cimmino_ctx *ctx, const double *f, int32_t nrhs, double 
     launch_proj(ctx->args, ctx->fs.p, ctx->y.p, 0, s);
     launch_spmv_t(ctx->args, ctx->y.p, ctx->psi.p, s);
     cols_out(ctx, ctx->psi.p, nrhs, xi, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
+int cimmino_sweeps(cimmino_ctx *ctx, const double *f, int32_t nrhs, double omega,
+                   int32_t sweeps, double *x, int32_t on_device) {
+  if (!ctx || !f || !x) return CIMMINO_EINVAL;
+  try {
+    if (ctx->nsys != 1) fail(CIMMINO_EINVAL, "cimmino_sweeps needs a single-system context");
+    if (nrhs < 1 || sweeps < 0) fail(CIMMINO_EINVAL, "nrhs must be >= 1 and sweeps >= 0");
+    if (!std::isfinite(omega)) fail(CIMMINO_EINVAL, "omega must be finite");
+    (void)on_device;
+    ensure_solve_buffers(ctx, nrhs);
+    cudaStream_t s = ctx->stream;
+    const int64_t N = ctx->N;
+    CUDA_TRY(cudaMemsetAsync(ctx->cnt.p, 0, sizeof(int32_t) * 4 * ctx->nsys, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->refine_total.p, 0, sizeof(int64_t), s));
+    CUDA_TRY(cudaMemsetAsync(ctx->refine_max.p, 0, sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(ctx->x.p, 0, sizeof(double) * N * nrhs, s));
+    h2d(ctx->Fin.p, f, N * nrhs, s);
+    launch_rhs_scale(ctx->args, ctx->Fin.p, ctx->perm.p, s);
+    for (int32_t t = 0; t < sweeps; ++t) launch_cim_sweep(ctx->args, omega, s);
+    cols_out(ctx, ctx->x.p, nrhs, x, s);
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
     return CIMMINO_OK;

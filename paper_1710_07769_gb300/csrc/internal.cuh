@@ -26,6 +26,7 @@ constexpr int kMaxBlockRows = 4096;
 constexpr int kSpgemmWarpCap = 1024;   // candidates per row handled by one warp
 constexpr int kSpgemmCtaCap = 8192;    // candidates per row handled by one CTA
 constexpr int kMaxProjSlots = 16;      // factor-tile slots of the projection kernel's ring
+constexpr int kVecRows = 256;          // rows (= threads) per CTA of the CG vector kernels
 constexpr int kProjSmemMax = 231424;   // dynamic shared memory budget of one projection CTA
 // Packed triangular tiles (rectangular full packed): row pair p = 0..31 holds the entries of
 // rows p and 63 - p of a lower (or upper) triangular 64 x 64 tile, 65 values, padded to 68.
@@ -303,6 +304,8 @@ void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, 
 void launch_spmv_t(const IterArgs &a, const double *y, double *out, cudaStream_t s);
 void launch_cg_init(const IterArgs &a, cudaStream_t s);
 void launch_iteration(const IterArgs &a, cudaStream_t s);
+// one sweep of Algorithm 1: x += omega * sum_i A_i^+ (f_i - A_i x) (4 launches)
+void launch_cim_sweep(const IterArgs &a, double omega, cudaStream_t s);
 void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,
                         cudaStream_t s);
 void launch_row_abs(const int64_t *rp, const double *va, const double *d, int64_t N,

@@ -18,7 +18,7 @@ namespace cimmino {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kVecRows;  // one thread per row; CTA table rows per CTA
 constexpr int T = kTile;
 constexpr int kWarps = kThreads / 32;
 
@@ -276,6 +276,36 @@ __global__ void __launch_bounds__(kThreads) k_update_xr(IterArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// Algorithm 1 (block Cimmino with relaxation parameter omega, Section 1.1):
+//   x <- x + omega * sum_i A_i^+ (f_i - A_i x)
+// u = f_s - A x over the scaled permuted rows (the per-block residuals f_i - A_i x)
+__global__ void __launch_bounds__(kThreads) k_cim_residual(IterArgs a) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  if (threadIdx.x >= C.rows) return;
+  const int64_t r = C.row0 + threadIdx.x;
+  const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  const int64_t o = a.aoff[sl];
+  const int wd = (int)((a.aoff[sl + 1] - o) >> 5);
+  for (int k = 0; k < a.nrhs; ++k) {
+    double sx = 0.0;
+    for (int e = 0; e < wd; ++e)
+      sx = fma(a.aval[o + 32 * e + l], a.x[(int64_t)a.acol[o + 32 * e + l] * a.nrhs + k], sx);
+    a.u[r * a.nrhs + k] = a.fs[r * a.nrhs + k] - sx;
+  }
+}
+
+// x += omega psi (psi = sum_i A_i^T y_i, the sum of the block projections)
+__global__ void __launch_bounds__(kThreads) k_cim_update(IterArgs a, double omega) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  if (threadIdx.x >= C.rows) return;
+  const int64_t j = C.row0 + threadIdx.x;
+  for (int k = 0; k < a.nrhs; ++k) {
+    const int64_t o = j * a.nrhs + k;
+    a.x[o] = fma(omega, a.psi[o], a.x[o]);
+  }
+}
+
 // p = r + beta p, then t += 1
 __global__ void __launch_bounds__(kThreads) k_update_p(IterArgs a) {
   const CtaDesc C = a.cta[blockIdx.x];
@@ -381,6 +411,13 @@ void launch_iteration(const IterArgs &a, cudaStream_t s) {
   k_spmv_t<1><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
   k_update_xr<<<a.ncta, kThreads, 0, s>>>(a);
   k_update_p<<<a.ncta, kThreads, 0, s>>>(a);
+}
+
+void launch_cim_sweep(const IterArgs &a, double omega, cudaStream_t s) {
+  k_cim_residual<<<a.ncta, kThreads, 0, s>>>(a);
+  launch_proj(a, a.u, a.y, 0, s);
+  k_spmv_t<0><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
+  k_cim_update<<<a.ncta, kThreads, 0, s>>>(a, omega);
 }
 
 void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,

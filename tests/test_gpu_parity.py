@@ -334,3 +334,21 @@ def test_relaxed_inner_tolerance_converges():
     assert s1[0]["refine_steps_total"] < s0[0]["refine_steps_total"]
     assert abs(s1[0]["iters"] - s0[0]["iters"]) <= 1 + s0[0]["iters"] // 100
     assert rel(x1, x0) <= 1e-8
+
+
+# ------------------------------------------------------------------ Algorithm 1
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32_refine", 1e-9)])
+def test_cimmino_sweeps_match_oracle(sys_small, precision, tol):
+    """Algorithm 1 from x = 0 on the same setup: the first sweep is omega * xi, later
+    sweeps follow the oracle's iterates; two right-hand sides at once."""
+    A, perm, f = sys_small
+    s = g.Solver(A, RAGGED, perm=perm, precision=precision)
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    x1 = s.sweeps(f, 0.7, 1)
+    assert rel(x1, 0.7 * o.project_rhs(f)) <= tol
+    F = np.stack([f, inputs.matvec(A, np.random.default_rng(2).uniform(-1, 1, A.n))])
+    for sweeps in (5, 30):
+        X = s.sweeps(F, 1.3, sweeps)
+        for k in range(2):
+            assert rel(X[k], o.cimmino_sweeps(F[k], 1.3, sweeps)) <= tol, (sweeps, k)
