@@ -277,6 +277,311 @@ __global__ void __launch_bounds__(kThreads) k_update_xr(IterArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// The same four per-iteration vector steps for several right-hand sides (CG lanes):
+// right-hand sides in chunks of up to KC per row, so every entry of A (or A^T) is read
+// once per chunk instead of once per right-hand side, and a row's values [r][k0 .. k0+KC)
+// are contiguous; one block reduction covers a whole chunk.
+constexpr int KC = 8;
+
+// Sum over the CTA of v[0..kc) (fixed order: warp butterflies, then the warps in order),
+// written to part[base + kk].  red: at least KC * kWarps doubles.
+__device__ __forceinline__ void chunk_partials(double (&v)[KC], int kc, double *red, double *part,
+                                               int64_t base) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) v[kk] = warp_sum(v[kk]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) red[kk * kWarps + warp] = v[kk];
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)kc) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += red[threadIdx.x * kWarps + w];
+    part[base + threadIdx.x] = t;
+  }
+}
+
+// u = A p for all lanes and the residual of x (convergence decision of running lanes)
+__global__ void __launch_bounds__(kThreads) k_spmv_res_mr(IterArgs a) {
+  __shared__ double red[KC * kWarps];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t r = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  const int64_t o = a.aoff[sl];
+  const int wd = (int)((a.aoff[sl + 1] - o) >> 5);
+  for (int k0 = 0; k0 < a.nrhs; k0 += KC) {
+    const int kc = min(KC, a.nrhs - k0);
+    double e2[KC];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) e2[kk] = 0.0;
+    if (act) {
+      double su[KC], sx[KC];
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) su[kk] = sx[kk] = 0.0;
+      if (kc == KC && (a.nrhs & 1) == 0) {  // full chunk, 16-byte aligned: vector loads
+        for (int e = 0; e < wd; ++e) {
+          const double v = a.aval[o + 32 * e + l];
+          const int64_t c = (int64_t)a.acol[o + 32 * e + l] * a.nrhs + k0;
+          const double2 *pp = reinterpret_cast<const double2 *>(a.p + c);
+          const double2 *xx = reinterpret_cast<const double2 *>(a.x + c);
+#pragma unroll
+          for (int h = 0; h < KC / 2; ++h) {
+            const double2 pv = pp[h], xv = xx[h];
+            su[2 * h] = fma(v, pv.x, su[2 * h]);
+            su[2 * h + 1] = fma(v, pv.y, su[2 * h + 1]);
+            sx[2 * h] = fma(v, xv.x, sx[2 * h]);
+            sx[2 * h + 1] = fma(v, xv.y, sx[2 * h + 1]);
+          }
+        }
+      } else {
+        for (int e = 0; e < wd; ++e) {
+          const double v = a.aval[o + 32 * e + l];
+          const int64_t c = (int64_t)a.acol[o + 32 * e + l] * a.nrhs + k0;
+#pragma unroll
+          for (int kk = 0; kk < KC; ++kk)
+            if (kk < kc) {
+              su[kk] = fma(v, a.p[c + kk], su[kk]);
+              sx[kk] = fma(v, a.x[c + kk], sx[kk]);
+            }
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk)
+        if (kk < kc) {
+          const int64_t q = r * a.nrhs + k0 + kk;
+          a.u[q] = su[kk];
+          const double ev = a.d[r] * (a.fs[q] - sx[kk]);
+          e2[kk] = ev * ev;
+        }
+    }
+    chunk_partials(e2, kc, red, part_ptr(a, kPartRes), (int64_t)blockIdx.x * a.nrhs + k0);
+  }
+  if (arrive_last(a.cnt + kPartRes * a.nsys + C.sys, S.ncta)) {
+    for (int k = 0; k < a.nrhs; ++k) {
+      LaneState &L = a.lane[C.sys * a.nrhs + k];
+      if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+      double e2 = reduce_partials(part_ptr(a, kPartRes), S, a.nrhs, k, red);
+      if (threadIdx.x == 0) {
+        double rel = sqrt(e2 / L.fnorm2);
+        L.relres = rel;
+        if (rel <= a.tol) {
+          L.status = CIMMINO_CONVERGED;
+          L.iters = L.t;
+        } else if (L.t >= a.max_iter) {
+          L.status = CIMMINO_ENOCONV;
+          L.iters = L.t;
+        }
+      }
+    }
+  }
+}
+
+// psi = A^T y for all lanes, p^T psi -> alpha of running lanes
+__global__ void __launch_bounds__(kThreads) k_spmv_t_mr(IterArgs a) {
+  __shared__ double red[KC * kWarps];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  const int64_t o = a.toff[sl];
+  const int wd = (int)((a.toff[sl + 1] - o) >> 5);
+  for (int k0 = 0; k0 < a.nrhs; k0 += KC) {
+    const int kc = min(KC, a.nrhs - k0);
+    double pq[KC];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) pq[kk] = 0.0;
+    if (act) {
+      double sv[KC];
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) sv[kk] = 0.0;
+      if (kc == KC && (a.nrhs & 1) == 0) {  // full chunk, 16-byte aligned: vector loads
+        for (int e = 0; e < wd; ++e) {
+          const double v = a.tval[o + 32 * e + l];
+          const int64_t c = (int64_t)a.tcol[o + 32 * e + l] * a.nrhs + k0;
+          const double2 *yy = reinterpret_cast<const double2 *>(a.y + c);
+#pragma unroll
+          for (int h = 0; h < KC / 2; ++h) {
+            const double2 yv = yy[h];
+            sv[2 * h] = fma(v, yv.x, sv[2 * h]);
+            sv[2 * h + 1] = fma(v, yv.y, sv[2 * h + 1]);
+          }
+        }
+      } else {
+        for (int e = 0; e < wd; ++e) {
+          const double v = a.tval[o + 32 * e + l];
+          const int64_t c = (int64_t)a.tcol[o + 32 * e + l] * a.nrhs + k0;
+#pragma unroll
+          for (int kk = 0; kk < KC; ++kk)
+            if (kk < kc) sv[kk] = fma(v, a.y[c + kk], sv[kk]);
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk)
+        if (kk < kc) {
+          const int64_t q = j * a.nrhs + k0 + kk;
+          a.psi[q] = sv[kk];
+          pq[kk] = a.p[q] * sv[kk];
+        }
+    }
+    chunk_partials(pq, kc, red, part_ptr(a, kPartPq), (int64_t)blockIdx.x * a.nrhs + k0);
+  }
+  if (arrive_last(a.cnt + kPartPq * a.nsys + C.sys, S.ncta)) {
+    for (int k = 0; k < a.nrhs; ++k) {
+      LaneState &L = a.lane[C.sys * a.nrhs + k];
+      if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+      double pq = reduce_partials(part_ptr(a, kPartPq), S, a.nrhs, k, red);
+      if (threadIdx.x == 0) {
+        L.pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          L.status = CIMMINO_EBREAKDOWN;
+          L.iters = L.t;
+          L.alpha = 0.0;
+        } else {
+          L.alpha = L.rho[L.t & 1] / pq;
+        }
+      }
+    }
+  }
+}
+
+// x += alpha p, r -= alpha psi (running lanes), rho_{t+1} = r^T r, beta
+__global__ void __launch_bounds__(kThreads) k_update_xr_mr(IterArgs a) {
+  __shared__ double red[KC * kWarps];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  const bool act = threadIdx.x < C.rows;
+  const LaneState *LS = a.lane + (int64_t)C.sys * a.nrhs;
+  for (int k0 = 0; k0 < a.nrhs; k0 += KC) {
+    const int kc = min(KC, a.nrhs - k0);
+    double rr[KC];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) rr[kk] = 0.0;
+    if (act) {
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk)
+        if (kk < kc && LS[k0 + kk].status == CIMMINO_RUNNING) {
+          const double alpha = LS[k0 + kk].alpha;
+          const int64_t q = j * a.nrhs + k0 + kk;
+          a.x[q] = fma(alpha, a.p[q], a.x[q]);
+          const double rn = fma(-alpha, a.psi[q], a.r[q]);
+          a.r[q] = rn;
+          rr[kk] = rn * rn;
+        }
+    }
+    chunk_partials(rr, kc, red, part_ptr(a, kPartRr), (int64_t)blockIdx.x * a.nrhs + k0);
+  }
+  if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
+    for (int k = 0; k < a.nrhs; ++k) {
+      LaneState &L = a.lane[C.sys * a.nrhs + k];
+      if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+      double rr = reduce_partials(part_ptr(a, kPartRr), S, a.nrhs, k, red);
+      if (threadIdx.x == 0) {
+        const int par = L.t & 1;
+        L.rho[par ^ 1] = rr;
+        L.beta = rr / L.rho[par];
+      }
+    }
+  }
+}
+
+// p = r + beta p for running lanes, then t += 1
+__global__ void __launch_bounds__(kThreads) k_update_p_mr(IterArgs a) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int64_t j = C.row0 + threadIdx.x;
+  const LaneState *LS = a.lane + (int64_t)C.sys * a.nrhs;
+  if (threadIdx.x < C.rows)
+    for (int k = 0; k < a.nrhs; ++k)
+      if (LS[k].status == CIMMINO_RUNNING) {
+        const int64_t q = j * a.nrhs + k;
+        a.p[q] = fma(LS[k].beta, a.p[q], a.r[q]);
+      }
+  if (blockIdx.x == (unsigned)S.cta0) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.nrhs; k += kThreads) {
+      LaneState &L = a.lane[C.sys * a.nrhs + k];
+      if (L.status == CIMMINO_RUNNING) L.t += 1;
+    }
+  }
+}
+
+// Flattened element-wise updates for nrhs dividing 32: consecutive threads touch
+// consecutive (row, lane) entries of the [row][nrhs] vectors (coalesced), and a thread
+// always meets the same lane k = threadIdx.x mod nrhs, so r^T r per lane is a fixed
+// shuffle tree over the lanes of a warp with equal k, then the warps in order.
+__global__ void __launch_bounds__(kThreads) k_update_xr_fl(IterArgs a) {
+  __shared__ double red[kWarps * 32];
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int nr = a.nrhs, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = threadIdx.x % nr;
+  const LaneState &Lk = a.lane[C.sys * nr + k];
+  const bool run = Lk.status == CIMMINO_RUNNING;
+  const double alpha = Lk.alpha;
+  double rr = 0.0;
+  const int64_t base = C.row0 * nr, cnt = (int64_t)C.rows * nr;
+  if (run)
+    for (int64_t e = threadIdx.x; e < cnt; e += kThreads) {
+      const int64_t q = base + e;
+      a.x[q] = fma(alpha, a.p[q], a.x[q]);
+      const double rn = fma(-alpha, a.psi[q], a.r[q]);
+      a.r[q] = rn;
+      rr += rn * rn;
+    }
+  for (int o = nr; o < 32; o <<= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  if (lane < nr) red[warp * 32 + lane] = rr;
+  __syncthreads();
+  if (threadIdx.x < (unsigned)nr) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += red[w * 32 + threadIdx.x];
+    part_ptr(a, kPartRr)[(int64_t)blockIdx.x * nr + threadIdx.x] = t;
+  }
+  if (arrive_last(a.cnt + kPartRr * a.nsys + C.sys, S.ncta)) {
+    for (int kk = 0; kk < nr; ++kk) {
+      LaneState &L = a.lane[C.sys * nr + kk];
+      if (L.status != CIMMINO_RUNNING) continue;  // uniform: read before any update
+      double rs = reduce_partials(part_ptr(a, kPartRr), S, nr, kk, red);
+      if (threadIdx.x == 0) {
+        const int par = L.t & 1;
+        L.rho[par ^ 1] = rs;
+        L.beta = rs / L.rho[par];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_update_p_fl(IterArgs a) {
+  const CtaDesc C = a.cta[blockIdx.x];
+  const SysDesc S = a.sys[C.sys];
+  const int nr = a.nrhs;
+  const int k = threadIdx.x % nr;
+  const LaneState &Lk = a.lane[C.sys * nr + k];
+  if (Lk.status == CIMMINO_RUNNING) {
+    const double beta = Lk.beta;
+    const int64_t base = C.row0 * nr, cnt = (int64_t)C.rows * nr;
+    for (int64_t e = threadIdx.x; e < cnt; e += kThreads) {
+      const int64_t q = base + e;
+      a.p[q] = fma(beta, a.p[q], a.r[q]);
+    }
+  }
+  if (blockIdx.x == (unsigned)S.cta0) {
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nr) {
+      LaneState &L = a.lane[C.sys * nr + threadIdx.x];
+      if (L.status == CIMMINO_RUNNING) L.t += 1;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Algorithm 1 (block Cimmino with relaxation parameter omega, Section 1.1):
 //   x <- x + omega * sum_i A_i^+ (f_i - A_i x)
 // u = f_s - A x over the scaled permuted rows (the per-block residuals f_i - A_i x)
@@ -406,6 +711,19 @@ void launch_cg_init(const IterArgs &a, cudaStream_t s) {
 }
 
 void launch_iteration(const IterArgs &a, cudaStream_t s) {
+  if (a.nrhs > 1) {
+    k_spmv_res_mr<<<a.ncta, kThreads, 0, s>>>(a);
+    launch_proj(a, a.u, a.y, 1, s);
+    k_spmv_t_mr<<<a.ncta, kThreads, 0, s>>>(a);
+    if (32 % a.nrhs == 0) {
+      k_update_xr_fl<<<a.ncta, kThreads, 0, s>>>(a);
+      k_update_p_fl<<<a.ncta, kThreads, 0, s>>>(a);
+    } else {
+      k_update_xr_mr<<<a.ncta, kThreads, 0, s>>>(a);
+      k_update_p_mr<<<a.ncta, kThreads, 0, s>>>(a);
+    }
+    return;
+  }
   k_spmv_res<<<a.ncta, kThreads, 0, s>>>(a);
   launch_proj(a, a.u, a.y, 1, s);
   k_spmv_t<1><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
