@@ -49,9 +49,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                // descriptor version; no swizzle
   return d;
 }
-// D f32, A/B tf32, both K-major, N = 128, M = 128
+// D f32, A/B tf32, both K-major, M = 128, N = 128 (trailing update) or 64 (TRSM)
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) |
                             ((128u >> 4) << 24);
+constexpr uint32_t kIdescN64 = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
+                               ((128u >> 4) << 24);
+constexpr int kStLd = T + 4;  // padded row of the TRSM epilogue staging area (floats)
 
 // byte offset of element (r, k) of a 128 x 64 operand in the canonical layout
 __device__ __forceinline__ uint32_t canon(int r, int k) {
@@ -105,12 +108,57 @@ __device__ __forceinline__ float *tile_ptr(float *fac, const TileRow &tr, int J)
   return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc,
+                                         uint32_t idesc = kIdesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
+}
+
+// One thread issues D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K = 64 (3xTF32, 24
+// MMAs) and commits them to mbar; every thread then waits for the commit (bounded: about
+// 2 s, after which s_err and bit 4 of the error word are set and the kernel winds down).
+__device__ __forceinline__ void mma_3xtf32(uint32_t tmem, const unsigned char *Ahi,
+                                           const unsigned char *Alo, const unsigned char *Bhi,
+                                           const unsigned char *Blo, uint32_t idesc,
+                                           uint64_t *mbar, uint32_t &phase, int *s_err,
+                                           int32_t *err) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (threadIdx.x == 0) {
+    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+    for (int s = 0; s < T / 8; ++s) {
+      const uint32_t ko = s * 2 * kCoreK;  // K = 8 per MMA: two core matrices
+      mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), s > 0, idesc);
+      mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), 1, idesc);
+      mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), 1, idesc);
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(mbar))
+        : "memory");
+  }
+  uint32_t ok = 0;
+  const uint64_t t0 = global_ns();
+  while (!ok) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(phase)
+        : "memory");
+    if (!ok && global_ns() - t0 > kWaitNs) {
+      *s_err = 1;
+      atomicOr(err, 4);
+      break;
+    }
+  }
+  phase ^= 1u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
@@ -168,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float *S = Bt + T * LD;                              // [T][LDS]
   float *Di = S + T * LDS;                             // [T][LDS]
   float *Dst = reinterpret_cast<float *>(Bhi);  // [128][kDstLd] epilogue staging (B, At)
+  float *St = At;  // [128][kStLd] TRSM epilogue staging (At, Bt, S)
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ double s_pmin;
@@ -275,25 +324,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 4; ++j) gKJ[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
     }
     __syncthreads();
-    // ---- 3. L_IK = G_IK inv(L_KK)^T (CUDA cores)
-    for (int e = tid; e < T * T; e += kThreads) {
-      int k = e / T, c = e % T;
-      Bt[k * LD + c] = Di[c * LDS + k];
-    }
-    __syncthreads();
-    for (int I = K + 1; I < B.nt; ++I) {
-      const TileRow TI = tr[I];
-      if (TI.j0 > K) continue;
-      float *gIK = tile_ptr(fac, TI, K);
-      for (int e = tid; e < T * T; e += kThreads) At[(e % T) * LD + (e / T)] = gIK[e];
-      __syncthreads();
-      float acc[4][4] = {};
-      mma_4x4(At, Bt, acc);
+    // ---- 3. L_IK = G_IK inv(L_KK)^T on the tensor cores, pairs of tile rows:
+    // D (128 x 64) = [G_I0K; G_I1K] inv(L_KK)^T, i.e. B = inv(L_KK) (K-major rows, read
+    // back from dK); D goes through a padded staging area (the CUDA-core scratch At, Bt,
+    // S, free by now) into coalesced 16-byte stores
+    __syncthreads();  // dK is complete
+    load_split2(dK, nullptr, Bhi, Blo);
+    for (int I0 = K + 1; I0 < B.nt && !s_err; I0 += 2) {
+      const int I1 = I0 + 1;
+      const bool has0 = tr[I0].j0 <= K;
+      const bool has1 = I1 < B.nt && tr[I1].j0 <= K;
+      if (!has0 && !has1) continue;
+      float *g0 = has0 ? tile_ptr(fac, tr[I0], K) : nullptr;
+      float *g1 = has1 ? tile_ptr(fac, tr[I1], K) : nullptr;
+      load_split2(g0, g1, Ahi, Alo);
+      mma_3xtf32(tmem, Ahi, Alo, Bhi, Blo, kIdescN64, &mbar, phase, &s_err, err);
+      if (warp < 4) {  // warp w reads TMEM lanes 32 w .. 32 w + 31, columns 0..63
+        const int rr = 32 * warp + lane;
+        float v[64];
+        tmem_ld64(tmem + ((uint32_t)(32 * warp) << 16), v);
+        float *st = St + rr * kStLd;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) gIK[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+        for (int c = 0; c < 64; c += 4)
+          *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+      }
       __syncthreads();
+      if (!s_err) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float *gq = q ? g1 : g0;
+          if (!gq) continue;
+          for (int e = tid; e < T * T / 4; e += kThreads) {
+            const int r = e >> 4, c = 4 * (e & 15);
+            *reinterpret_cast<float4 *>(gq + r * T + c) =
+                *reinterpret_cast<const float4 *>(St + (64 * q + r) * kStLd + c);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     // ---- 4. trailing update on the tensor cores: pairs of tile rows x pairs of tile columns
     for (int I0 = K + 1; I0 < B.nt && !s_err; I0 += 2) {
@@ -311,43 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!hj0 && !hj1) continue;
         load_split2(hj0 ? tile_ptr(fac, tr[J0], K) : nullptr,
                     hj1 ? tile_ptr(fac, tr[J1], K) : nullptr, Bhi, Blo);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-          const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi),
-                         bl = smem_u32(Blo);
-          for (int s = 0; s < T / 8; ++s) {
-            const uint32_t ko = s * 2 * kCoreK;  // K = 8 per MMA: two core matrices
-            mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), s > 0);
-            mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), 1);
-            mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), 1);
-          }
-          asm volatile(
-              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&mbar))
-              : "memory");
-        }
-        {  // bounded wait for the MMAs
-          uint32_t ok = 0;
-          const uint64_t t0 = global_ns();
-          while (!ok) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                "selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(ok)
-                : "r"(smem_u32(&mbar)), "r"(phase)
-                : "memory");
-            if (!ok && global_ns() - t0 > kWaitNs) {
-              s_err = 1;
-              atomicOr(err, 4);
-              break;
-            }
-          }
-          phase ^= 1u;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        mma_3xtf32(tmem, Ahi, Alo, Bhi, Blo, kIdesc, &mbar, phase, &s_err, err);
         // epilogue: warp w reads lanes 32 (w mod 4).. and column half w / 4 of D into the
         // staging area (the B operands, free once the MMAs completed; rows padded to 132
         // floats so that a quarter-warp's 16-byte stores hit 8 distinct bank groups), then
@@ -419,8 +453,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 constexpr int kTcSmem = 4 * 32768 + (int)sizeof(float) * (2 * T * LD + 2 * T * LDS);
-// the epilogue staging area (128 x kDstLd floats from Bhi) fits in Bhi, Blo and At
+// the epilogue staging area (128 x kDstLd floats from Bhi) fits in Bhi, Blo and At; the
+// TRSM staging area (128 x kStLd floats from At) in At, Bt and S, short of Di
 static_assert(128 * kDstLd * 4 <= 2 * 32768 + (int)sizeof(float) * T * LD, "staging area");
+static_assert(128 * kStLd <= 2 * T * LD + T * LDS, "TRSM staging area");
 
 }  // namespace
 
