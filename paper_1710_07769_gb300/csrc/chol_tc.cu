@@ -104,6 +104,46 @@ __device__ __forceinline__ void load_split2(const float *__restrict__ g0,
     }
 }
 
+// Transposed operand layout (second canonical no-swizzle K-major form): core matrices of
+// 8 rows x 16 bytes, 8-row groups 128 bytes apart, K chunks of 4 values 2048 bytes apart.
+constexpr uint32_t kTCoreK = 2048;  // bytes between core matrices along K
+constexpr uint32_t kTCoreRow = 128; // bytes between 8-row groups
+__device__ __forceinline__ uint64_t smem_desc_t(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(kTCoreK >> 4) << 16;
+  d |= (uint64_t)(kTCoreRow >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// B operand rows 0..63 = columns of g0, rows 64..127 = columns of g1 (B[n][k] = g[k][n]),
+// hi/lo split, in the transposed layout: in every step a warp stores 8 rows x 4 k values,
+// 32 consecutive words (conflict-free); the loads read 4 rows x 32 contiguous bytes.
+__device__ __forceinline__ void load_split2_t(const float *__restrict__ g0,
+                                              const float *__restrict__ g1, unsigned char *hi,
+                                              unsigned char *lo) {
+  const int tid = threadIdx.x, kk = tid & 3;
+  constexpr int IT = 128 * T / kThreads;  // 32 values per thread
+#pragma unroll 4
+  for (int h = 0; h < IT; h += 8) {
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int it = h + j, k4 = it & 15, n = (tid >> 2) + 64 * (it >> 4);
+      const float *g = n < 64 ? g0 : g1;
+      x[j] = g ? g[(4 * k4 + kk) * T + (n & 63)] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int it = h + j, k4 = it & 15, n = (tid >> 2) + 64 * (it >> 4);
+      const uint32_t o = (uint32_t)(k4 * kTCoreK + (n >> 3) * kTCoreRow + (n & 7) * 16 + kk * 4);
+      const float t = tf32_hi(x[j]);
+      *reinterpret_cast<float *>(hi + o) = t;
+      *reinterpret_cast<float *>(lo + o) = x[j] - t;
+    }
+  }
+}
+
 __device__ __forceinline__ float *tile_ptr(float *fac, const TileRow &tr, int J) {
   return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
 }
@@ -120,6 +160,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
 // One thread issues D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K = 64 (3xTF32, 24
 // MMAs) and commits them to mbar; every thread then waits for the commit (bounded: about
 // 2 s, after which s_err and bit 4 of the error word are set and the kernel winds down).
+// BT: B is in the transposed layout (smem_desc_t, K chunks kTCoreK apart).
+template <bool BT = false>
 __device__ __forceinline__ void mma_3xtf32(uint32_t tmem, const unsigned char *Ahi,
                                            const unsigned char *Alo, const unsigned char *Bhi,
                                            const unsigned char *Blo, uint32_t idesc,
@@ -133,9 +175,12 @@ __device__ __forceinline__ void mma_3xtf32(uint32_t tmem, const unsigned char *A
     const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
     for (int s = 0; s < T / 8; ++s) {
       const uint32_t ko = s * 2 * kCoreK;  // K = 8 per MMA: two core matrices
-      mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bh + ko), s > 0, idesc);
-      mma_tf32(tmem, smem_desc(ah + ko), smem_desc(bl + ko), 1, idesc);
-      mma_tf32(tmem, smem_desc(al + ko), smem_desc(bh + ko), 1, idesc);
+      const uint32_t kb = s * 2 * (BT ? kTCoreK : kCoreK);
+      const uint64_t bdh = BT ? smem_desc_t(bh + kb) : smem_desc(bh + kb);
+      const uint64_t bdl = BT ? smem_desc_t(bl + kb) : smem_desc(bl + kb);
+      mma_tf32(tmem, smem_desc(ah + ko), bdh, s > 0, idesc);
+      mma_tf32(tmem, smem_desc(ah + ko), bdl, 1, idesc);
+      mma_tf32(tmem, smem_desc(al + ko), bdh, 1, idesc);
     }
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -182,23 +227,6 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// acc(r, c) for the thread's 4 x 4 block: sum_k At[k][r] * Bt[k][c] (CUDA cores)
-__device__ __forceinline__ void mma_4x4(const float *At, const float *Bt, float acc[4][4]) {
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
-#pragma unroll 8
-  for (int k = 0; k < T; ++k) {
-    float a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = At[k * LD + tr * 4 + i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = Bt[k * LD + tc * 4 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -306,24 +334,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       gKK[e] = c <= r ? S[r * LDS + c] : 0.f;
       dK[e] = c <= r ? Di[r * LDS + c] : 0.f;
     }
-    // N_KJ = inv(L_KK) L_KJ for the final row K (CUDA cores)
-    for (int e = tid; e < T * T; e += kThreads) {
-      int k = e / T, r = e % T;
-      At[k * LD + r] = Di[r * LDS + k];
-    }
-    for (int J = TK.j0; J < K; ++J) {
-      float *gKJ = tile_ptr(fac, TK, J);
-      __syncthreads();
-      for (int e = tid; e < T * T; e += kThreads) Bt[(e / T) * LD + (e % T)] = gKJ[e];
-      __syncthreads();
-      float acc[4][4] = {};
-      mma_4x4(At, Bt, acc);
+    // N_KJ = inv(L_KK) L_KJ for the final row K on the tensor cores, pairs of tiles:
+    // D (128 x 128) = [inv(L_KK); 0] [L_KJ0 L_KJ1] (rows 64..127 of A are zero, so half of
+    // D is unused), A = inv(L_KK) read back from dK, B row n = column n of the pair in the
+    // transposed layout; rows 0..63 of D go through the padded staging area (At, Bt, S)
+    __syncthreads();  // dK is complete
+    if (TK.j0 < K) load_split2(dK, nullptr, Ahi, Alo);
+    for (int J0 = TK.j0; J0 < K && !s_err; J0 += 2) {
+      const bool has1 = J0 + 1 < K;
+      float *g0 = tile_ptr(fac, TK, J0);
+      float *g1 = has1 ? tile_ptr(fac, TK, J0 + 1) : nullptr;
+      load_split2_t(g0, g1, Bhi, Blo);
+      mma_3xtf32<true>(tmem, Ahi, Alo, Bhi, Blo, kIdesc, &mbar, phase, &s_err, err);
+      if ((warp & 3) < 2) {  // TMEM lanes 0..63 (warps 0, 1, 4, 5), column half warp / 4
+        const int rr = 32 * (warp & 3) + lane, jh = warp >> 2;
+        float v[64];
+        tmem_ld64(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * jh), v);
+        float *st = St + rr * kDstLd + 64 * jh;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 64; c += 4)
+          *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+      }
+      __syncthreads();
+      if (!s_err) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) gKJ[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+        for (int q = 0; q < 2; ++q) {
+          float *gq = q ? g1 : g0;
+          if (!gq) continue;
+          for (int e = tid; e < T * T / 4; e += kThreads) {
+            const int r = e >> 4, c = 4 * (e & 15);
+            *reinterpret_cast<float4 *>(gq + r * T + c) =
+                *reinterpret_cast<const float4 *>(St + r * kDstLd + 64 * q + c);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    __syncthreads();
     // ---- 3. L_IK = G_IK inv(L_KK)^T on the tensor cores, pairs of tile rows:
     // D (128 x 64) = [G_I0K; G_I1K] inv(L_KK)^T, i.e. B = inv(L_KK) (K-major rows, read
     // back from dK); D goes through a padded staging area (the CUDA-core scratch At, Bt,
@@ -457,6 +505,7 @@ constexpr int kTcSmem = 4 * 32768 + (int)sizeof(float) * (2 * T * LD + 2 * T * L
 // TRSM staging area (128 x kStLd floats from At) in At, Bt and S, short of Di
 static_assert(128 * kDstLd * 4 <= 2 * 32768 + (int)sizeof(float) * T * LD, "staging area");
 static_assert(128 * kStLd <= 2 * T * LD + T * LDS, "TRSM staging area");
+static_assert(64 * kDstLd <= 2 * T * LD + T * LDS, "N-transform staging area");
 
 }  // namespace
 
