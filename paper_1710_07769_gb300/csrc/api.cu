@@ -129,7 +129,7 @@ struct cimmino_ctx {
   DBuf<TileRow> trow;
   DBuf<SysDesc> sys;
   DBuf<CtaDesc> cta;
-  DBuf<float> fac32, dinv32, facT32, dinvT32;
+  DBuf<float> fac32, dinv32, facT32, dinvT32, dinvP32, dinvTP32;
   DBuf<double> fac64, dinv64, facT64, dinvT64, dinvP64, dinvTP64;
   DBuf<TileRow> trowT;
   std::vector<TileRow> htrowT;
@@ -559,28 +559,34 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
         ntiles += (I - c->htrow[B.trow0 + I].j0) + (j1 - I) + 2;
       }
     }
-    // bytes one single-vector solve pass streams: the N and NT rows and the two diagonal
-    // tiles inv(L_II), inv(L_II)^T of every tile row (packed triangles in FP64)
+    // bytes one single-vector solve pass streams: the N and NT rows and the two packed
+    // diagonal tiles inv(L_II), inv(L_II)^T of every tile row
     c->pass_bytes = 0;
     for (const auto &B : c->hblk) {
       int64_t t = 0;
       for (int32_t I = 0; I < B.nt; ++I)
         t += (I - c->htrow[B.trow0 + I].j0) + (c->htrowT[B.trow0 + I].j0 - I);
-      c->pass_bytes += (t * TT + 2 * (int64_t)B.nt * (B.prec64 ? kPackTile : TT)) * (B.prec64 ? 8 : 4);
+      c->pass_bytes +=
+          (t * TT + 2 * (int64_t)B.nt * (B.prec64 ? kPackTile : kBPackTile)) * (B.prec64 ? 8 : 4);
     }
     (void)ntiles;
     c->trowT.alloc(ntrow);
     h2d(c->trowT.p, c->htrowT.data(), ntrow, s);
     if (oT32) c->facT32.alloc(oT32);
     if (oT64) c->facT64.alloc(oT64);
-    if (c->dinv32.p) c->dinvT32.alloc(c->dinv32.n);
+    if (c->dinv32.p) {
+      c->dinvT32.alloc(c->dinv32.n);
+      c->dinvP32.alloc(c->dinv32.n / TT * kBPackTile);
+      c->dinvTP32.alloc(c->dinv32.n / TT * kBPackTile);
+    }
     if (c->dinv64.p) {
       c->dinvT64.alloc(c->dinv64.n);
       c->dinvP64.alloc(c->dinv64.n / TT * kPackTile);
       c->dinvTP64.alloc(c->dinv64.n / TT * kPackTile);
     }
-    FactorPtrs f{c->fac32.p, c->dinv32.p, c->facT32.p, c->dinvT32.p, c->fac64.p,
-                 c->dinv64.p, c->facT64.p, c->dinvT64.p, c->dinvP64.p, c->dinvTP64.p};
+    FactorPtrs f{c->fac32.p,   c->dinv32.p,   c->facT32.p, c->dinvT32.p,
+                 c->fac64.p,   c->dinv64.p,   c->facT64.p, c->dinvT64.p,
+                 c->dinvP64.p, c->dinvTP64.p, c->dinvP32.p, c->dinvTP32.p};
     launch_transpose_factor(c->blk.p, nblk, c->trow.p, c->trowT.p, f, s);
     c->setup_launches += 2;  // transposed copies, packed diagonal tiles
   }
@@ -713,6 +719,8 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.dinv64 = c->dinv64.p;
   a.facT64 = c->facT64.p;
   a.dinvT64 = c->dinvT64.p;
+  a.dinvP32 = c->dinvP32.p;
+  a.dinvTP32 = c->dinvTP32.p;
   a.dinvP64 = c->dinvP64.p;
   a.dinvTP64 = c->dinvTP64.p;
   a.sys = c->sys.p;

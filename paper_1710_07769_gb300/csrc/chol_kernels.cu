@@ -278,10 +278,42 @@ __device__ void pack_block(const BlockDesc &B, const W *__restrict__ dinv,
   }
 }
 
+// Block-packed copies for FP32 blocks: row pair p (b = p / 16) holds, for the lower tile,
+// row p columns 0 .. 16 (b + 1) - 1 and then row 63 - p columns 0 .. 16 (4 - b) - 1; for
+// the upper tile row p columns 16 b .. 63 and then row 63 - p columns 16 (3 - b) .. 63;
+// 80 values (entries outside the triangle inside a diagonal sub-tile are zero), padded to
+// kBPackPair.
+__device__ void bpack_block(const BlockDesc &B, const float *__restrict__ dinv,
+                            const float *__restrict__ dinvT, float *__restrict__ P,
+                            float *__restrict__ PT) {
+  const int64_t o = B.dinv_off, op = B.dinv_off / (T * T) * kBPackTile;
+  for (int64_t e = threadIdx.x; e < (int64_t)B.nt * kBPackTile; e += kThreads) {
+    const int I = (int)(e / kBPackTile), q = (int)(e % kBPackTile);
+    const int p = q / kBPackPair, j = q % kBPackPair, b = p / 16;
+    const float *D = dinv + o + (int64_t)I * T * T;
+    const float *DT = dinvT + o + (int64_t)I * T * T;
+    const int la = 16 * (b + 1), ua = 16 * (4 - b);  // entries of the pair's first row
+    float lv = 0.f, uv = 0.f;
+    if (j < la)
+      lv = D[p * T + j];
+    else if (j < 80)
+      lv = D[(63 - p) * T + (j - la)];
+    if (j < ua)
+      uv = DT[p * T + 16 * b + j];
+    else if (j < 80)
+      uv = DT[(63 - p) * T + 16 * (3 - b) + (j - ua)];
+    P[op + e] = lv;
+    PT[op + e] = uv;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_pack_diag(const BlockDesc *__restrict__ blk, FactorPtrs f) {
   const BlockDesc B = blk[blockIdx.x];
-  if (B.prec64) pack_block<double>(B, f.dinv64, f.dinvT64, f.dinvP64, f.dinvTP64);
+  if (B.prec64)
+    pack_block<double>(B, f.dinv64, f.dinvT64, f.dinvP64, f.dinvTP64);
+  else
+    bpack_block(B, f.dinv32, f.dinvT32, f.dinvP32, f.dinvTP32);
 }
 
 __global__ void __launch_bounds__(kThreads)

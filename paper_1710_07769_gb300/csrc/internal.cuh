@@ -32,6 +32,10 @@ constexpr int kProjSmemMax = 231424;   // dynamic shared memory budget of one pr
 // rows p and 63 - p of a lower (or upper) triangular 64 x 64 tile, 65 values, padded to 68.
 constexpr int kPackPair = 68;
 constexpr int kPackTile = 32 * kPackPair;  // 2176 entries instead of 4096
+// Block-packed triangular tiles (FP32): row pair p holds the 16-wide sub-tile segments of
+// rows p and 63 - p inside the triangle, 5 segments = 80 values, padded to 84.
+constexpr int kBPackPair = 84;
+constexpr int kBPackTile = 32 * kBPackPair;  // 2688 entries instead of 4096
 
 struct BlockDesc {
   int64_t row0;      // first global (permuted, concatenated) row
@@ -196,6 +200,8 @@ struct FactorPtrs {
   double *dinvT64;
   double *dinvP64;   // packed inv(L_II) (lower) and inv(L_II)^T (upper) of FP64 blocks,
   double *dinvTP64;  // kPackTile entries per tile
+  float *dinvP32;    // block-packed ones of FP32 blocks, kBPackTile entries per tile
+  float *dinvTP32;
 };
 
 // chol_tc.cu: FP32 blocks, trailing update on the tensor cores (tcgen05, 3xTF32)
@@ -244,6 +250,8 @@ struct IterArgs {
   const double *dinvT64;
   const double *dinvP64;  // packed triangular inv(L_II), inv(L_II)^T of FP64 blocks
   const double *dinvTP64;
+  const float *dinvP32;   // block-packed ones of FP32 blocks
+  const float *dinvTP32;
   const SysDesc *sys;
   const CtaDesc *cta;
   LaneState *lane;

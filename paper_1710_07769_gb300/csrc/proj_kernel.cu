@@ -13,9 +13,9 @@
 //    shared-memory slots in the consumers' order.  full[s] completes when a copy lands,
 //    empty[s] when all 8 consumer warps have passed the slot.  Every wait is bounded; a
 //    wait that runs out sets the error flag and the kernel finishes without waiting again.
-//  * inv(L_II) and its transpose (independent tile rows): one warp computes a tile, no
-//    reduction.  FP64 blocks stream them as packed triangles (rectangular full packed,
-//    2176 of 4096 entries, a lane per row pair (p, 63 - p)); FP32 blocks as full tiles.
+//  * inv(L_II) and its transpose (independent tile rows): one warp computes a tile, a lane
+//    per row pair (p, 63 - p), no reduction.  They are streamed as packed triangles:
+//    rectangular full packed in FP64 (2176 of 4096 values), block-packed in FP32 (2688).
 //    Every consumer warp waits for and releases every slot in order, so a warp never waits on a slot more than one use ahead (which would
 //    make the mbarrier phase parity ambiguous).
 //  * Chain steps: thread (rg, cg) owns rows 4rg..4rg+3 and four columns of each tile
@@ -67,29 +67,55 @@ __device__ __forceinline__ void tile_rows(const double *L, const double *v, int 
   }
 }
 
-// Whole tile times v by one warp (FP32 blocks): lane l owns rows l and l+32 and walks the
-// 16-byte chunks of its rows in the order (k + l) mod 16, so the 8 lanes of a quarter-warp
-// always touch 8 distinct bank groups; four independent accumulators, no reduction.
-__device__ __forceinline__ void tile_rows_warp(const float *D, const float *v, float *o, int lane) {
-  const float4 *R0 = reinterpret_cast<const float4 *>(D + lane * T);
-  const float4 *R1 = reinterpret_cast<const float4 *>(D + (lane + 32) * T);
+// Block-packed triangular tile times v by one warp (FP32 blocks).  Lane p owns row pair
+// (p, 63 - p), b = p / 16: the pair's 80 values are 20 16-byte chunks of whole 16-wide
+// sub-tile segments, so every chunk multiplies one aligned chunk of v (a broadcast within
+// each half-warp).  The chunks split into three fixed ranges: those of the first row,
+// those of the second row, and 4 in the middle whose row depends on the half-warp.  Pair
+// stride 336 bytes: a quarter-warp's 16-byte loads hit 8 distinct bank groups.
+//   lower (inv(L_II)):   row p columns 0 .. 16 (b+1) - 1, row 63 - p columns 0 .. 16 (4-b) - 1
+//   upper (inv(L_II)^T): row p columns 16 b .. 63,        row 63 - p columns 16 (3-b) .. 63
+__device__ __forceinline__ void dot4(float4 d, float4 x, float &s0, float &s1) {
+  s0 = fmaf(d.x, x.x, s0);
+  s1 = fmaf(d.y, x.y, s1);
+  s0 = fmaf(d.z, x.z, s0);
+  s1 = fmaf(d.w, x.w, s1);
+}
+template <bool UPPER>
+__device__ __forceinline__ void bpacked_rows_warp(const float *P, const float *v, float *o,
+                                                  int p) {
+  const float4 *R = reinterpret_cast<const float4 *>(P + p * kBPackPair);
   const float4 *V = reinterpret_cast<const float4 *>(v);
-  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-#pragma unroll 8
-  for (int k = 0; k < T / 4; ++k) {
-    const int ch = (k + lane) & (T / 4 - 1);
-    const float4 x = V[ch], p = R0[ch], q = R1[ch];
-    a0 = fma(p.x, x.x, a0);
-    a1 = fma(p.y, x.y, a1);
-    a0 = fma(p.z, x.z, a0);
-    a1 = fma(p.w, x.w, a1);
-    b0 = fma(q.x, x.x, b0);
-    b1 = fma(q.y, x.y, b1);
-    b0 = fma(q.z, x.z, b0);
-    b1 = fma(q.w, x.w, b1);
+  const int b = p >> 4;
+  float a0 = 0.f, a1 = 0.f, c0 = 0.f, c1 = 0.f;
+  if (!UPPER) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dot4(R[q], V[q], a0, a1);
+    if (b) {
+#pragma unroll
+      for (int q = 4; q < 8; ++q) dot4(R[q], V[q], a0, a1);
+    } else {
+#pragma unroll
+      for (int q = 4; q < 8; ++q) dot4(R[q], V[q - 4], c0, c1);
+    }
+    const int sh = 4 * (b + 1);
+#pragma unroll
+    for (int q = 8; q < 20; ++q) dot4(R[q], V[q - sh], c0, c1);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) dot4(R[q], V[4 * b + q], a0, a1);
+    if (!b) {
+#pragma unroll
+      for (int q = 12; q < 16; ++q) dot4(R[q], V[q], a0, a1);
+    } else {
+#pragma unroll
+      for (int q = 12; q < 16; ++q) dot4(R[q], V[q - 4], c0, c1);
+    }
+#pragma unroll
+    for (int q = 16; q < 20; ++q) dot4(R[q], V[q - 4], c0, c1);
   }
-  o[lane] = a0 + a1;
-  o[lane + 32] = b0 + b1;
+  o[p] = a0 + a1;
+  o[T - 1 - p] = c0 + c1;
 }
 
 // Packed triangular tile times v by one warp (FP64 blocks, where every FMA counts on
@@ -136,12 +162,12 @@ __device__ __forceinline__ void packed_rows_warp(const W *P, const W *v, W *o, i
   o[T - 1 - p] = acc;
 }
 
-// Diagonal-tile products: FP32 blocks stream full tiles of inv(L_II) and inv(L_II)^T
-// (bandwidth-bound: the vectorised full-tile product is cheaper than unpacking), FP64
-// blocks stream the packed triangles (FP64-bound: 68 instead of 128 FMAs per lane).
+// Diagonal-tile products: FP32 blocks stream block-packed triangles of inv(L_II) and
+// inv(L_II)^T (2688 of 4096 values, aligned vector reads), FP64 blocks the rectangular full
+// packed ones (FP64-bound: 68 instead of 128 FMAs per lane).
 template <bool UPPER>
 __device__ __forceinline__ void diag_rows(const float *D, const float *v, float *o, int lane) {
-  tile_rows_warp(D, v, o, lane);
+  bpacked_rows_warp<UPPER>(D, v, o, lane);
 }
 template <bool UPPER>
 __device__ __forceinline__ void diag_rows(const double *D, const double *v, double *o, int lane) {
@@ -337,15 +363,15 @@ __device__ void producer_block(const IterArgs &a, const BlockDesc &B, const Ring
                                  : reinterpret_cast<const unsigned char *>(a.fac32);
   const unsigned char *facT = p64 ? reinterpret_cast<const unsigned char *>(a.facT64)
                                   : reinterpret_cast<const unsigned char *>(a.facT32);
-  // diagonal tiles: packed triangles for FP64 blocks, full tiles for FP32 blocks
-  const int64_t po = B.dinv_off / (T * T) * kPackTile;
-  const unsigned char *dinv = p64 ? reinterpret_cast<const unsigned char *>(a.dinvP64 + po)
-                                  : reinterpret_cast<const unsigned char *>(a.dinv32 + B.dinv_off);
-  const unsigned char *dinvT = p64
-                                   ? reinterpret_cast<const unsigned char *>(a.dinvTP64 + po)
-                                   : reinterpret_cast<const unsigned char *>(a.dinvT32 + B.dinv_off);
+  // diagonal tiles: packed triangles (rectangular full packed in FP64, block-packed in FP32)
+  const int64_t nd = B.dinv_off / (T * T);  // the block's first diagonal tile
+  const unsigned char *dinv = p64 ? reinterpret_cast<const unsigned char *>(a.dinvP64 + nd * kPackTile)
+                                  : reinterpret_cast<const unsigned char *>(a.dinvP32 + nd * kBPackTile);
+  const unsigned char *dinvT =
+      p64 ? reinterpret_cast<const unsigned char *>(a.dinvTP64 + nd * kPackTile)
+          : reinterpret_cast<const unsigned char *>(a.dinvTP32 + nd * kBPackTile);
   const uint32_t tb = (uint32_t)(T * T * (p64 ? 8 : 4));
-  const uint32_t db = p64 ? (uint32_t)(kPackTile * 8) : tb;
+  const uint32_t db = p64 ? (uint32_t)(kPackTile * 8) : (uint32_t)(kBPackTile * 4);
   for (;;) {
     if (leader)
       producer_pass(R, a.trow + B.trow0, a.trowT + B.trow0, B.nt, fac, dinv, facT, dinvT, tb, db,
