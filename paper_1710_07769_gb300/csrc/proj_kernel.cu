@@ -320,23 +320,41 @@ __device__ void consumer_block(const IterArgs &a, const BlockDesc &B, const Ring
     csync();
     int again = 0;
     if (s < refine_steps) {
-      // res = u - G_i y straight into w; a warp covers whole 32-row slices (coalesced)
+      // res = u - G_i y straight into w; a warp covers whole 32-row slices (coalesced) and a
+      // thread two rows kConsumers apart at once (two independent load chains in flight;
+      // slice widths are uniform across a warp, so the interleaving does not diverge)
       double e2 = 0.0;
-      for (int r = tid; r < mp; r += kConsumers) {
-        if (r >= B.m) {
-          w[r] = W(0);
-          continue;
+      for (int r0 = tid; r0 < mp; r0 += 2 * kConsumers) {
+        const int r1 = r0 + kConsumers;
+        int wd0 = 0, wd1 = 0;
+        const double *sv0 = nullptr, *sv1 = nullptr;
+        const int16_t *sc0 = nullptr, *sc1 = nullptr;
+        double acc0 = 0.0, acc1 = 0.0;
+        if (r0 < B.m) {
+          const int sl = B.slice0 + (r0 >> 5), l = r0 & 31;
+          const int64_t o = a.soff[sl];
+          wd0 = (int)((a.soff[sl + 1] - o) >> 5);
+          sv0 = a.sval + o + l;
+          sc0 = a.scol + o + l;
+          acc0 = ub[(int64_t)r0 * a.nrhs];
         }
-        const int sl = B.slice0 + (r >> 5), l = r & 31;
-        const int64_t o = a.soff[sl];
-        const int wd = (int)((a.soff[sl + 1] - o) >> 5);
-        const double *sv = a.sval + o + l;
-        const int16_t *sc = a.scol + o + l;
-        double acc = ub[(int64_t)r * a.nrhs];
-#pragma unroll 4
-        for (int kk = 0; kk < wd; ++kk) acc = fma(-sv[32 * kk], V.y[sc[32 * kk]], acc);
-        w[r] = W(acc);
-        e2 += acc * acc;
+        if (r1 < B.m) {
+          const int sl = B.slice0 + (r1 >> 5), l = r1 & 31;
+          const int64_t o = a.soff[sl];
+          wd1 = (int)((a.soff[sl + 1] - o) >> 5);
+          sv1 = a.sval + o + l;
+          sc1 = a.scol + o + l;
+          acc1 = ub[(int64_t)r1 * a.nrhs];
+        }
+        const int wmax = wd0 > wd1 ? wd0 : wd1;
+#pragma unroll 2
+        for (int kk = 0; kk < wmax; ++kk) {
+          if (kk < wd0) acc0 = fma(-sv0[32 * kk], V.y[sc0[32 * kk]], acc0);
+          if (kk < wd1) acc1 = fma(-sv1[32 * kk], V.y[sc1[32 * kk]], acc1);
+        }
+        if (r0 < mp) w[r0] = W(acc0);  // rows past m (padding) get zero
+        if (r1 < mp) w[r1] = W(acc1);
+        e2 += acc0 * acc0 + acc1 * acc1;
       }
       e2 = csum(e2, red);
       const double tol = RELAX ? inner_tol(a, 1, (int64_t)B.sys * a.nrhs + k) : a.refine_tol;
