@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -59,7 +60,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"cimmino_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
@@ -98,6 +99,18 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def max_over_ranks(value, device=None):
+    """The largest value over all ranks of the default process group (every rank gets it);
+    the value itself in a single process.  Replicas report the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def algorithmic_bytes(n, nnz, factor_bytes, w_factor, refine_mean, nnz_bd):
@@ -185,9 +198,7 @@ def run_ours(args, rank, local):
     wall = time.time() - t_wall0
     ms_step = sum(t64) / len(t64)
     if args.gpus > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dev)
         torch.distributed.barrier()
     # kernel timing of the dominant kernel (projection) on the library's stream
     kt64 = s64.time_kernels(reps=10)
