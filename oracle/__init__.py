@@ -7,7 +7,9 @@ FP64, no floating-point contraction); this module only builds that file with
 gcc and marshals arguments through ctypes.
 
 Functions and the paper passages they follow:
-  * ``Oracle(...)``: row 2-norm prescaling (Section 2.1), row permutation
+  * ``Oracle(..., ruiz=k)``: k sweeps of row and column infinity-norm
+    equilibration first (Section 3.1; ``equil()`` returns the factors), then
+    row 2-norm prescaling (Section 2.1), row permutation
     A^Pi = P A (Section 2.2), C = A A^T by Gustavson SpGEMM (Section 2.3),
     Gram blocks G_i = A_i A_i^T and their Cholesky factors (the pseudoinverse
     A_i^+ = A_i^T (A_i A_i^T)^{-1} of Section 1, applied, never formed).
@@ -64,7 +66,7 @@ def _load():
             return _lib
         lib = C.CDLL(build())
         lib.orc_setup.argtypes = [C.c_int64, _i64p, _i32p, _f64p, C.c_int32, _i32p, _i64p,
-                                  C.c_int, C.c_int, C.POINTER(_p)]
+                                  C.c_int32, C.c_int, C.c_int, C.POINTER(_p)]
         lib.orc_setup.restype = C.c_int
         lib.orc_free.argtypes = [_p]
         lib.orc_fail_block.argtypes = [_p]
@@ -73,6 +75,7 @@ def _load():
         lib.orc_aat_nnz.restype = C.c_int64
         lib.orc_aat_get.argtypes = [_p, _i64p, _i32p, _f64p]
         lib.orc_scaled_get.argtypes = [_p, _i64p, _i32p, _f64p, _f64p]
+        lib.orc_equil_get.argtypes = [_p, _f64p, _f64p]
         lib.orc_factor_get.argtypes = [_p, C.c_int32, _f64p]
         lib.orc_gram_get.argtypes = [_p, C.c_int32, _f64p]
         lib.orc_project.argtypes = [_p, _f64p, _f64p]
@@ -102,7 +105,8 @@ class OracleError(RuntimeError):
 class Oracle:
     """Setup of the FP64 oracle for one system and one row-block partition."""
 
-    def __init__(self, A, block_ptr, perm=None, factor: bool = True, nthreads: int = 1):
+    def __init__(self, A, block_ptr, perm=None, factor: bool = True, nthreads: int = 1,
+                 ruiz: int = 0):
         lib = _load()
         self.lib = lib
         self.n = int(A.n)
@@ -114,8 +118,9 @@ class Oracle:
                    np.ascontiguousarray(A.col_idx, dtype=np.int32),
                    np.ascontiguousarray(A.val, dtype=np.float64))
         h = _p()
-        st = lib.orc_setup(self.n, *self._A, self.K, self.perm, self.block_ptr, int(factor),
-                           int(nthreads), C.byref(h))
+        self.ruiz = int(ruiz)
+        st = lib.orc_setup(self.n, *self._A, self.K, self.perm, self.block_ptr, self.ruiz,
+                           int(factor), int(nthreads), C.byref(h))
         self._h = h
         if st != ORC_OK:
             fb = lib.orc_fail_block(h) if h.value else -1
@@ -150,6 +155,13 @@ class Oracle:
         d = np.zeros(self.n, np.float64)
         self.lib.orc_scaled_get(self._h, rp, ci, v, d)
         return rp, ci[:nnz], v[:nnz], d
+
+    def equil(self):
+        """(rs, cs) with A = diag(rs) Ae diag(cs), Ae the equilibrated matrix."""
+        rs = np.zeros(self.n, np.float64)
+        cs = np.zeros(self.n, np.float64)
+        self.lib.orc_equil_get(self._h, rs, cs)
+        return rs, cs
 
     def block_size(self, b: int) -> int:
         return int(self.block_ptr[b + 1] - self.block_ptr[b])

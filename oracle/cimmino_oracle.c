@@ -10,6 +10,10 @@
  *
  * Everything is written as the plain definition in plain loops, in double
  * precision, compiled without floating-point contraction:
+ *   - optional row and column infinity-norm equilibration before the row
+ *     2-norm step (Section 3.1: the iterative procedure that brings the largest
+ *     entry of every row and column to one; column scaling changes H and acts
+ *     as a preconditioner, row scaling does not);
  *   - row 2-norm prescaling (Section 2.1) and the row permutation A^Pi = P A
  *     decoded from a partition (Section 2.2);
  *   - C = A A^T by row-wise Gustavson SpGEMM (Section 2.3, "Constructing
@@ -56,7 +60,11 @@ typedef struct orc_ctx {
   int64_t *rp;
   int32_t *ci;
   double *v;
-  double *d;     /* d[r] = 2-norm of original row perm[r] */
+  double *d;     /* original row perm[r] = d[r] * (scaled row r) * diag(cs) */
+  /* equilibration (Section 3.1): A = diag(rs) Ae diag(cs); all ones when off */
+  int32_t ruiz;  /* equilibration sweeps (0 = off) */
+  double *rs, *cs;
+  double *ve;    /* values of Ae (pattern of the original matrix) */
   int32_t *perm; /* permuted row r is original row perm[r] */
   int64_t *bp;   /* block r-ranges over permuted rows, K+1 */
   /* column-wise copy of the scaled permuted matrix (CSC), rows increasing */
@@ -77,7 +85,50 @@ typedef struct orc_ctx {
 
 static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
 
-/* ---- Section 2.1: scale every row to unit 2-norm; Section 2.2: permute rows ---- */
+/* ---- Section 3.1: row and column infinity-norm equilibration ----
+ * One sweep takes, on the current matrix Ae, the largest magnitude of every row
+ * (rmax_i) and of every column (cmax_j), and divides entry (i, j) by
+ * sqrt(rmax_i) * sqrt(cmax_j); rs_i and cs_j accumulate the divisors, so that
+ * A = diag(rs) Ae diag(cs) holds throughout.  An empty row or column keeps the
+ * divisor 1.  The largest entry of every row and column tends to one. */
+static int equilibrate(orc_ctx *c) {
+  int64_t n = c->n;
+  c->rs = (double *)xcalloc(n, sizeof(double));
+  c->cs = (double *)xcalloc(n, sizeof(double));
+  c->ve = (double *)xcalloc(c->nnz, sizeof(double));
+  double *rmax = (double *)xcalloc(n, sizeof(double));
+  double *cmax = (double *)xcalloc(n, sizeof(double));
+  if (!c->rs || !c->cs || !c->ve || !rmax || !cmax) { free(rmax); free(cmax); return ORC_ENOMEM; }
+  for (int64_t i = 0; i < n; ++i) c->rs[i] = c->cs[i] = 1.0;
+  memcpy(c->ve, c->v0, sizeof(double) * (size_t)c->nnz);
+  for (int32_t sweep = 0; sweep < c->ruiz; ++sweep) {
+    for (int64_t i = 0; i < n; ++i) rmax[i] = cmax[i] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = c->rp0[i]; q < c->rp0[i + 1]; ++q) {
+        double a = fabs(c->ve[q]);
+        if (a > rmax[i]) rmax[i] = a;
+        if (a > cmax[c->ci0[q]]) cmax[c->ci0[q]] = a;
+      }
+    for (int64_t i = 0; i < n; ++i) {
+      rmax[i] = rmax[i] > 0.0 ? sqrt(rmax[i]) : 1.0;
+      cmax[i] = cmax[i] > 0.0 ? sqrt(cmax[i]) : 1.0;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = c->rp0[i]; q < c->rp0[i + 1]; ++q)
+        c->ve[q] = c->ve[q] / (rmax[i] * cmax[c->ci0[q]]);
+    for (int64_t i = 0; i < n; ++i) {
+      c->rs[i] = c->rs[i] * rmax[i];
+      c->cs[i] = c->cs[i] * cmax[i];
+    }
+  }
+  free(rmax);
+  free(cmax);
+  return ORC_OK;
+}
+
+/* ---- Section 2.1: scale every row to unit 2-norm; Section 2.2: permute rows ----
+ * The input is the equilibrated matrix Ae (the original one when equilibration
+ * is off); d[r] carries both row factors back to the original row. */
 static int scale_permute(orc_ctx *c) {
   int64_t n = c->n;
   c->rp = (int64_t *)xcalloc(n + 1, sizeof(int64_t));
@@ -93,14 +144,14 @@ static int scale_permute(orc_ctx *c) {
   for (int64_t r = 0; r < n; ++r) {
     int64_t o = c->perm[r];
     double ss = 0.0;
-    for (int64_t q = c->rp0[o]; q < c->rp0[o + 1]; ++q) ss += c->v0[q] * c->v0[q];
+    for (int64_t q = c->rp0[o]; q < c->rp0[o + 1]; ++q) ss += c->ve[q] * c->ve[q];
     double nr = sqrt(ss);
     if (!(nr > 0.0)) return ORC_ESINGULAR; /* an empty / zero row makes A singular */
-    c->d[r] = nr;
+    c->d[r] = c->ruiz > 0 ? nr * c->rs[o] : nr;
     int64_t w = c->rp[r];
     for (int64_t q = c->rp0[o]; q < c->rp0[o + 1]; ++q, ++w) {
       c->ci[w] = c->ci0[q];
-      c->v[w] = c->v0[q] / nr;
+      c->v[w] = c->ve[q] / nr;
     }
   }
   return ORC_OK;
@@ -308,16 +359,21 @@ void orc_free(orc_ctx *c) {
   free(c->cp); free(c->ri); free(c->cv);
   free(c->crp); free(c->cci); free(c->ccv);
   free(c->foff); free(c->L);
+  free(c->rs); free(c->cs); free(c->ve);
   free(c);
 }
 
-/* Build everything the solve needs: copy A, scale rows to unit 2-norm, permute
- * rows by perm (NULL = identity), column copy, C = A A^T, Gram blocks and their
- * Cholesky factors.  factor=0 skips the factorisation (graph-only use). */
+/* Build everything the solve needs: copy A, equilibrate rows and columns for
+ * ruiz sweeps (0 = off), scale rows to unit 2-norm, permute rows by perm (NULL =
+ * identity), column copy, C = A A^T, Gram blocks and their Cholesky factors.
+ * factor=0 skips the factorisation (graph-only use).  With equilibration the
+ * projections and the CG iterates live in the column-scaled space y = diag(cs) x;
+ * orc_solve and orc_cimmino_sweeps return x. */
 int orc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int32_t K,
-              const int32_t *perm, const int64_t *bp, int factor, int nthreads, orc_ctx **out) {
+              const int32_t *perm, const int64_t *bp, int32_t ruiz, int factor, int nthreads,
+              orc_ctx **out) {
   *out = NULL;
-  if (n <= 0 || K <= 0 || !rp || !ci || !v || !bp) return ORC_EINVAL;
+  if (n <= 0 || K <= 0 || !rp || !ci || !v || !bp || ruiz < 0) return ORC_EINVAL;
   if (bp[0] != 0 || bp[K] != n) return ORC_EINVAL;
   for (int32_t b = 0; b < K; ++b)
     if (bp[b + 1] <= bp[b]) return ORC_EINVAL;
@@ -327,6 +383,7 @@ int orc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
   c->nnz = rp[n];
   c->K = K;
   c->fail_block = -1;
+  c->ruiz = ruiz;
   c->nthreads = nthreads > 0 ? nthreads : 1;
   c->rp0 = (int64_t *)xcalloc(n + 1, sizeof(int64_t));
   c->ci0 = (int32_t *)xcalloc(c->nnz, sizeof(int32_t));
@@ -339,7 +396,8 @@ int orc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
   memcpy(c->v0, v, sizeof(double) * (size_t)c->nnz);
   memcpy(c->bp, bp, sizeof(int64_t) * (size_t)(K + 1));
   for (int64_t r = 0; r < n; ++r) c->perm[r] = perm ? perm[r] : (int32_t)r;
-  int st = scale_permute(c);
+  int st = equilibrate(c);
+  if (st == ORC_OK) st = scale_permute(c);
   if (st == ORC_OK) st = transpose(c);
   if (st == ORC_OK) st = aat(c);
   if (st == ORC_OK && factor) st = factor_all(c);
@@ -361,6 +419,12 @@ void orc_scaled_get(const orc_ctx *c, int64_t *rp, int32_t *ci, double *v, doubl
   memcpy(ci, c->ci, sizeof(int32_t) * (size_t)c->nnz);
   memcpy(v, c->v, sizeof(double) * (size_t)c->nnz);
   memcpy(d, c->d, sizeof(double) * (size_t)c->n);
+}
+
+/* the equilibration factors: A = diag(rs) Ae diag(cs) (all ones when off) */
+void orc_equil_get(const orc_ctx *c, double *rs, double *cs) {
+  memcpy(rs, c->rs, sizeof(double) * (size_t)c->n);
+  memcpy(cs, c->cs, sizeof(double) * (size_t)c->n);
 }
 
 /* dense m x m row-major copy of block b's factor L (upper part zero) */
@@ -441,7 +505,8 @@ int orc_solve(const orc_ctx *c, const double *f, double tol, int32_t maxit, doub
   double *r = (double *)xcalloc(n, sizeof(double));
   double *p = (double *)xcalloc(n, sizeof(double));
   double *psi = (double *)xcalloc(n, sizeof(double));
-  orc_project_rhs(c, f, r); /* r^(0) = xi - H x^(0) = xi */
+  double *y = (double *)xcalloc(n, sizeof(double)); /* iterate of A diag(1/cs) y = f */
+  orc_project_rhs(c, f, r); /* r^(0) = xi - H y^(0) = xi */
   memcpy(p, r, sizeof(double) * (size_t)n);
   double rho = dot(n, r, r);
   int st = ORC_ENOCONV;
@@ -450,12 +515,13 @@ int orc_solve(const orc_ctx *c, const double *f, double tol, int32_t maxit, doub
     double pq = dot(n, p, psi);
     if (!(pq > 0.0) || !isfinite(pq)) { st = ORC_EBREAKDOWN; *iters = t + 1; break; }
     double alpha = rho / pq;
-    for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) y[i] += alpha * p[i];
     for (int64_t i = 0; i < n; ++i) r[i] -= alpha * psi[i];
     double rho1 = dot(n, r, r);
     double beta = rho1 / rho;
     for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
     rho = rho1;
+    for (int64_t i = 0; i < n; ++i) x[i] = c->ruiz > 0 ? y[i] / c->cs[i] : y[i];
     double nr;
     true_residual(c, f, x, &nr, gamma);
     *relres = nr / nf;
@@ -463,7 +529,9 @@ int orc_solve(const orc_ctx *c, const double *f, double tol, int32_t maxit, doub
     if (hist) hist[t] = *relres;
     if (*relres <= tol) { st = ORC_OK; break; }
   }
-  free(r); free(p); free(psi);
+  if (st == ORC_EBREAKDOWN)
+    for (int64_t i = 0; i < n; ++i) x[i] = c->ruiz > 0 ? y[i] / c->cs[i] : y[i];
+  free(r); free(p); free(psi); free(y);
   return st;
 }
 
@@ -486,6 +554,9 @@ void orc_cimmino_sweeps(const orc_ctx *c, const double *f, double omega, int32_t
     spmv_t(c, y, delta);
     for (int64_t i = 0; i < n; ++i) x[i] += omega * delta[i];
   }
+  /* the sweeps ran on the column-scaled system; return x = y / cs */
+  if (c->ruiz > 0)
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] / c->cs[i];
   free(res); free(y); free(delta);
 }
 

@@ -373,6 +373,119 @@ def test_algorithm1_first_sweep_and_convergence():
     assert err <= 10 * np.sqrt(lam[-1] / lam[0]) * rate ** 400 + 1e-12
 
 
+# ---------------------------------------------------------------- equilibration (Section 3.1)
+
+def badly_scaled(n, seed, spread=3.0):
+    """A diagonally dominant sparse matrix with rows and columns multiplied by
+    10^U[-spread, spread]: a poorly scaled input (Section 3.1)."""
+    D = dense(small_system(n, 4, seed))
+    rng = np.random.default_rng(seed + 100)
+    D = D * 10.0 ** rng.uniform(-spread, spread, n)[:, None]
+    D = D * 10.0 ** rng.uniform(-spread, spread, n)[None, :]
+    return csr_from_dense(D), D
+
+
+def test_equilibration_diagonal_closed_form():
+    """A diagonal matrix: the largest entry of row i and column i is |d_i|, so one sweep
+    divides by sqrt|d_i| twice and leaves +-1; further sweeps change nothing."""
+    rng = np.random.default_rng(31)
+    d = rng.choice([-1.0, 1.0], 40) * 10.0 ** rng.uniform(-4, 4, 40)
+    A = csr_from_dense(np.diag(d))
+    bp = np.arange(0, 41, 8)
+    rs, cs = oracle.Oracle(A, bp, ruiz=1).equil()
+    np.testing.assert_allclose(rs, np.sqrt(np.abs(d)), rtol=1e-15)
+    np.testing.assert_allclose(cs, np.sqrt(np.abs(d)), rtol=1e-15)
+    rs5, cs5 = oracle.Oracle(A, bp, ruiz=5).equil()
+    np.testing.assert_allclose(rs5 * cs5, np.abs(d), rtol=4e-16 * 8)
+    o = oracle.Oracle(A, bp, ruiz=5)
+    x, it, rr, g, st = o.solve(d * np.arange(1, 41))
+    assert st == 0 and it == 1      # Ae = sign(D): every block projection is exact
+    np.testing.assert_allclose(x, np.arange(1, 41), rtol=1e-14)
+
+
+def test_equilibration_rank_one_closed_form():
+    """A = u v^T (positive): row max u_i max(v), column max max(u) v_j, so one sweep
+    gives rs_i = sqrt(u_i max v), cs_j = sqrt(max u v_j) and
+    Ae_ij = sqrt(u_i v_j / (max u max v)).  One-row blocks keep every G_i nonsingular."""
+    rng = np.random.default_rng(32)
+    u, v = rng.uniform(0.1, 100, 9), rng.uniform(0.1, 100, 9)
+    A = csr_from_dense(np.outer(u, v))
+    o = oracle.Oracle(A, np.arange(10), ruiz=1)
+    rs, cs = o.equil()
+    np.testing.assert_allclose(rs, np.sqrt(u * v.max()), rtol=2e-16 * 4)
+    np.testing.assert_allclose(cs, np.sqrt(u.max() * v), rtol=2e-16 * 4)
+    Ae = np.outer(u, v) / np.outer(rs, cs)
+    np.testing.assert_allclose(Ae, np.sqrt(np.outer(u, v) / (u.max() * v.max())), rtol=1e-15)
+
+
+def test_equilibration_converges_and_factors_reconstruct_A():
+    """After k sweeps every row and column of Ae has largest magnitude close to one
+    (Section 3.1), and A = diag(d) S diag(cs) for the scaled permuted rows S."""
+    A, D = badly_scaled(150, 33, spread=4.0)
+    bp = np.array([0, 50, 100, 150])
+    perm = np.random.default_rng(5).permutation(150).astype(np.int32)
+    o = oracle.Oracle(A, bp, perm=perm, factor=False, ruiz=30)
+    rs, cs = o.equil()
+    Ae = D / np.outer(rs, cs)
+    dev = max(np.abs(np.abs(Ae).max(axis=1) - 1).max(), np.abs(np.abs(Ae).max(axis=0) - 1).max())
+    assert dev <= 1e-6, dev
+    rp, ci, v, d = o.scaled()
+    S = inputs.CSR(150, rp, ci, v).to_dense()
+    np.testing.assert_allclose(d[:, None] * S * cs[None, :], D[perm], rtol=1e-13)
+    assert np.allclose(np.linalg.norm(S, axis=1), 1.0, rtol=1e-15)
+
+
+def test_equilibrated_projection_is_column_scaled_pseudoinverse_sum():
+    """Column scaling changes H (Section 3.1): with equilibration the oracle's H is
+    sum_i pinv(B_i) B_i for B = A diag(1/cs), not the H of A."""
+    A, D = badly_scaled(60, 34)
+    bp = np.array([0, 20, 45, 60])
+    o = oracle.Oracle(A, bp, ruiz=8)
+    rs, cs = o.equil()
+    B = D / cs[None, :]
+    Href = sum(np.linalg.pinv(B[bp[b]:bp[b + 1]]) @ B[bp[b]:bp[b + 1]] for b in range(3))
+    H = oracle_H(o)
+    np.testing.assert_allclose(H, Href, atol=1e-10)
+    H0 = oracle_H(oracle.Oracle(A, bp))
+    assert np.abs(H - H0).max() > 0.1
+    assert np.trace(H) == pytest.approx(60, rel=1e-12)   # still a sum of projections
+
+
+def test_equilibrated_solve_matches_dense_lu_and_preconditions():
+    """With equilibration the solve still reaches A^{-1} f, K = 1 still takes one step,
+    and on a badly column-scaled matrix it takes fewer CG iterations than without
+    (column scaling acts as a preconditioner, Section 3.1).  Algorithm 1 returns x too."""
+    A, D = badly_scaled(120, 35)
+    bp = np.array([0, 30, 60, 90, 120])
+    xt = np.random.default_rng(9).uniform(-1, 1, 120)
+    f = D @ xt
+    x_lu = np.linalg.solve(D, f)
+    kappa = np.linalg.cond(D)
+    x1, it1, rr1, g1, st1 = oracle.Oracle(A, bp, ruiz=10).solve(f)
+    x0, it0, rr0, g0, st0 = oracle.Oracle(A, bp).solve(f)
+    assert st1 == 0 and rr1 <= 1e-10
+    assert np.linalg.norm(x1 - x_lu) <= kappa * 1e-10 * np.linalg.norm(x_lu)
+    assert st0 == 0 and it1 < it0, (it1, it0)
+    xk, itk, *_ = oracle.Oracle(A, np.array([0, 120]), ruiz=10).solve(f)
+    assert itk == 1 and np.linalg.norm(xk - x_lu) <= kappa * 1e-14 * np.linalg.norm(x_lu)
+    # Algorithm 1 on the equilibrated system: the first sweep is omega * xi in the
+    # column-scaled space, returned as x = y / cs; the sweeps converge to A^{-1} f
+    A, D = badly_scaled(60, 36, spread=1.0)
+    bp = np.array([0, 20, 40, 60])
+    f = D @ xt[:60]
+    o = oracle.Oracle(A, bp, ruiz=10)
+    cs = o.equil()[1]
+    np.testing.assert_allclose(o.cimmino_sweeps(f, 0.7, 1) * cs, 0.7 * o.project_rhs(f),
+                               rtol=1e-14, atol=1e-300)
+    lam = np.linalg.eigvalsh(oracle_H(o))
+    xs = o.cimmino_sweeps(f, 2.0 / (lam[0] + lam[-1]), 400)
+    rate = (lam[-1] - lam[0]) / (lam[-1] + lam[0])
+    bound = 10 * np.sqrt(lam[-1] / lam[0]) * rate ** 400 * cs.max() / cs.min()
+    assert bound < 1e-4
+    x_lu = np.linalg.solve(D, f)
+    assert np.linalg.norm(xs - x_lu) / np.linalg.norm(x_lu) <= bound + 1e-12
+
+
 def test_zero_rhs_and_zero_row():
     w = inputs.workload(1)
     o = oracle.Oracle(w.A, w.block_ptr)
