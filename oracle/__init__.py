@@ -19,6 +19,9 @@ Functions and the paper passages they follow:
     true relative residual; gamma of Eq. 3.1 is reported too.
   * ``Oracle.cimmino_sweeps``: Algorithm 1 with relaxation omega.
   * ``cutsize`` / ``ip_matrix``: Eqs. 2.6-2.9.
+  * ``sparsify_dense_columns``: the dense-column rule of Section 2.3 (the graph
+    is built from a copy of A whose dense columns keep their sqrt(n) largest
+    entries).
   * ``aat_plain`` / ``cholesky_dense``: the same SpGEMM / Cholesky code on a
     caller matrix, for pins against independent references.
 Parity status of every function is pinned by ``tests/test_oracle_pins.py``; the
@@ -90,6 +93,9 @@ def _load():
         lib.orc_aat_plain.argtypes = [C.c_int64, _i64p, _i32p, _f64p, _p, _p, _p,
                                       C.POINTER(C.c_int64)]
         lib.orc_aat_plain.restype = C.c_int
+        lib.orc_sparsify_dense_columns.argtypes = [C.c_int64, _i64p, _i32p, _f64p, _i64p,
+                                                   _i32p, _f64p]
+        lib.orc_sparsify_dense_columns.restype = C.c_int64
         lib.orc_cholesky_dense.argtypes = [C.c_int64, _f64p]
         lib.orc_cholesky_dense.restype = C.c_int
         _lib = lib
@@ -229,6 +235,20 @@ def ip_matrix(Crp, Cci, Cv, part, K: int) -> np.ndarray:
                       np.ascontiguousarray(Cci, np.int32), np.ascontiguousarray(Cv, np.float64),
                       np.ascontiguousarray(part, np.int32), int(K), out)
     return out.reshape(K, K)
+
+
+def sparsify_dense_columns(A):
+    """(row_ptr, col_idx, val) of A with every dense column (more than floor(sqrt(n))
+    nonzeros) cut to its floor(sqrt(n)) largest magnitudes (Section 2.3)."""
+    lib = _load()
+    rp, ci, v = (np.ascontiguousarray(A.row_ptr, np.int64), np.ascontiguousarray(A.col_idx, np.int32),
+                 np.ascontiguousarray(A.val, np.float64))
+    nnz = int(rp[-1])
+    orp = np.zeros(A.n + 1, np.int64)
+    oci = np.zeros(max(nnz, 1), np.int32)
+    ov = np.zeros(max(nnz, 1), np.float64)
+    w = lib.orc_sparsify_dense_columns(A.n, rp, ci, v, orp, oci, ov)
+    return orp, oci[:w], ov[:w]
 
 
 def aat_plain(A):

@@ -27,6 +27,8 @@
  *     relative residual ||f - A x||_2 / ||f||_2 and also reporting the
  *     normwise backward error gamma of Eq. 3.1;
  *   - Algorithm 1 (block Cimmino with relaxation omega);
+ *   - the dense-column rule for building the graph (Section 2.3): a column with
+ *     more than sqrt(n) nonzeros keeps only its sqrt(n) largest magnitudes;
  *   - the partition metrics cutsize(Pi) = interIP(Pi) (Eqs. 2.6-2.7) and the
  *     inter-block inner-product matrix ip_km (Eqs. 2.8-2.9).
  *
@@ -632,4 +634,52 @@ int orc_cholesky_dense(int64_t m, double *A) {
     for (int64_t j = 0; j < m; ++j) A[i * m + j] = j <= i ? L[pk(i, j)] : 0.0;
   free(L);
   return st;
+}
+
+/* ---- Section 2.3, dense columns: the graph is built from a sparser copy of A ----
+ * t = floor(sqrt(n)) (integer square root).  A column with more than t nonzeros is
+ * dense; it keeps its t entries of largest magnitude (equal magnitudes: the lower
+ * row index first) and drops the rest.  Other columns are copied.  The output is a
+ * CSR of the same shape whose rows keep their column order; it has at most nnz(A)
+ * entries, so out_ci / out_v must hold rp[n] entries.  Returns nnz of the output. */
+typedef struct { double a; int64_t row; } orc_mag_row;
+
+static int cmp_mag_row(const void *x, const void *y) {
+  const orc_mag_row *p = (const orc_mag_row *)x, *q = (const orc_mag_row *)y;
+  if (p->a > q->a) return -1;
+  if (p->a < q->a) return 1;
+  return p->row < q->row ? -1 : (p->row > q->row ? 1 : 0);
+}
+
+int64_t orc_sparsify_dense_columns(int64_t n, const int64_t *rp, const int32_t *ci,
+                                   const double *v, int64_t *out_rp, int32_t *out_ci,
+                                   double *out_v) {
+  int64_t t = 0;
+  while ((t + 1) * (t + 1) <= n) ++t;
+  int64_t nnz = rp[n];
+  int64_t *count = (int64_t *)xcalloc(n, sizeof(int64_t));
+  char *keep = (char *)xcalloc(nnz, 1);
+  for (int64_t q = 0; q < nnz; ++q) count[ci[q]]++;
+  for (int64_t q = 0; q < nnz; ++q) keep[q] = 1;
+  orc_mag_row *buf = (orc_mag_row *)xcalloc(n, sizeof(orc_mag_row));
+  int64_t *where = (int64_t *)xcalloc(n, sizeof(int64_t));
+  for (int64_t j = 0; j < n; ++j) {
+    if (count[j] <= t) continue;
+    /* gather column j: (|a_ij|, i), rows in increasing order */
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        if (ci[q] == j) { buf[m].a = fabs(v[q]); buf[m].row = i; where[i] = q; ++m; }
+    qsort(buf, (size_t)m, sizeof(orc_mag_row), cmp_mag_row);
+    for (int64_t k = t; k < m; ++k) keep[where[buf[k].row]] = 0;
+  }
+  int64_t w = 0;
+  out_rp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+      if (keep[q]) { out_ci[w] = ci[q]; out_v[w] = v[q]; ++w; }
+    out_rp[i + 1] = w;
+  }
+  free(count); free(keep); free(buf); free(where);
+  return w;
 }

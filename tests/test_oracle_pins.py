@@ -534,3 +534,71 @@ def test_cutsize_brute_force_bisection():
         assert cut == pytest.approx(brute, rel=1e-12, abs=1e-12)
         best = cut if best is None else min(best, cut)
     assert best >= 0
+
+
+# ---------------------------------------------------------------- dense columns (Section 2.3)
+
+def numpy_sparsify(D):
+    """Independent restatement on a dense array: keep the floor(sqrt(n)) largest
+    magnitudes of every column with more nonzeros than that (lower row first on ties)."""
+    n = D.shape[0]
+    t = int(np.floor(np.sqrt(n)))
+    out = D.copy()
+    for j in range(n):
+        rows = np.nonzero(D[:, j])[0]
+        if len(rows) > t:
+            order = np.lexsort((rows, -np.abs(D[rows, j])))
+            out[rows[order[t:]], j] = 0.0
+    return out
+
+
+def test_dense_column_example_25():
+    """The paper's example: n = 25 and one column with 23 nonzeros; sqrt(25) = 5, so the
+    column keeps its 5 largest entries and the other columns are untouched."""
+    ex = json.load(open(os.path.join(GOLDEN, "dense_column_25.json")))
+    n = ex["n"]
+    rng = np.random.default_rng(12)
+    D = np.diag(rng.uniform(1, 2, n))
+    rows = np.sort(rng.choice(n, ex["dense_column_nnz"], replace=False))
+    D[rows, 3] = rng.uniform(-5, 5, len(rows))
+    D[3, 3] = 9.0
+    A = csr_from_dense(D)
+    assert np.count_nonzero(D[:, 3]) == ex["dense_column_nnz"]
+    rp, ci, v = oracle.sparsify_dense_columns(A)
+    S = inputs.CSR(n, rp, ci, v).to_dense()
+    assert np.count_nonzero(S[:, 3]) == ex["kept"]
+    kept = np.sort(np.abs(S[:, 3][S[:, 3] != 0]))
+    assert np.array_equal(kept, np.sort(np.abs(D[:, 3]))[-ex["kept"]:])
+    others = [j for j in range(n) if j != 3]
+    assert np.array_equal(S[:, others], D[:, others])
+
+
+@pytest.mark.parametrize("n,seed", [(50, 1), (144, 2), (200, 3)])
+def test_dense_columns_match_numpy_and_sparsify_graph(n, seed):
+    """Several dense columns with tied magnitudes: the same entries as an independent
+    numpy restatement; C of the sparsified matrix has fewer nonzeros; a matrix without
+    dense columns comes back unchanged."""
+    rng = np.random.default_rng(seed)
+    D = np.diag(rng.uniform(1, 2, n)) + np.diag(-np.ones(n - 1), 1)
+    for j in rng.choice(n, 3, replace=False):
+        rows = rng.choice(n, n // 2, replace=False)
+        D[rows, j] = rng.choice([-2.0, -1.0, 1.0, 3.0], len(rows))   # many ties
+    A = csr_from_dense(D)
+    rp, ci, v = oracle.sparsify_dense_columns(A)
+    S = inputs.CSR(n, rp, ci, v).to_dense()
+    assert np.array_equal(S, numpy_sparsify(D))
+    assert len(oracle.aat_plain(inputs.CSR(n, rp, ci, v))[1]) < len(oracle.aat_plain(A)[1])
+    # the boundary: a column with floor(sqrt(n)) + 1 nonzeros is dense, one with
+    # floor(sqrt(n)) is not
+    t = int(np.floor(np.sqrt(n)))
+    E = np.diag(rng.uniform(1, 2, n))
+    E[rng.choice(np.arange(1, n), t, replace=False), 0] = rng.uniform(3, 4, t)      # t + 1
+    E[rng.choice(np.arange(0, n - 1), t - 1, replace=False), n - 1] = 5.0           # t
+    rp3, ci3, v3 = oracle.sparsify_dense_columns(csr_from_dense(E))
+    S3 = inputs.CSR(n, rp3, ci3, v3).to_dense()
+    assert np.count_nonzero(S3[:, 0]) == t and np.count_nonzero(E[:, 0]) == t + 1
+    assert np.array_equal(S3[:, 1:], E[:, 1:])
+    B = inputs.convdiff2d(12, 20.0)
+    rp2, ci2, v2 = oracle.sparsify_dense_columns(B)
+    assert np.array_equal(rp2, B.row_ptr) and np.array_equal(ci2, B.col_idx)
+    assert np.array_equal(v2, B.val)
