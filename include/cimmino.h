@@ -95,6 +95,11 @@ typedef struct cimmino_opts {
   int32_t multi_rhs;      /* 1 (default): with several right-hand sides, groups of  */
                           /* 8 or 16 share every factor tile read; 0: one factor    */
                           /* pass per right-hand side                               */
+  int32_t ruiz_sweeps;    /* sweeps of row and column infinity-norm equilibration  */
+                          /* before the row 2-norm step (Section 3.1), 0..100;     */
+                          /* 0 (default): off.  Column scaling changes H (it acts  */
+                          /* as a preconditioner); CG then runs on y = diag(cs) x, */
+                          /* and solutions are returned as x                       */
   void *stream;           /* cudaStream_t for all device work (NULL: own stream)   */
 } cimmino_opts;
 
@@ -180,9 +185,16 @@ const char *cimmino_last_error(const cimmino_ctx *ctx);
 int cimmino_get_aat_nnz(cimmino_ctx *ctx, int64_t *nnz);
 int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val);
 
-/* Scaled permuted matrix D^{-1} P A (CSR, nnz entries) and the row norms d (n). */
+/* Scaled permuted matrix S (CSR, nnz entries) and the row factors d (n), with
+ * P A = diag(d) S diag(cs): S has unit 2-norm rows; d is the row 2-norm times the
+ * equilibration row divisor, cs the column divisors (cimmino_get_colscale). */
 int cimmino_get_scaled(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val,
                        double *d);
+
+/* Column equilibration divisors cs (n doubles; all ones with opts.ruiz_sweeps = 0).
+ * The projections (cimmino_project, cimmino_project_rhs) act in the column-scaled
+ * space y = diag(cs) x.  Errors: EINVAL (NULL pointer), ECUDA. */
+int cimmino_get_colscale(cimmino_ctx *ctx, double *cs);
 
 /* Number of rows m of global block b (blocks of all systems in order). */
 int cimmino_block_rows(cimmino_ctx *ctx, int32_t b, int32_t *m);
@@ -238,6 +250,21 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
  * available from cimmino_last_error(NULL). */
 int cimmino_aat_noalloc(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
                         int32_t *col_idx, double *val, int64_t capacity);
+
+/* Dense columns (Section 2.3): a column with more than sqrt(n) nonzeros would make
+ * C = A A^T, and the row inner-product graph, dense.  Writes a copy of A in which every
+ * column with more than t = floor(sqrt(n)) nonzeros keeps only its t entries of
+ * largest magnitude (equal magnitudes: lower row first); other entries are copied in
+ * their row order.  For building the partitioning graph only (cimmino_aat on the copy,
+ * then cimmino_partition_rip); the solve uses the full A.  Host-only, no GPU.
+ *   n, row_ptr, col_idx, val     host CSR of A (n x n).
+ *   out_row_ptr (n + 1), out_col_idx and out_val (row_ptr[n] entries each, the most
+ *                                the copy can have): caller-allocated host arrays.
+ *   nnz_out                      out: nnz of the copy.
+ * Errors: EINVAL (NULL pointer, n < 1, malformed row_ptr, column out of range), ENOMEM. */
+int cimmino_sparsify_dense_columns(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                   const double *val, int64_t *out_row_ptr,
+                                   int32_t *out_col_idx, double *out_val, int64_t *nnz_out);
 
 /* Block-row partition by the row inner-product graph G_RIP (Sections 2.1-2.3): vertices
  * are rows, edge (i, j) carries cost |c_ij| / sqrt(c_ii c_jj), the cosine of rows i and j

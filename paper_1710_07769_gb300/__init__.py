@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["FP64", "FP32_REFINE", "DENSE", "SKYLINE", "CimminoError", "Solver", "BatchSolver",
-           "aat", "partition_rip", "load", "lib_path", "EXPORTS"]
+           "aat", "partition_rip", "sparsify_dense_columns", "load", "lib_path", "EXPORTS"]
 
 FP64, FP32_REFINE = 0, 1
 DENSE, SKYLINE = 0, 1
@@ -32,10 +32,10 @@ _NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOCONV", -
 # every entry point declared in include/cimmino.h
 EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimmino_solve",
            "cimmino_solve_batch", "cimmino_free", "cimmino_last_error", "cimmino_get_aat_nnz",
-           "cimmino_get_aat", "cimmino_get_scaled", "cimmino_block_rows", "cimmino_get_factor",
+           "cimmino_get_aat", "cimmino_get_scaled", "cimmino_get_colscale", "cimmino_block_rows", "cimmino_get_factor",
            "cimmino_project", "cimmino_project_rhs", "cimmino_sweeps", "cimmino_aat",
            "cimmino_aat_noalloc",
-           "cimmino_partition_rip", "cimmino_time_kernels", "cimmino_version"]
+           "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_time_kernels", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -48,7 +48,8 @@ class OptsStruct(C.Structure):
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_ratio_min", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
-                ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32), ("stream", C.c_void_p)]
+                ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32),
+                ("ruiz_sweeps", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StatsStruct(C.Structure):
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_get_aat_nnz.argtypes = [vp, C.POINTER(i64)]
         L.cimmino_get_aat.argtypes = [vp, vp, vp, vp]
         L.cimmino_get_scaled.argtypes = [vp, vp, vp, vp, vp]
+        L.cimmino_get_colscale.argtypes = [vp, vp]
         L.cimmino_block_rows.argtypes = [vp, i32, C.POINTER(i32)]
         L.cimmino_get_factor.argtypes = [vp, i32, vp, C.POINTER(i32)]
         L.cimmino_project.argtypes = [vp, vp, i32, vp, i32]
@@ -115,6 +117,8 @@ def load(build_if_missing: bool = False):
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
                                             C.POINTER(dbl)]
+        L.cimmino_sparsify_dense_columns.argtypes = [i64, vp, vp, vp, vp, vp, vp,
+                                                     C.POINTER(i64)]
         L.cimmino_aat_noalloc.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp, i64]
         L.cimmino_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -145,7 +149,8 @@ def _check(L, code: int, ctx=None):
 
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
-          keep_aat=False, refine_relax=None, multi_rhs=None, stream=None) -> OptsStruct:
+          keep_aat=False, refine_relax=None, multi_rhs=None, ruiz_sweeps=None,
+          stream=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -167,6 +172,8 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
         o.multi_rhs = int(bool(multi_rhs))
     if refine_relax is not None:
         o.refine_relax = int(bool(refine_relax))
+    if ruiz_sweeps is not None:
+        o.ruiz_sweeps = int(ruiz_sweeps)
     o.stream = stream
     return o
 
@@ -295,8 +302,15 @@ class Solver:
                                                  v.ctypes.data), self._h)
         return rp, ci[: nnz.value], v[: nnz.value]
 
+    def colscale(self):
+        """Column equilibration divisors cs (ones without equilibration)."""
+        cs = np.empty(self.n, np.float64)
+        _check(self._L, self._L.cimmino_get_colscale(self._h, cs.ctypes.data), self._h)
+        return cs
+
     def scaled_csr(self, nnz: int):
-        """Scaled permuted matrix D^{-1} P A (nnz = nnz(A)) and the row norms d."""
+        """Scaled permuted matrix S (nnz = nnz(A)) and the row factors d, with
+        P A = diag(d) S diag(cs)."""
         rp = np.empty(self.n + 1, np.int64)
         ci = np.empty(max(nnz, 1), np.int32)
         v = np.empty(max(nnz, 1), np.float64)
@@ -399,6 +413,24 @@ def aat(A, stream=None):
     _check(L, L.cimmino_aat(C.byref(csr), stream, C.byref(nnz), rp.ctypes.data, ci.ctypes.data,
                             v.ctypes.data))
     return rp, ci[: nnz.value], v[: nnz.value]
+
+
+def sparsify_dense_columns(A):
+    """Copy of A whose dense columns (more than floor(sqrt(n)) nonzeros) keep only their
+    floor(sqrt(n)) largest magnitudes (Section 2.3), for building the partitioning graph.
+    A has n, row_ptr, col_idx, val (host arrays).  Returns (row_ptr, col_idx, val)."""
+    L = load()
+    rp, ci, v = _host(A.row_ptr, np.int64), _host(A.col_idx, np.int32), _host(A.val, np.float64)
+    n = int(A.n)
+    nnz = int(rp[-1])
+    orp = np.empty(n + 1, np.int64)
+    oci = np.empty(max(nnz, 1), np.int32)
+    ov = np.empty(max(nnz, 1), np.float64)
+    w = C.c_int64(0)
+    _check(L, L.cimmino_sparsify_dense_columns(n, rp.ctypes.data, ci.ctypes.data, v.ctypes.data,
+                                               orp.ctypes.data, oci.ctypes.data,
+                                               ov.ctypes.data, C.byref(w)))
+    return orp, oci[: w.value].copy(), ov[: w.value].copy()
 
 
 def partition_rip(n: int, aat_csr, K: int, cap: Optional[int] = None, eps: float = 0.0,

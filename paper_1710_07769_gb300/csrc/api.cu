@@ -121,6 +121,7 @@ struct cimmino_ctx {
   DBuf<int64_t> rp, cp, brp, crp;
   DBuf<int32_t> ci, ri, bci, cci, perm;
   DBuf<double> va, cv, d, bcv, ccv, rowabs, sval;
+  DBuf<double> cs;  // column equilibration divisors (allocated when opts.ruiz_sweeps > 0)
   DBuf<int64_t> soff, aoff, toff;
   DBuf<int16_t> scol;
   DBuf<int32_t> acol, tcol;
@@ -171,6 +172,7 @@ void opts_default(cimmino_opts *o) {
   o->keep_aat = 0;
   o->multi_rhs = 1;
   o->refine_relax = 0;
+  o->ruiz_sweeps = 0;
   o->stream = nullptr;
 }
 
@@ -185,6 +187,8 @@ void check_opts(const cimmino_opts &o) {
   if (o.max_iter < 0) fail(CIMMINO_EINVAL, "opts.max_iter must be >= 0");
   if (o.check_every < 1 || o.check_every > 1024)
     fail(CIMMINO_EINVAL, "opts.check_every not in [1,1024]");
+  if (o.ruiz_sweeps < 0 || o.ruiz_sweeps > 100)
+    fail(CIMMINO_EINVAL, "opts.ruiz_sweeps not in [0,100]");
 }
 
 // ------------------------------------------------------------------ setup
@@ -308,6 +312,22 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                        : "column indices not strictly increasing within a row";
     fail(CIMMINO_EINVAL, "malformed CSR: " + why);
   }
+  // ---- row and column equilibration (Section 3.1), in place on our own copy of A's values
+  DBuf<double> rs;
+  if (c->opts.ruiz_sweeps > 0) {
+    if (dv0 != v0.p) {  // caller-owned device values: copy before scaling
+      v0.alloc(NNZ);
+      CUDA_TRY(cudaMemcpyAsync(v0.p, dv0, sizeof(double) * NNZ, cudaMemcpyDefault, s));
+      dv0 = v0.p;
+    }
+    DBuf<double> work;
+    work.alloc(3 * N);
+    rs.alloc(N);
+    c->cs.alloc(N);
+    launch_equilibrate(drp0, dci0, v0.p, N, c->opts.ruiz_sweeps, rs.p, c->cs.p, work.p, s);
+    c->setup_launches += 1 + 3 * c->opts.ruiz_sweeps;
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   // ---- permutation and blocks
   std::vector<int32_t> hperm(N);
   for (int32_t q = 0; q < nsys; ++q) {
@@ -354,7 +374,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   c->va.alloc(NNZ);
   c->d.alloc(N);
   launch_scale_permute(drp0, dci0, dv0, c->perm.p, c->rp.p, N, c->ci.p, c->va.p, c->d.p,
-                       flag.p + 1, s);
+                       c->opts.ruiz_sweeps > 0 ? rs.p : nullptr, flag.p + 1, s);
   c->setup_launches += 1;
   // ---- transpose
   c->cp.alloc(N + 1);
@@ -369,6 +389,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   rp0.release();
   ci0.release();
   v0.release();
+  rs.release();
 
   // ---- C = A A^T (Section 2.3)
   DBuf<int64_t> cntc;
@@ -649,7 +670,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   c->cta.alloc(c->hcta.size());
   h2d(c->cta.p, c->hcta.data(), c->hcta.size(), s);
   c->rowabs.alloc(N);
-  launch_row_abs(c->rp.p, c->va.p, c->d.p, N, c->rowabs.p, s);
+  launch_row_abs(c->rp.p, c->ci.p, c->va.p, c->d.p, c->cs.p, N, c->rowabs.p, s);
   c->setup_launches += 1;
   // projection ring: as many factor-tile slots as fit beside the block vectors
   bool any64 = false;
@@ -696,6 +717,7 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.ri = c->ri.p;
   a.cv = c->cv.p;
   a.d = c->d.p;
+  a.cs = c->cs.p;
   a.brp = c->brp.p;
   a.bci = c->bci.p;
   a.bcv = c->bcv.p;
@@ -830,6 +852,8 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   }
   // backward error gamma (Eq. 3.1) per lane
   launch_final_stats(a, c->Fin.p, c->rowabs.p, c->stats4.p, s);
+  // the CG iterate lives in the column-scaled space y = diag(cs) x
+  if (a.cs) launch_unscale_cols(c->x.p, a.cs, c->N, nrhs, s);
   std::vector<double> h4((size_t)4 * c->hcta.size() * nrhs);
   d2h(h4.data(), c->stats4.p, h4.size(), s);
   int64_t rtot = 0;
@@ -875,7 +899,8 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.factor_bytes = c->factor_bytes;
         o.pass_bytes = c->pass_bytes;
         // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
-        o.kernel_launches = c->setup_launches + 5 + 5 * launched + (nrhs > 1 ? 1 : 0);
+        o.kernel_launches =
+            c->setup_launches + 5 + 5 * launched + (nrhs > 1 ? 1 : 0) + (a.cs ? 1 : 0);
       }
     }
   }
@@ -1049,6 +1074,21 @@ int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double
   }
 }
 
+int cimmino_get_colscale(cimmino_ctx *ctx, double *cs) {
+  if (!ctx || !cs) return CIMMINO_EINVAL;
+  try {
+    if (!ctx->cs.p) {
+      for (int64_t j = 0; j < ctx->N; ++j) cs[j] = 1.0;
+      return CIMMINO_OK;
+    }
+    d2h(cs, ctx->cs.p, ctx->N, ctx->stream);
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(ctx, e);
+  }
+}
+
 int cimmino_get_scaled(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double *val,
                        double *d) {
   if (!ctx || !row_ptr || !col_idx || !val || !d) return CIMMINO_EINVAL;
@@ -1213,6 +1253,7 @@ int cimmino_sweeps(cimmino_ctx *ctx, const double *f, int32_t nrhs, double omega
     h2d(ctx->Fin.p, f, N * nrhs, s);
     launch_rhs_scale(ctx->args, ctx->Fin.p, ctx->perm.p, s);
     for (int32_t t = 0; t < sweeps; ++t) launch_cim_sweep(ctx->args, omega, s);
+    if (ctx->args.cs) launch_unscale_cols(ctx->x.p, ctx->args.cs, N, nrhs, s);
     cols_out(ctx, ctx->x.p, nrhs, x, s);
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());

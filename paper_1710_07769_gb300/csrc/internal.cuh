@@ -150,9 +150,14 @@ void launch_scan_counts(const int64_t *counts, int64_t *out, int64_t n, int64_t 
                         int64_t tmp_len, cudaStream_t s);
 void launch_permuted_lengths(const int64_t *rp0, const int32_t *perm, int64_t N, int64_t *len,
                              cudaStream_t s);
+// Section 3.1 equilibration, in place on v (pattern rp/ci): `sweeps` sweeps of
+// row and column infinity-norm scaling; rs / cs receive the accumulated divisors
+// (A = diag(rs) Ae diag(cs)).  work: 3 N doubles of scratch.
+void launch_equilibrate(const int64_t *rp, const int32_t *ci, double *v, int64_t N,
+                        int32_t sweeps, double *rs, double *cs, double *work, cudaStream_t s);
 void launch_scale_permute(const int64_t *rp0, const int32_t *ci0, const double *v0,
                           const int32_t *perm, const int64_t *rp, int64_t N, int32_t *ci,
-                          double *va, double *d, int32_t *flag, cudaStream_t s);
+                          double *va, double *d, const double *rs, int32_t *flag, cudaStream_t s);
 void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, int64_t N,
                       int64_t nnz, int64_t *cp, int32_t *ri, double *cv, int64_t *work,
                       int64_t *tmp, int64_t tmp_len, cudaStream_t s);
@@ -225,6 +230,7 @@ struct IterArgs {
   const int32_t *ri;
   const double *cv;
   const double *d;
+  const double *cs;  // column equilibration divisors (x = y / cs), nullptr when off
   const int64_t *brp;
   const int32_t *bci;
   const double *bcv;
@@ -316,7 +322,9 @@ void launch_iteration(const IterArgs &a, cudaStream_t s);
 void launch_cim_sweep(const IterArgs &a, double omega, cudaStream_t s);
 void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,
                         cudaStream_t s);
-void launch_row_abs(const int64_t *rp, const double *va, const double *d, int64_t N,
-                    double *rowabs, cudaStream_t s);
+void launch_row_abs(const int64_t *rp, const int32_t *ci, const double *va, const double *d,
+                    const double *cs, int64_t N, double *rowabs, cudaStream_t s);
+// x (N x nrhs, [column][rhs]) /= cs per column: the column-scaled iterate back to x
+void launch_unscale_cols(double *x, const double *cs, int64_t N, int32_t nrhs, cudaStream_t s);
 
 }  // namespace cimmino

@@ -19,6 +19,7 @@
 #include <numeric>
 #include <queue>
 #include <random>
+#include <new>
 #include <vector>
 
 #include "../../include/cimmino.h"
@@ -495,4 +496,76 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
   } catch (...) {
     return CIMMINO_ENOMEM;
   }
+}
+
+// Section 2.3, dense columns: a column of A with more than sqrt(n) nonzeros makes the
+// rows that share it pairwise adjacent, so C = A A^T, and the graph, turn dense.  The
+// graph is therefore built from a copy of A in which every column with more than
+// t = floor(sqrt(n)) nonzeros keeps only its t entries of largest magnitude; equal
+// magnitudes keep the lower row first, so the kept set is unique.  The solve itself
+// always uses the full A.
+extern "C" int cimmino_sparsify_dense_columns(int64_t n, const int64_t *rp, const int32_t *ci,
+                                              const double *val, int64_t *out_rp,
+                                              int32_t *out_ci, double *out_val,
+                                              int64_t *nnz_out) {
+  if (n < 1 || !rp || !ci || !val || !out_rp || !out_ci || !out_val || !nnz_out)
+    return CIMMINO_EINVAL;
+  const int64_t nnz = rp[n];
+  if (rp[0] != 0 || nnz < 0) return CIMMINO_EINVAL;
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return CIMMINO_EINVAL;
+  int64_t t = (int64_t)std::sqrt((double)n);
+  while (t * t > n) --t;
+  while ((t + 1) * (t + 1) <= n) ++t;
+  try {
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t q = 0; q < nnz; ++q) {
+      if (ci[q] < 0 || ci[q] >= n) return CIMMINO_EINVAL;
+      ++cnt[ci[q] + 1];
+    }
+    std::vector<char> keep(nnz, 1);
+    // entries of the dense columns, grouped by column (rows increasing inside a column)
+    std::vector<int64_t> start(n + 1, 0);
+    for (int64_t j = 0; j < n; ++j) start[j + 1] = start[j] + (cnt[j + 1] > t ? cnt[j + 1] : 0);
+    if (start[n] > 0) {
+      std::vector<int64_t> pos(start[n]);
+      std::vector<int32_t> row(start[n]);
+      std::vector<int64_t> fill(start.begin(), start.end() - 1);
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+          if (cnt[ci[q] + 1] > t) {
+            const int64_t w = fill[ci[q]]++;
+            pos[w] = q;
+            row[w] = (int32_t)i;
+          }
+      std::vector<int64_t> idx;
+      for (int64_t j = 0; j < n; ++j) {
+        const int64_t a = start[j], b = start[j + 1];
+        if (b == a) continue;
+        idx.resize(b - a);
+        std::iota(idx.begin(), idx.end(), a);
+        auto before = [&](int64_t x, int64_t y) {
+          const double ax = std::fabs(val[pos[x]]), ay = std::fabs(val[pos[y]]);
+          return ax > ay || (ax == ay && row[x] < row[y]);
+        };
+        std::nth_element(idx.begin(), idx.begin() + t, idx.end(), before);
+        for (size_t k = (size_t)t; k < idx.size(); ++k) keep[pos[idx[k]]] = 0;
+      }
+    }
+    int64_t w = 0;
+    out_rp[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        if (keep[q]) {
+          out_ci[w] = ci[q];
+          out_val[w] = val[q];
+          ++w;
+        }
+      out_rp[i + 1] = w;
+    }
+    *nnz_out = w;
+  } catch (const std::bad_alloc &) {
+    return CIMMINO_ENOMEM;
+  }
+  return CIMMINO_OK;
 }

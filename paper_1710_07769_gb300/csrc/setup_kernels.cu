@@ -141,13 +141,63 @@ __global__ void k_permuted_lengths(const int64_t *__restrict__ rp0, const int32_
   len[r] = rp0[o + 1] - rp0[o];
 }
 
+// ---------------------------------------------------------------- equilibration
+// Section 3.1: before the row 2-norm step, rows and columns are scaled so that the
+// largest magnitude of every row and column tends to one.  One sweep takes the
+// row maxima and the column maxima of the current matrix and divides entry (i, j)
+// by sqrt(rmax_i) * sqrt(cmax_j) (an empty row or column keeps divisor 1).  Column
+// maxima are combined with an integer atomicMax on the bit patterns, which order
+// like the values for non-negative doubles, so the result does not depend on the
+// order of the atomics.
+__global__ void k_fill_one(double *__restrict__ a, double *__restrict__ b, int64_t N) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) a[i] = b[i] = 1.0;
+}
+
+__global__ void k_equil_max(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int64_t N, double *__restrict__ rdiv,
+                            unsigned long long *__restrict__ cmax) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  double m = 0.0;
+  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+    const double a = fabs(v[q]);
+    if (a > m) m = a;
+    atomicMax(&cmax[ci[q]], (unsigned long long)__double_as_longlong(a));
+  }
+  rdiv[r] = m > 0.0 ? __dsqrt_rn(m) : 1.0;
+}
+
+__global__ void k_equil_cols(unsigned long long *__restrict__ cmax, int64_t N,
+                             double *__restrict__ cdiv, double *__restrict__ cs) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double m = __longlong_as_double((long long)cmax[j]);
+  cmax[j] = 0ull;  // ready for the next sweep
+  const double dv = m > 0.0 ? __dsqrt_rn(m) : 1.0;
+  cdiv[j] = dv;
+  cs[j] = __dmul_rn(cs[j], dv);
+}
+
+__global__ void k_equil_apply(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              double *__restrict__ v, int64_t N, const double *__restrict__ rdiv,
+                              const double *__restrict__ cdiv, double *__restrict__ rs) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const double dr = rdiv[r];
+  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) v[q] = __ddiv_rn(v[q], __dmul_rn(dr, cdiv[ci[q]]));
+  rs[r] = __dmul_rn(rs[r], dr);
+}
+
 // Section 2.1: every row is divided by its 2-norm (so that the entries of
 // A A^T are cosines); Section 2.2: permuted row r is original row perm[r].
+// With equilibration, d[r] also carries the row's equilibration divisor rs.
 __global__ void k_scale_permute(const int64_t *__restrict__ rp0, const int32_t *__restrict__ ci0,
                                 const double *__restrict__ v0, const int32_t *__restrict__ perm,
                                 const int64_t *__restrict__ rp, int64_t N,
                                 int32_t *__restrict__ ci, double *__restrict__ va,
-                                double *__restrict__ d, int32_t *flag) {
+                                double *__restrict__ d, const double *__restrict__ rs,
+                                int32_t *flag) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   int64_t o = perm[r];
@@ -159,7 +209,7 @@ __global__ void k_scale_permute(const int64_t *__restrict__ rp0, const int32_t *
     atomicOr(flag, 1);
     nr = 1.0;
   }
-  d[r] = nr;
+  d[r] = rs ? __dmul_rn(nr, rs[o]) : nr;
   int64_t w = rp[r];
   for (int64_t q = a; q < b; ++q, ++w) {
     ci[w] = ci0[q];
@@ -601,9 +651,23 @@ void launch_permuted_lengths(const int64_t *rp0, const int32_t *perm, int64_t N,
 
 void launch_scale_permute(const int64_t *rp0, const int32_t *ci0, const double *v0,
                           const int32_t *perm, const int64_t *rp, int64_t N, int32_t *ci,
-                          double *va, double *d, int32_t *flag, cudaStream_t s) {
+                          double *va, double *d, const double *rs, int32_t *flag,
+                          cudaStream_t s) {
   k_scale_permute<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp0, ci0, v0, perm, rp, N, ci, va,
-                                                             d, flag);
+                                                             d, rs, flag);
+}
+
+void launch_equilibrate(const int64_t *rp, const int32_t *ci, double *v, int64_t N,
+                        int32_t sweeps, double *rs, double *cs, double *work, cudaStream_t s) {
+  double *rdiv = work, *cdiv = work + N;
+  unsigned long long *cmax = reinterpret_cast<unsigned long long *>(work + 2 * N);
+  k_fill_one<<<grid_for(N, kThreads), kThreads, 0, s>>>(rs, cs, N);
+  cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * N, s);
+  for (int32_t t = 0; t < sweeps; ++t) {
+    k_equil_max<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp, ci, v, N, rdiv, cmax);
+    k_equil_cols<<<grid_for(N, kThreads), kThreads, 0, s>>>(cmax, N, cdiv, cs);
+    k_equil_apply<<<grid_for(N, kThreads), kThreads, 0, s>>>(rp, ci, v, N, rdiv, cdiv, rs);
+  }
 }
 
 void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, int64_t N,

@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kThreads)
       double sx = 0.0;
       for (int64_t q = a.rp[r]; q < a.rp[r + 1]; ++q) sx = fma(a.va[q], a.x[(int64_t)a.ci[q] * a.nrhs + k], sx);
       rmax = fabs(a.d[r] * (a.fs[r * a.nrhs + k] - sx));
-      x1 = fabs(a.x[r * a.nrhs + k]);
+      x1 = a.cs ? fabs(a.x[r * a.nrhs + k] / a.cs[r]) : fabs(a.x[r * a.nrhs + k]);
       fmax_ = fabs(Fin[(int64_t)k * a.N + r]);
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -682,13 +682,25 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void k_row_abs(const int64_t *__restrict__ rp, const double *__restrict__ va,
-                          const double *__restrict__ d, int64_t N, double *__restrict__ rowabs) {
+// ||row r of the original A||_1 = d_r * sum_j |S_rj| cs_j (S the scaled permuted matrix)
+__global__ void k_row_abs(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ va, const double *__restrict__ d,
+                          const double *__restrict__ cs, int64_t N, double *__restrict__ rowabs) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   double s = 0.0;
-  for (int64_t q = rp[r]; q < rp[r + 1]; ++q) s += fabs(va[q]);
+  if (cs)
+    for (int64_t q = rp[r]; q < rp[r + 1]; ++q) s += fabs(va[q]) * cs[ci[q]];
+  else
+    for (int64_t q = rp[r]; q < rp[r + 1]; ++q) s += fabs(va[q]);
   rowabs[r] = s * d[r];
+}
+
+__global__ void k_unscale_cols(double *__restrict__ x, const double *__restrict__ cs, int64_t N,
+                               int32_t nrhs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * nrhs) return;
+  x[i] = x[i] / cs[i / nrhs];
 }
 
 }  // namespace
@@ -743,9 +755,14 @@ void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowa
   k_final_stats<<<a.ncta, kThreads, 0, s>>>(a, Fin, rowabs, out);
 }
 
-void launch_row_abs(const int64_t *rp, const double *va, const double *d, int64_t N,
-                    double *rowabs, cudaStream_t s) {
-  k_row_abs<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rp, va, d, N, rowabs);
+void launch_row_abs(const int64_t *rp, const int32_t *ci, const double *va, const double *d,
+                    const double *cs, int64_t N, double *rowabs, cudaStream_t s) {
+  k_row_abs<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rp, ci, va, d, cs, N, rowabs);
+}
+
+void launch_unscale_cols(double *x, const double *cs, int64_t N, int32_t nrhs, cudaStream_t s) {
+  const int64_t tot = N * nrhs;
+  k_unscale_cols<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, cs, N, nrhs);
 }
 
 }  // namespace cimmino

@@ -352,3 +352,71 @@ def test_cimmino_sweeps_match_oracle(sys_small, precision, tol):
         X = s.sweeps(F, 1.3, sweeps)
         for k in range(2):
             assert rel(X[k], o.cimmino_sweeps(F[k], 1.3, sweeps)) <= tol, (sweeps, k)
+
+
+# ------------------------------------------------------------------ equilibration (Section 3.1)
+
+@pytest.fixture(scope="module")
+def sys_badly_scaled():
+    """The 700-row random matrix with rows and columns multiplied by 10^U[-1.5,1.5]: the
+    oracle's CG takes 3596 iterations without equilibration and 125-128 with 10 sweeps.
+    (With a wider spread the residual creeps across 1e-10 by a few percent per
+    iteration, and rounding alone moves the crossing by more than one iteration.)"""
+    A = inputs.random_dd(700, 5, 11)
+    rng = np.random.default_rng(41)
+    rf, cf = 10.0 ** rng.uniform(-1.5, 1.5, 700), 10.0 ** rng.uniform(-1.5, 1.5, 700)
+    rows = np.repeat(np.arange(700), np.diff(A.row_ptr))
+    B = inputs.CSR(700, A.row_ptr.copy(), A.col_idx.copy(), A.val * rf[rows] * cf[A.col_idx])
+    perm = np.random.default_rng(5).permutation(700).astype(np.int32)
+    F = np.stack([inputs.matvec(B, rng.uniform(-1, 1, 700)) for _ in range(3)])
+    return B, perm, F, oracle.Oracle(B, RAGGED, perm=perm, ruiz=10)
+
+
+def test_equilibration_setup_bitwise(sys_badly_scaled):
+    """Equilibrated, row-normalised, permuted matrix, its row factors d and the column
+    divisors cs: the same rounded operations in the same order on both sides."""
+    B, perm, F, o = sys_badly_scaled
+    s = g.Solver(B, RAGGED, perm=perm, ruiz_sweeps=10)
+    rp, ci, v, d = s.scaled_csr(B.nnz)
+    orp, oci, ov, od = o.scaled()
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    assert np.array_equal(v, ov) and np.array_equal(d, od)
+    assert np.array_equal(s.colscale(), o.equil()[1])
+    assert np.array_equal(g.Solver(B, RAGGED, perm=perm).colscale(), np.ones(700))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-10)])
+def test_equilibrated_projection_and_solve_match_oracle(sys_badly_scaled, precision, tol):
+    """H of the column-scaled system (FP32 blocks: kappa(G_i) <= 72, so the refined inner
+    solves hold H v to 1e-10); three right-hand sides solved at
+    once, each returned as x = y / cs, with the oracle's iteration count +-1 and gamma."""
+    B, perm, F, o = sys_badly_scaled
+    s = g.Solver(B, RAGGED, perm=perm, precision=precision, ruiz_sweeps=10)
+    v = np.random.default_rng(8).standard_normal(700)
+    assert rel(s.project(v), o.project(v)) <= tol
+    assert rel(s.project_rhs(F[0]), o.project_rhs(F[0])) <= tol
+    X, st, code = s.solve(F)
+    assert code == 0
+    for k in range(3):
+        xo, ito, rro, go, sto = o.solve(F[k])
+        assert sto == 0 and abs(st[k]["iters"] - ito) <= 1, (k, st[k]["iters"], ito)
+        assert st[k]["rel_res"] <= 1e-10
+        assert rel(X[k], xo) <= 1e-8, k
+        # gamma of Eq. 3.1 for the returned x, recomputed on the host with the original A
+        res = F[k] - inputs.matvec(B, X[k])
+        ainf = np.add.reduceat(np.abs(B.val), B.row_ptr[:-1]).max()
+        gam = np.abs(res).max() / (ainf * np.abs(X[k]).sum() + np.abs(F[k]).max())
+        assert st[k]["backward_err"] == pytest.approx(gam, rel=0.05)
+    # one right-hand side alone (the single-vector kernels) reaches the same x
+    x1, st1, code1 = s.solve(F[1])
+    assert code1 == 0 and abs(st1[0]["iters"] - st[1]["iters"]) <= 1
+    assert rel(x1, o.solve(F[1])[0]) <= 1e-8
+
+
+def test_equilibrated_sweeps_match_oracle(sys_badly_scaled):
+    B, perm, F, o = sys_badly_scaled
+    s = g.Solver(B, RAGGED, perm=perm, ruiz_sweeps=10)
+    for sweeps in (1, 12):
+        X = s.sweeps(F[:2], 0.9, sweeps)
+        for k in range(2):
+            assert rel(X[k], o.cimmino_sweeps(F[k], 0.9, sweeps)) <= 1e-11, (sweeps, k)

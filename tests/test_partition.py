@@ -59,3 +59,59 @@ def test_partition_solves_like_any_partition():
     assert st == 0 and rr <= 1e-10
     x2, it2, *_ = oracle.Oracle(A, inputs.contiguous_blocks(A.n, 256)).solve(f)
     np.testing.assert_allclose(x, x2, atol=1e-8)
+
+
+def matrix_with_dense_columns(n, ndense, seed):
+    """A 2D stencil plus ndense columns holding n/3 random entries each."""
+    B = inputs.convdiff2d(int(np.sqrt(n)), 20.0)
+    n = B.n
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(n), np.diff(B.row_ptr))
+    r, c, v = [rows], [B.col_idx.astype(np.int64)], [B.val]
+    for j in rng.choice(n, ndense, replace=False):
+        rr = rng.choice(n, n // 3, replace=False)
+        r.append(rr)
+        c.append(np.full(len(rr), j))
+        v.append(rng.choice([-1.0, 0.5, 2.0], len(rr)) * rng.integers(1, 4, len(rr)))  # ties
+    r, c, v = np.concatenate(r), np.concatenate(c), np.concatenate(v)
+    key = r * n + c
+    uk, first = np.unique(key, return_index=True)        # keep one entry per (row, col)
+    r, c, v = r[first], c[first], v[first]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, r + 1, 1)
+    return inputs.CSR(n, np.cumsum(rp), c.astype(np.int32), v)
+
+
+@pytest.mark.parametrize("n,ndense,seed", [(400, 2, 1), (2500, 5, 2), (4900, 1, 3)])
+def test_sparsify_dense_columns_matches_oracle(n, ndense, seed):
+    """The library's dense-column rule (Section 2.3) returns exactly the oracle's copy."""
+    A = matrix_with_dense_columns(n, ndense, seed)
+    rp, ci, v = g.sparsify_dense_columns(A)
+    orp, oci, ov = oracle.sparsify_dense_columns(A)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(v, ov)
+    t = int(np.floor(np.sqrt(A.n)))
+    before = np.bincount(A.col_idx, minlength=A.n)
+    after = np.bincount(ci, minlength=A.n)
+    assert (before > t).sum() == ndense
+    assert np.array_equal(after, np.where(before > t, t, before))
+
+
+def test_partition_after_sparsifying_dense_columns():
+    """With dense columns C = A A^T is nearly dense; the graph of the sparsified copy is
+    small, and its partition is still a valid one that beats contiguous blocks on the
+    cut of the full C."""
+    A = matrix_with_dense_columns(2500, 3, 7)
+    C_full = oracle.aat_plain(A)
+    S = inputs.CSR(A.n, *g.sparsify_dense_columns(A))
+    C_sp = oracle.aat_plain(S)
+    assert len(C_sp[1]) * 20 < len(C_full[1])
+    K = 10
+    perm, bp, _ = g.partition_rip(A.n, C_sp, K, eps=0.05, seed=3)
+    assert np.array_equal(np.sort(perm), np.arange(A.n))
+    assert np.diff(bp).max() <= int(np.ceil(A.n / K * 1.05))
+    rows = np.repeat(np.arange(A.n), np.diff(C_full[0]))
+    d = np.sqrt(C_full[2][rows == C_full[1]])
+    cos = (C_full[0], C_full[1], C_full[2] / (d[rows] * d[C_full[1]]))
+    cut_gp = oracle.cutsize(*cos, part_of(perm, bp, A.n))
+    contiguous = np.repeat(np.arange(K), A.n // K).astype(np.int32)
+    assert cut_gp < oracle.cutsize(*cos, contiguous)
