@@ -372,6 +372,10 @@ def sys_badly_scaled():
     return B, perm, F, oracle.Oracle(B, RAGGED, perm=perm, ruiz=10)
 
 
+def kappa2(B):
+    return np.linalg.cond(B.to_dense())
+
+
 def test_equilibration_setup_bitwise(sys_badly_scaled):
     """Equilibrated, row-normalised, permuted matrix, its row factors d and the column
     divisors cs: the same rounded operations in the same order on both sides."""
@@ -397,11 +401,14 @@ def test_equilibrated_projection_and_solve_match_oracle(sys_badly_scaled, precis
     assert rel(s.project_rhs(F[0]), o.project_rhs(F[0])) <= tol
     X, st, code = s.solve(F)
     assert code == 0
+    # two x with relative residual <= 1e-10 differ by at most 2 kappa(A) 1e-10 relative
+    # (kappa(A) is about 1.2e6 here); a wrong column unscaling is off by O(1)
+    xbound = 2 * kappa2(B) * 1e-10
     for k in range(3):
         xo, ito, rro, go, sto = o.solve(F[k])
         assert sto == 0 and abs(st[k]["iters"] - ito) <= 1, (k, st[k]["iters"], ito)
         assert st[k]["rel_res"] <= 1e-10
-        assert rel(X[k], xo) <= 1e-8, k
+        assert rel(X[k], xo) <= xbound, k
         # gamma of Eq. 3.1 for the returned x, recomputed on the host with the original A
         res = F[k] - inputs.matvec(B, X[k])
         ainf = np.add.reduceat(np.abs(B.val), B.row_ptr[:-1]).max()
@@ -410,7 +417,7 @@ def test_equilibrated_projection_and_solve_match_oracle(sys_badly_scaled, precis
     # one right-hand side alone (the single-vector kernels) reaches the same x
     x1, st1, code1 = s.solve(F[1])
     assert code1 == 0 and abs(st1[0]["iters"] - st[1]["iters"]) <= 1
-    assert rel(x1, o.solve(F[1])[0]) <= 1e-8
+    assert rel(x1, o.solve(F[1])[0]) <= xbound
 
 
 def test_equilibrated_sweeps_match_oracle(sys_badly_scaled):
