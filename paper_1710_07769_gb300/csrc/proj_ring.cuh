@@ -60,12 +60,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
   }
   return false;
 }
+// L2 policy for the factor stream: each tile is read once per pass and the stream is
+// several times larger than L2, so its lines go first; the Gram copy, A, A^T and the
+// vectors that every CG iteration re-reads keep their place in L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
+                                         uint64_t *bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
 // consumer-only barrier (8 warps) and whole-CTA barrier (consumers + producer)
@@ -107,7 +115,7 @@ __device__ __forceinline__ void slot_fill(const Ring &R, uint32_t &t, const void
       atomicOr(err, 2);
     } else {
       mbar_expect_tx(&R.full[s], bytes);
-      bulk_g2s(R.base + (size_t)s * R.slot_bytes, src, bytes, &R.full[s]);
+      bulk_g2s(R.base + (size_t)s * R.slot_bytes, src, bytes, &R.full[s], l2_evict_first());
     }
   }
   ++t;
