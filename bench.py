@@ -380,17 +380,39 @@ def main():
     ap.add_argument("--layout", default="skyline", choices=["skyline", "dense"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--no-gp", action="store_true", help="skip the graph-partitioned leg")
-    ap.add_argument("--profile", default=None, choices=["fp64", "fp32_refine"],
-                    help="profiling target: one setup + 4 CG iterations, nothing timed")
+    ap.add_argument("--profile", default=None,
+                    choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "cholesky_tc", "spgemm"],
+                    help="profiling target, nothing timed: fp64 / fp32_refine / "
+                         "fp32_refine_16rhs = one setup + 4 CG iterations of the workload "
+                         "(16 right-hand sides sharing the factors for the last); cholesky_tc = "
+                         "setup of 128 dense 2048-row Gram blocks (random n = 2^18, 8 entries "
+                         "per row); spgemm = standalone C = A A^T of the workload")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.profile:
+        import numpy as np
+
         import inputs
         import paper_1710_07769_gb300 as g
-        w = inputs.workload(args.config)
-        s = g.Solver(w.A, w.block_ptr, perm=w.perm, precision=args.profile, layout=args.layout,
+        if args.profile == "spgemm":
+            w = inputs.workload(args.config)
+            rp, ci, v = g.aat(w.A)
+            print(json.dumps({"profile": "spgemm", "workload": w.name, "nnz_aat": int(len(v))}))
+            return 0
+        if args.profile == "cholesky_tc":
+            n = 1 << 18
+            A = inputs.random_dd(n, 8, 3)
+            s = g.Solver(A, inputs.contiguous_blocks(n, 2048), precision="fp32_refine", max_iter=1)
+            x, st, code = s.solve(inputs.matvec(A, np.ones(n)), tol=TOL)
+            print(json.dumps({"profile": "cholesky_tc", "n": n, "factor_ms": st[0]["t_factor_ms"]}))
+            s.close()
+            return 0
+        multi = args.profile == "fp32_refine_16rhs"
+        w = inputs.workload(args.config, nrhs=16 if multi else None)
+        s = g.Solver(w.A, w.block_ptr, perm=w.perm,
+                     precision="fp32_refine" if multi else args.profile, layout=args.layout,
                      max_iter=4, check_every=1)
-        x, st, code = s.solve(w.F[0], tol=TOL)
+        x, st, code = s.solve(w.F if multi else w.F[0], tol=TOL)
         print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
                           "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
         s.close()

@@ -224,10 +224,16 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
     ++t;
   }
   csync();
-  // F1: w_I = out_I - sum_{J<I} N_IJ w_J (sequential over I)
+  // F1: w_I = out_I - sum_{J<I} N_IJ w_J (sequential over I).  Only the last tile of a
+  // row, J = I-1, needs the w of the step just finished, so the barrier that publishes
+  // w_{I-1} sits right before that tile and the row's other tiles run while slower warps
+  // are still reducing.  A row without that tile ends with the barrier instead, so every
+  // w_J is published before any later step reads it.
   for (int I = 0; I < nt; ++I) {
     W a[4] = {W(0), W(0), W(0), W(0)};
-    for (int J = tr[I].j0; J < I; ++J) {
+    const int j0 = tr[I].j0;
+    for (int J = j0; J < I; ++J) {
+      if (J == I - 1) csync();
       tile_rows(static_cast<const W *>(slot_acquire(R, t, err)), w + J * T, rg, cg, a);
       slot_release(R, t);
       ++t;
@@ -235,21 +241,25 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
     const W c = reduce_rows(a, lane, row);
     const int o = I * T + 4 * rg + row;
     if (writer) w[o] = out[o] - c;
-    csync();
+    if (j0 >= I) csync();
   }
-  // B1: w_I = w_I - sum_{J>I} NT_IJ w_J (sequential over I descending)
+  csync();
+  // B1: w_I = w_I - sum_{J>I} NT_IJ w_J (sequential over I descending); the tiles of a row
+  // come in descending J, so the one that needs the previous step, J = I+1, is last
   for (int I = nt - 1; I >= 0; --I) {
     W a[4] = {W(0), W(0), W(0), W(0)};
     const int j1 = trT[I].j0;
-    for (int J = I + 1; J <= j1; ++J) {
+    for (int J = j1; J > I; --J) {
+      if (J == I + 1) csync();
       tile_rows(static_cast<const W *>(slot_acquire(R, t, err)), w + J * T, rg, cg, a);
       slot_release(R, t);
       ++t;
     }
     const W c = reduce_rows(a, lane, row);
     if (writer) w[I * T + 4 * rg + row] -= c;
-    csync();
+    if (j1 <= I) csync();
   }
+  csync();
   // B2: out_I = inv(L_II)^T w_I (packed upper triangles, one warp per tile)
   for (int I = 0; I < nt; ++I) {
     const W *D = static_cast<const W *>(slot_acquire(R, t, err));
@@ -278,7 +288,7 @@ __device__ void producer_pass(const Ring &R, const TileRow *__restrict__ tr,
   for (int I = nt - 1; I >= 0; --I) {
     const TileRow U = trT[I];
     const unsigned char *row = facT + (size_t)U.off * esz;
-    for (int J = I + 1; J <= U.j0; ++J) issue(row + (size_t)(J - I - 1) * TB);
+    for (int J = U.j0; J > I; --J) issue(row + (size_t)(J - I - 1) * TB);
   }
   for (int I = 0; I < nt; ++I) slot_fill(R, t, dinvT + (size_t)I * diag_bytes, diag_bytes, err);
 }
