@@ -18,10 +18,12 @@
 //    rectangular full packed in FP64 (2176 of 4096 values), block-packed in FP32 (2688).
 //    Every consumer warp waits for and releases every slot in order, so a warp never waits on a slot more than one use ahead (which would
 //    make the mbarrier phase parity ambiguous).
-//  * Chain steps: thread (rg, cg) owns rows 4rg..4rg+3 and four columns of each tile
-//    (4 x 4 register block: 16 FMAs per tile from 4 or 8 16-byte loads of the tile and
-//    1 or 2 of the vector); a quarter-warp's 16-byte loads cover 8 distinct bank groups.
-//    The 16 column groups of a row meet in a 5-shuffle butterfly.
+//  * Chain steps: every consumer thread does 16 FMAs per tile.  FP32: thread (rg, cg) owns
+//    rows 4rg..4rg+3 and four columns (4 x 4 register block, 4 16-byte loads of the tile
+//    and 1 of the vector), and the 16 column groups of a row meet in a 5-shuffle butterfly.
+//    FP64: rows 2rg, 2rg+1 and eight columns, an 8-lane reduction of 3 shuffles and 3 adds
+//    (GB300's FP64 pipe bounds the FP64 kernel, so adds count).  A quarter-warp's 16-byte
+//    loads cover 8 distinct bank groups in both layouts.
 //  * FP32 blocks are refined in FP64 against the exact Gram block (sliced-ELL copy):
 //    res = u - G_i y, y += L^{-T} L^{-1} res, until ||res|| <= tol ||u|| (refine_tol, or
 //    the relaxed inner tolerance of the lane inside CG iterations).
@@ -37,8 +39,9 @@ namespace {
 
 using namespace ring;
 
-// 4 x 4 register block of a row product: a[i] += sum over the thread's 4 columns of
-// L(4rg+i, c) v(c).  FP32: columns 4cg..4cg+3.  FP64: columns 2cg, 2cg+1, 32+2cg, 33+2cg.
+// Chain-step row products of a 64 x 64 tile with a vector, 16 FMAs per thread per tile.
+// FP32: thread (rg, cg) = (tid / 16, tid % 16) owns rows 4rg..4rg+3 and columns
+// 4cg..4cg+3 (4 x 4 register block).
 __device__ __forceinline__ void tile_rows(const float *L, const float *v, int rg, int cg,
                                           float (&a)[4]) {
   const float4 x = *reinterpret_cast<const float4 *>(v + 4 * cg);
@@ -51,19 +54,24 @@ __device__ __forceinline__ void tile_rows(const float *L, const float *v, int rg
     a[i] = fma(l.w, x.w, a[i]);
   }
 }
+// FP64: thread (rg, cg) = (tid / 8, tid % 8) owns rows 2rg, 2rg+1 and the column pairs
+// 2cg + 16k, 2cg + 16k + 1 (k < 4): a quarter-warp's 16-byte loads cover one contiguous
+// 128-byte row segment (no bank conflict), and the row sums need an 8-lane reduction of
+// 3 shuffles and 3 adds instead of 5 and 5 (GB300's FP64 pipe is this kernel's bound).
 __device__ __forceinline__ void tile_rows(const double *L, const double *v, int rg, int cg,
-                                          double (&a)[4]) {
-  const double2 x0 = *reinterpret_cast<const double2 *>(v + 2 * cg);
-  const double2 x1 = *reinterpret_cast<const double2 *>(v + 32 + 2 * cg);
+                                          double (&a)[2]) {
+  double2 x[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const double *Lr = L + (4 * rg + i) * T;
-    const double2 l0 = *reinterpret_cast<const double2 *>(Lr + 2 * cg);
-    const double2 l1 = *reinterpret_cast<const double2 *>(Lr + 32 + 2 * cg);
-    a[i] = fma(l0.x, x0.x, a[i]);
-    a[i] = fma(l0.y, x0.y, a[i]);
-    a[i] = fma(l1.x, x1.x, a[i]);
-    a[i] = fma(l1.y, x1.y, a[i]);
+  for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const double2 *>(v + 16 * k + 2 * cg);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double *Lr = L + (2 * rg + i) * T + 2 * cg;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 l = *reinterpret_cast<const double2 *>(Lr + 16 * k);
+      a[i] = fma(l.x, x[k].x, a[i]);
+      a[i] = fma(l.y, x[k].y, a[i]);
+    }
   }
 }
 
@@ -192,6 +200,19 @@ __device__ __forceinline__ W reduce_rows(const W (&a)[4], int lane, int &row) {
   return c;
 }
 
+// FP64 layout: sum of a[0..1] over the 8 column groups of a quarter-warp (3 shuffles,
+// fixed order).  Returns the sum of row 2rg + row, row = lane bit 2; the four lanes that
+// share that bit hold it.
+__device__ __forceinline__ double reduce_rows(const double (&a)[2], int lane, int &row) {
+  const bool hi = (lane & 4) != 0;
+  const double s = __shfl_xor_sync(0xffffffffu, hi ? a[0] : a[1], 4);
+  double c = (hi ? a[1] : a[0]) + s;
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  row = hi ? 1 : 0;
+  return c;
+}
+
 // Deterministic sum over the 256 consumer threads (fixed order).
 __device__ __forceinline__ double csum(double v, double *red) {
   v = warp_sum(v);
@@ -210,7 +231,9 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
                               const TileRow *__restrict__ trT, int nt, W *w, W *out, uint32_t &t,
                               int32_t *err) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const int rg = tid >> 4, cg = tid & 15;
+  constexpr bool D64 = sizeof(W) == 8;
+  constexpr int RPT = D64 ? 2 : 4;  // rows per thread in the chain steps
+  const int rg = D64 ? tid >> 3 : tid >> 4, cg = D64 ? tid & 7 : tid & 15;
   const bool writer = (lane & 3) == 0;
   int row;
   const int warp = tid >> 5;
@@ -230,7 +253,7 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
   // are still reducing.  A row without that tile ends with the barrier instead, so every
   // w_J is published before any later step reads it.
   for (int I = 0; I < nt; ++I) {
-    W a[4] = {W(0), W(0), W(0), W(0)};
+    W a[RPT] = {};
     const int j0 = tr[I].j0;
     for (int J = j0; J < I; ++J) {
       if (J == I - 1) csync();
@@ -239,7 +262,7 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
       ++t;
     }
     const W c = reduce_rows(a, lane, row);
-    const int o = I * T + 4 * rg + row;
+    const int o = I * T + RPT * rg + row;
     if (writer) w[o] = out[o] - c;
     if (j0 >= I) csync();
   }
@@ -247,7 +270,7 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
   // B1: w_I = w_I - sum_{J>I} NT_IJ w_J (sequential over I descending); the tiles of a row
   // come in descending J, so the one that needs the previous step, J = I+1, is last
   for (int I = nt - 1; I >= 0; --I) {
-    W a[4] = {W(0), W(0), W(0), W(0)};
+    W a[RPT] = {};
     const int j1 = trT[I].j0;
     for (int J = j1; J > I; --J) {
       if (J == I + 1) csync();
@@ -256,7 +279,7 @@ __device__ void consumer_pass(const Ring &R, const TileRow *__restrict__ tr,
       ++t;
     }
     const W c = reduce_rows(a, lane, row);
-    if (writer) w[I * T + 4 * rg + row] -= c;
+    if (writer) w[I * T + RPT * rg + row] -= c;
     if (j1 <= I) csync();
   }
   csync();
