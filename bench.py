@@ -34,7 +34,7 @@ TOL = 1e-10
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (recipe table); the FMA probe measured 1.196
 # DRAM bytes per k_proj launch from one ncu capture of the current kernel (ncu
 # --set full, 64^3 workload, CG iteration 1; profiles/k_proj_convdiff3d_64.md)
-PROJ_TRAFFIC = {"fp64": 660006144, "fp32": 726424320}
+PROJ_TRAFFIC = {"fp64": 659753728, "fp32": 726496512}
 
 
 def peaks():
@@ -260,7 +260,7 @@ def run_ours(args, rank, local):
     gp = None if args.no_gp else gp_leg(w, dA, dF, dX, stream, args.layout)
     hbm = float(pk.get("hbm_gbs", 6800.0))
     # FP64 projection: every streamed FP64 factor element feeds one FMA, so it is bound by
-    # GB300's FP64 pipe (ncu: FP64 pipe 71% / DRAM 33% busy); FP32 projection: HBM-bound.
+    # GB300's FP64 pipe (ncu: FP64 pipe 73% / DRAM 35% busy); FP32 projection: HBM-bound.
     flops64 = st64["pass_bytes"] / 4.0           # 2 flops per 8-byte element, one pass
     tf64 = flops64 / (kt64["proj_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_PEAK_TFLOPS,
