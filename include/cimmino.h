@@ -100,6 +100,10 @@ typedef struct cimmino_opts {
                           /* 0 (default): off.  Column scaling changes H (it acts  */
                           /* as a preconditioner); CG then runs on y = diag(cs) x, */
                           /* and solutions are returned as x                       */
+  int32_t time_proj;      /* 1: record CUDA events around every projection launch of */
+                          /* the CG iterations for cimmino_proj_timing(); the       */
+                          /* iterations are then launched eagerly, not as a graph   */
+                          /* (events inside a graph cannot be timed); 0 (default)   */
   void *stream;           /* cudaStream_t for all device work (NULL: own stream)   */
 } cimmino_opts;
 
@@ -305,6 +309,15 @@ int cimmino_sweeps(cimmino_ctx *ctx, const double *f, int32_t nrhs, double omega
  *         FP32 mode), ms[1] u = A p, ms[2] psi = A^T y.
  * ms is a caller array of 3 doubles.  Errors: EINVAL (no solve yet, reps < 1). */
 int cimmino_time_kernels(cimmino_ctx *ctx, int32_t reps, double *ms);
+
+/* Benchmark hook: device time of the projection launches inside the CG iterations of
+ * the last cimmino_solve() / cimmino_solve_batch() on a context set up with
+ * opts.time_proj = 1, measured live in the iteration sequence (CUDA events recorded on
+ * the context's stream before and after each projection launch).  Only the launches of
+ * iterations in which some lane was still running count (the projections that produced
+ * the returned x).  *ms_total receives their summed milliseconds, *launches their number.
+ * Errors: EINVAL (NULL pointer, time_proj off, no solve yet). */
+int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches);
 
 /* Library build information (compile-time architecture, version). */
 const char *cimmino_version(void);

@@ -35,7 +35,7 @@ EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimm
            "cimmino_get_aat", "cimmino_get_scaled", "cimmino_get_colscale", "cimmino_block_rows", "cimmino_get_factor",
            "cimmino_project", "cimmino_project_rhs", "cimmino_sweeps", "cimmino_aat",
            "cimmino_aat_noalloc",
-           "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_time_kernels", "cimmino_version"]
+           "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_proj_timing", "cimmino_time_kernels", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -49,7 +49,7 @@ class OptsStruct(C.Structure):
                 ("pivot_ratio_min", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
                 ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32),
-                ("ruiz_sweeps", C.c_int32), ("stream", C.c_void_p)]
+                ("ruiz_sweeps", C.c_int32), ("time_proj", C.c_int32), ("stream", C.c_void_p)]
 
 
 class StatsStruct(C.Structure):
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_sweeps.argtypes = [vp, vp, i32, dbl, i32, vp, i32]
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
+        L.cimmino_proj_timing.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
                                             C.POINTER(dbl)]
         L.cimmino_sparsify_dense_columns.argtypes = [i64, vp, vp, vp, vp, vp, vp,
@@ -150,7 +151,7 @@ def _check(L, code: int, ctx=None):
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
           keep_aat=False, refine_relax=None, multi_rhs=None, ruiz_sweeps=None,
-          stream=None) -> OptsStruct:
+          time_proj=None, stream=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -174,6 +175,8 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
         o.refine_relax = int(bool(refine_relax))
     if ruiz_sweeps is not None:
         o.ruiz_sweeps = int(ruiz_sweeps)
+    if time_proj is not None:
+        o.time_proj = int(bool(time_proj))
     o.stream = stream
     return o
 
@@ -324,6 +327,14 @@ class Solver:
         ms = np.zeros(3)
         _check(self._L, self._L.cimmino_time_kernels(self._h, int(reps), ms.ctypes.data), self._h)
         return {"proj_ms": ms[0], "spmv_ms": ms[1], "spmv_t_ms": ms[2]}
+
+    def proj_timing(self):
+        """Live projection time of the last solve's CG iterations (opts time_proj=True):
+        (summed ms, launches)."""
+        ms = C.c_double(0.0)
+        n = C.c_int64(0)
+        _check(self._L, self._L.cimmino_proj_timing(self._h, C.byref(ms), C.byref(n)), self._h)
+        return ms.value, n.value
 
     def block_rows(self, b: int) -> int:
         m = C.c_int32(0)

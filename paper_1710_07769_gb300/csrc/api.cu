@@ -149,9 +149,15 @@ struct cimmino_ctx {
   cudaGraphExec_t graph = nullptr;
   int32_t graph_nrhs = 0, graph_iters = 0;
   IterArgs args{};
+  // opts.time_proj: events around the projection launches of one check interval, and the
+  // live projection time of the last solve
+  std::vector<cudaEvent_t> pev;
+  double proj_ms_total = 0.0;
+  int64_t proj_launches = -1;
 
   ~cimmino_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (cudaEvent_t e : pev) cudaEventDestroy(e);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
@@ -173,6 +179,7 @@ void opts_default(cimmino_opts *o) {
   o->multi_rhs = 1;
   o->refine_relax = 0;
   o->ruiz_sweeps = 0;
+  o->time_proj = 0;
   o->stream = nullptr;
 }
 
@@ -189,6 +196,7 @@ void check_opts(const cimmino_opts &o) {
     fail(CIMMINO_EINVAL, "opts.check_every not in [1,1024]");
   if (o.ruiz_sweeps < 0 || o.ruiz_sweeps > 100)
     fail(CIMMINO_EINVAL, "opts.ruiz_sweeps not in [0,100]");
+  if (o.time_proj != 0 && o.time_proj != 1) fail(CIMMINO_EINVAL, "opts.time_proj must be 0 or 1");
 }
 
 // ------------------------------------------------------------------ setup
@@ -821,9 +829,22 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   const int32_t nl = c->nsys * nrhs;
   std::vector<LaneState> hl(nl);
   int64_t launched = 0;
+  const bool timing = c->opts.time_proj != 0;
+  std::vector<double> iter_ms;  // live projection time per iteration (timing only)
+  bool timing_ok = timing;
+  if (timing && c->pev.size() != (size_t)2 * G) {
+    for (cudaEvent_t e : c->pev) cudaEventDestroy(e);
+    c->pev.assign((size_t)2 * G, nullptr);
+    for (auto &e : c->pev) CUDA_TRY(cudaEventCreate(&e));
+  }
+  auto ev = [&](int32_t i, int which) -> cudaEvent_t {
+    return timing ? c->pev[(size_t)2 * i + which] : nullptr;
+  };
   const int64_t limit = (int64_t)c->opts.max_iter + 2 * G + 2;
   for (;;) {
-    if (c->opts.use_graph) {
+    // timed solves launch eagerly: events recorded inside a captured graph are internal
+    // to it and cannot be timed
+    if (c->opts.use_graph && !timing) {
       if (!c->graph || c->graph_nrhs != nrhs || c->graph_iters != G) {
         if (c->graph) cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -839,12 +860,21 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
       }
       CUDA_TRY(cudaGraphLaunch(c->graph, s));
     } else {
-      for (int32_t i = 0; i < G; ++i) launch_iteration(a, s);
+      for (int32_t i = 0; i < G; ++i) launch_iteration(a, s, ev(i, 0), ev(i, 1));
       CUDA_TRY(cudaGetLastError());
     }
     launched += G;
     d2h(hl.data(), c->lane.p, nl, s);
     CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t i = 0; timing_ok && i < G; ++i) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, c->pev[(size_t)2 * i], c->pev[(size_t)2 * i + 1]) !=
+          cudaSuccess) {
+        cudaGetLastError();  // timing unavailable: report none, the solve goes on
+        timing_ok = false;
+      }
+      iter_ms.push_back(ms);
+    }
     bool running = false;
     for (const auto &L : hl) running |= (L.status == CIMMINO_RUNNING);
     if (!running) break;
@@ -854,6 +884,16 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   launch_final_stats(a, c->Fin.p, c->rowabs.p, c->stats4.p, s);
   // the CG iterate lives in the column-scaled space y = diag(cs) x
   if (a.cs) launch_unscale_cols(c->x.p, a.cs, c->N, nrhs, s);
+  // live projection time: the iterations in which some lane still ran its projection
+  c->proj_ms_total = 0.0;
+  c->proj_launches = -1;
+  if (timing_ok) {
+    int64_t nrun = 0;
+    for (const auto &L : hl) nrun = std::max<int64_t>(nrun, L.iters);
+    nrun = std::min<int64_t>(nrun, (int64_t)iter_ms.size());
+    for (int64_t t = 0; t < nrun; ++t) c->proj_ms_total += iter_ms[(size_t)t];
+    c->proj_launches = nrun;
+  }
   std::vector<double> h4((size_t)4 * c->hcta.size() * nrhs);
   d2h(h4.data(), c->stats4.p, h4.size(), s);
   int64_t rtot = 0;
@@ -1072,6 +1112,17 @@ int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double
   } catch (const Error &e) {
     return set_error(ctx, e);
   }
+}
+
+int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches) {
+  if (!ctx || !ms_total || !launches) return CIMMINO_EINVAL;
+  if (!ctx->opts.time_proj || ctx->proj_launches < 0) {
+    ctx->err = "no projection timing: set opts.time_proj = 1 and solve first";
+    return CIMMINO_EINVAL;
+  }
+  *ms_total = ctx->proj_ms_total;
+  *launches = ctx->proj_launches;
+  return CIMMINO_OK;
 }
 
 int cimmino_get_colscale(cimmino_ctx *ctx, double *cs) {

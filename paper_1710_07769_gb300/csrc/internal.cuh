@@ -317,7 +317,9 @@ void launch_spmv_plain(const IterArgs &a, const double *v, double *out, cudaStre
 void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s);
 void launch_spmv_t(const IterArgs &a, const double *y, double *out, cudaStream_t s);
 void launch_cg_init(const IterArgs &a, cudaStream_t s);
-void launch_iteration(const IterArgs &a, cudaStream_t s);
+// one CG iteration; e0 / e1 (may be null) are recorded around the projection launch
+void launch_iteration(const IterArgs &a, cudaStream_t s, cudaEvent_t e0 = nullptr,
+                      cudaEvent_t e1 = nullptr);
 // one sweep of Algorithm 1: x += omega * sum_i A_i^+ (f_i - A_i x) (4 launches)
 void launch_cim_sweep(const IterArgs &a, double omega, cudaStream_t s);
 void launch_final_stats(const IterArgs &a, const double *Fin, const double *rowabs, double *out,

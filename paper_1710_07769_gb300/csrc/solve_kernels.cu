@@ -722,10 +722,12 @@ void launch_cg_init(const IterArgs &a, cudaStream_t s) {
   k_cg_init<<<a.ncta, kThreads, 0, s>>>(a);
 }
 
-void launch_iteration(const IterArgs &a, cudaStream_t s) {
+void launch_iteration(const IterArgs &a, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   if (a.nrhs > 1) {
     k_spmv_res_mr<<<a.ncta, kThreads, 0, s>>>(a);
+    if (e0) cudaEventRecord(e0, s);
     launch_proj(a, a.u, a.y, 1, s);
+    if (e1) cudaEventRecord(e1, s);
     k_spmv_t_mr<<<a.ncta, kThreads, 0, s>>>(a);
     if (32 % a.nrhs == 0) {
       k_update_xr_fl<<<a.ncta, kThreads, 0, s>>>(a);
@@ -737,7 +739,9 @@ void launch_iteration(const IterArgs &a, cudaStream_t s) {
     return;
   }
   k_spmv_res<<<a.ncta, kThreads, 0, s>>>(a);
+  if (e0) cudaEventRecord(e0, s);
   launch_proj(a, a.u, a.y, 1, s);
+  if (e1) cudaEventRecord(e1, s);
   k_spmv_t<1><<<a.ncta, kThreads, 0, s>>>(a, a.y, a.psi);
   k_update_xr<<<a.ncta, kThreads, 0, s>>>(a);
   k_update_p<<<a.ncta, kThreads, 0, s>>>(a);

@@ -40,4 +40,4 @@ def test_opts_defaults_without_gpu():
     assert o.precision == g.FP64 and o.layout == g.SKYLINE
     assert o.max_iter == 10000 and o.refine_tol == 1e-12 and o.pivot_ratio_min == 1e-4
     assert o.multi_rhs == 1 and o.keep_aat == 0 and o.use_graph == 1 and o.refine_relax == 0
-    assert o.ruiz_sweeps == 0
+    assert o.ruiz_sweeps == 0 and o.time_proj == 0

@@ -427,3 +427,24 @@ def test_equilibrated_sweeps_match_oracle(sys_badly_scaled):
         X = s.sweeps(F[:2], 0.9, sweeps)
         for k in range(2):
             assert rel(X[k], o.cimmino_sweeps(F[k], 0.9, sweeps)) <= 1e-11, (sweeps, k)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_live_projection_timing(sys_small, precision):
+    """opts time_proj records CUDA events around every projection launch of the CG loop
+    (eager launches): the same iterates bit for bit as the graph-launched solve, and one
+    timed launch per iteration that produced the returned x."""
+    A, perm, f = sys_small
+    ref = g.Solver(A, RAGGED, perm=perm, precision=precision)
+    x0, st0, _ = ref.solve(f)
+    for use_graph in (True, False):
+        s = g.Solver(A, RAGGED, perm=perm, precision=precision, time_proj=True,
+                     use_graph=use_graph)
+        x, st, code = s.solve(f)
+        assert code == 0 and st[0]["iters"] == st0[0]["iters"]
+        assert np.array_equal(x, x0)
+        ms, n = s.proj_timing()
+        assert n == st[0]["iters"] and ms > 0.0
+        s.close()
+    with pytest.raises(g.CimminoError):
+        ref.proj_timing()
