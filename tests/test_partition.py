@@ -115,3 +115,23 @@ def test_partition_after_sparsifying_dense_columns():
     cut_gp = oracle.cutsize(*cos, part_of(perm, bp, A.n))
     contiguous = np.repeat(np.arange(K), A.n // K).astype(np.int32)
     assert cut_gp < oracle.cutsize(*cos, contiguous)
+
+
+def test_host_entry_points_reject_bad_input():
+    """The host-only entry points validate their CSR input and sizes (no GPU needed)."""
+    A = inputs.convdiff2d(8, 20.0)
+    bad_col = inputs.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.val.copy())
+    bad_col.col_idx[3] = A.n            # column out of range
+    with pytest.raises(g.CimminoError) as e:
+        g.sparsify_dense_columns(bad_col)
+    assert e.value.code == g.EINVAL
+    bad_rp = inputs.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.val.copy())
+    bad_rp.row_ptr[5] = bad_rp.row_ptr[6] + 1   # row pointers not monotone
+    with pytest.raises(g.CimminoError) as e:
+        g.sparsify_dense_columns(bad_rp)
+    assert e.value.code == g.EINVAL
+    C = oracle.aat_plain(A)
+    for K, cap in ((0, 8), (A.n + 1, 1), (4, A.n // 4 - 1)):   # K out of range, cap * K < n
+        with pytest.raises(g.CimminoError) as e:
+            g.partition_rip(A.n, C, K, cap=cap)
+        assert e.value.code == g.EINVAL
