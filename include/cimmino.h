@@ -319,6 +319,15 @@ int cimmino_time_kernels(cimmino_ctx *ctx, int32_t reps, double *ms);
  * Errors: EINVAL (NULL pointer, time_proj off, no solve yet). */
 int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches);
 
+/* Watchdog self-test (failure detection without a GPU fault): one device thread waits,
+ * with the same bounded try_wait loop as the projection ring, on an mbarrier that nothing
+ * completes.  After limit_us microseconds (or 2^20 polls) it gives up and sets bit 8 of
+ * the device error word, which is copied to *err_word.  Needs no context; runs on a
+ * stream of its own on the current device.
+ * Returns CIMMINO_ETIMEOUT when the wait gave up (the expected outcome), CIMMINO_OK if
+ * it did not, EINVAL (limit_us outside [1, 1e6], NULL err_word), ECUDA, ENOMEM. */
+int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word);
+
 /* Library build information (compile-time architecture, version). */
 const char *cimmino_version(void);
 

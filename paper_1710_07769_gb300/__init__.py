@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["FP64", "FP32_REFINE", "DENSE", "SKYLINE", "CimminoError", "Solver", "BatchSolver",
-           "aat", "partition_rip", "sparsify_dense_columns", "load", "lib_path", "EXPORTS"]
+           "aat", "partition_rip", "sparsify_dense_columns", "selftest_wait", "load", "lib_path", "EXPORTS"]
 
 FP64, FP32_REFINE = 0, 1
 DENSE, SKYLINE = 0, 1
@@ -35,7 +35,8 @@ EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimm
            "cimmino_get_aat", "cimmino_get_scaled", "cimmino_get_colscale", "cimmino_block_rows", "cimmino_get_factor",
            "cimmino_project", "cimmino_project_rhs", "cimmino_sweeps", "cimmino_aat",
            "cimmino_aat_noalloc",
-           "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_proj_timing", "cimmino_time_kernels", "cimmino_version"]
+           "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_proj_timing",
+           "cimmino_selftest_wait", "cimmino_time_kernels", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_aat.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp]
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
         L.cimmino_proj_timing.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
+        L.cimmino_selftest_wait.argtypes = [i32, C.POINTER(i32)]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
                                             C.POINTER(dbl)]
         L.cimmino_sparsify_dense_columns.argtypes = [i64, vp, vp, vp, vp, vp, vp,
@@ -424,6 +426,15 @@ def aat(A, stream=None):
     _check(L, L.cimmino_aat(C.byref(csr), stream, C.byref(nnz), rp.ctypes.data, ci.ctypes.data,
                             v.ctypes.data))
     return rp, ci[: nnz.value], v[: nnz.value]
+
+
+def selftest_wait(limit_us: int = 2000):
+    """Watchdog self-test: a device wait on a barrier nothing completes must give up after
+    limit_us.  Returns (status code, device error word); ETIMEOUT is the expected status."""
+    L = load()
+    word = C.c_int32(0)
+    code = L.cimmino_selftest_wait(int(limit_us), C.byref(word))
+    return code, word.value
 
 
 def sparsify_dense_columns(A):

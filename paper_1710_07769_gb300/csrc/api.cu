@@ -1114,6 +1114,36 @@ int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double
   }
 }
 
+int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word) {
+  if (limit_us < 1 || limit_us > 1000000 || !err_word) {
+    g_last_error = "limit_us must be in [1, 1e6] and err_word non-NULL";
+    return CIMMINO_EINVAL;
+  }
+  try {
+    DBuf<int32_t> err;
+    err.alloc(1);
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaError_t e = cudaMemsetAsync(err.p, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+      launch_wait_selftest((uint64_t)limit_us * 1000ull, err.p, s);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err_word, err.p, sizeof(int32_t), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    CUDA_TRY(e);
+    if (*err_word) {
+      g_last_error = "the self-test wait ran out of its budget (error word " +
+                     std::to_string(*err_word) + ")";
+      return CIMMINO_ETIMEOUT;
+    }
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(nullptr, e);
+  }
+}
+
 int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches) {
   if (!ctx || !ms_total || !launches) return CIMMINO_EINVAL;
   if (!ctx->opts.time_proj || ctx->proj_launches < 0) {

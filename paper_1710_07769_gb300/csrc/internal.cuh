@@ -307,6 +307,8 @@ __device__ __forceinline__ double inner_tol(const IterArgs &a, int check_lane, i
 
 int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_smem_attr(int bytes);
+// watchdog self-test: a bounded wait on an mbarrier nothing completes; sets bit 8 of *err
+void launch_wait_selftest(uint64_t limit_ns, int32_t *err, cudaStream_t s);
 // proj_mr.cu: groups of rg right-hand sides share every factor tile read
 int proj_mr_smem_bytes(int max_mp, int rg, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_mr_smem_attr(int rg, int bytes);

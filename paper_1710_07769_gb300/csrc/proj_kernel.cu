@@ -479,7 +479,32 @@ __global__ void __launch_bounds__(kProjThreads, 1)
   if (producer && (threadIdx.x & 31) == 0) ring_drain(R, t);
 }
 
+// Watchdog self-test: one thread waits, with the same try_wait loop as the projection
+// ring, on an mbarrier that nothing ever completes.  The wait must give up after
+// limit_ns and report it in the error word; the spin count is bounded too (2^20 polls), so
+// the kernel ends even if the global timer stood still.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const uint64_t t0 = global_ns();
+  bool done = false;
+  for (uint32_t i = 0; i < (1u << 20) && !done; ++i) {
+    done = mbar_try_wait(&bar, 0u);
+    if (global_ns() - t0 > limit_ns) break;
+  }
+  if (!done) atomicOr(err, 8);
+}
+
 }  // namespace
+
+void launch_wait_selftest(uint64_t limit_ns, int32_t *err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, err);
+}
 
 int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes) {
   return slots * slot_bytes + 8 * max_mp + 2 * wbytes * max_mp;

@@ -41,3 +41,10 @@ def test_opts_defaults_without_gpu():
     assert o.max_iter == 10000 and o.refine_tol == 1e-12 and o.pivot_ratio_min == 1e-4
     assert o.multi_rhs == 1 and o.keep_aat == 0 and o.use_graph == 1 and o.refine_relax == 0
     assert o.ruiz_sweeps == 0 and o.time_proj == 0
+
+
+def test_selftest_rejects_bad_limit_without_gpu():
+    """The watchdog self-test validates its arguments before any CUDA call."""
+    import paper_1710_07769_gb300 as g
+    assert g.selftest_wait(limit_us=0)[0] == g.EINVAL
+    assert g.selftest_wait(limit_us=2_000_000)[0] == g.EINVAL
