@@ -109,7 +109,8 @@ typedef struct cimmino_opts {
 
 /* Statistics of one right-hand side of one system. */
 typedef struct cimmino_stats {
-  int32_t status;             /* CIMMINO_OK, _ENOCONV or _EBREAKDOWN               */
+  int32_t status;             /* CIMMINO_OK, _ENOCONV, _EBREAKDOWN or _EINVAL (NaN  */
+                              /* or Inf in this right-hand side)                    */
   int32_t iters;              /* projection sums H p evaluated (xi excluded)       */
   double rel_res;             /* ||f - A x||_2 / ||f||_2 of the returned x          */
   double backward_err;        /* gamma of Eq. 3.1 for the returned x                */
@@ -164,7 +165,8 @@ int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
  *   tol        stop right-hand side k once ||f_k - A x_k||_2 <= tol * ||f_k||_2.
  *   stats      NULL or an array of nrhs entries.
  * Returns CIMMINO_OK when every right-hand side converged, else the first
- * failure (ENOCONV / EBREAKDOWN; X still holds the last iterates). */
+ * failure (ENOCONV / EBREAKDOWN; X still holds the last iterates; EINVAL for a
+ * right-hand side holding NaN or Inf, whose x stays 0). */
 int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, double tol,
                   double *X, int32_t on_device, cimmino_stats *stats);
 

@@ -261,7 +261,10 @@ class Solver:
         nrhs = Fm.shape[0]
         stats = (StatsStruct * nrhs)()
         st = L.cimmino_solve(self._h, _ptr(Fm), nrhs, self.n, float(tol), _ptr(X), int(dev), stats)
-        if st not in (OK, ENOCONV, EBREAKDOWN) or (raise_on_fail and st != OK):
+        # EINVAL from a lane (a non-finite right-hand side) comes back with the other lanes'
+        # solutions; EINVAL from the arguments leaves every lane's stats untouched and raises
+        lane_einval = st == EINVAL and any(q.status == EINVAL for q in stats)
+        if (st not in (OK, ENOCONV, EBREAKDOWN) and not lane_einval) or (raise_on_fail and st != OK):
             _check(L, st, self._h)
         two_d = F.dim() == 2 if dev else np.ndim(F) == 2
         out = X if two_d else X.reshape(self.n)
@@ -397,7 +400,8 @@ class BatchSolver:
         xarr = (C.c_void_p * nsys)(*[x.ctypes.data for x in Xh])
         stats = (StatsStruct * nsys)()
         st = self._L.cimmino_solve_batch(self._h, farr, float(tol), xarr, 0, stats)
-        if st not in (OK, ENOCONV, EBREAKDOWN):
+        lane_einval = st == EINVAL and any(q.status == EINVAL for q in stats)
+        if st not in (OK, ENOCONV, EBREAKDOWN) and not lane_einval:
             _check(self._L, st, self._h)
         return Xh, [s.as_dict() for s in stats], st
 

@@ -1056,7 +1056,8 @@ int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, d
     CUDA_TRY(cudaStreamSynchronize(s));
     if (ret != CIMMINO_OK)
       ctx->err = ret == CIMMINO_ENOCONV ? "max_iter reached before convergence"
-                                        : "CG breakdown (p^T H p <= 0 or not finite)";
+                 : ret == CIMMINO_EINVAL  ? "a right-hand side holds NaN or Inf"
+                                          : "CG breakdown (p^T H p <= 0 or not finite)";
     return ret;
   } catch (const Error &e) {
     return set_error(ctx, e);

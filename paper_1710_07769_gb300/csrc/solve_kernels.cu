@@ -87,7 +87,10 @@ __global__ void __launch_bounds__(kThreads)
           L.t = 0;
           L.iters = 0;
           L.relres = f2 > 0.0 ? 1.0 : 0.0;
-          L.status = f2 > 0.0 ? CIMMINO_RUNNING : CIMMINO_CONVERGED;
+          // a NaN or Inf right-hand side is an input error of that lane, not a zero one
+          L.status = !isfinite(f2) ? CIMMINO_EINVAL
+                     : f2 > 0.0    ? CIMMINO_RUNNING
+                                   : CIMMINO_CONVERGED;
         }
       }
   }

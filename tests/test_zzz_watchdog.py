@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: a device-side wait that nothing completes gives
 up after its budget, the host reads CIMMINO_ETIMEOUT with the device error word, and the
-CUDA context stays usable (a solve afterwards still matches the oracle).  Collected last."""
+CUDA context stays usable (a solve afterwards still matches the oracle); a non-finite
+right-hand side is reported as an input error.  Collected last."""
 import time
 
 import numpy as np
@@ -27,3 +28,17 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert code == 0 and abs(st[0]["iters"] - ito) <= 1
     assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
 
+
+
+def test_nonfinite_rhs_is_an_input_error():
+    """A right-hand side holding NaN (or Inf) stops its lane with EINVAL instead of being
+    taken for a zero vector; the other lanes of the same solve are unaffected."""
+    w = inputs.workload(1)
+    s = g.Solver(w.A, w.block_ptr)
+    F = np.stack([w.F[0], w.F[0].copy(), w.F[0]])
+    F[1, 17] = np.nan
+    X, st, code = s.solve(F, tol=1e-10)
+    assert code == g.EINVAL
+    assert st[1]["status"] == g.EINVAL and not X[1].any()
+    for k in (0, 2):
+        assert st[k]["status"] == 0 and st[k]["rel_res"] <= 1e-10
