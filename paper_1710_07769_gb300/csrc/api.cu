@@ -9,6 +9,7 @@
 // sequence of five kernels, captured in a CUDA graph of check_every iterations;
 // the host reads one status word per right-hand side between graph launches.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -199,11 +200,26 @@ void check_opts(const cimmino_opts &o) {
   if (o.time_proj != 0 && o.time_proj != 1) fail(CIMMINO_EINVAL, "opts.time_proj must be 0 or 1");
 }
 
+// One NVTX range per stage (header-only NVTX 3: a no-op unless a profiler attaches), so
+// that a trace, or an ncu capture filtered with --nvtx, can select a stage.
+class Stages {
+ public:
+  explicit Stages(const char *first) { nvtxRangePushA(first); }
+  void next(const char *name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  ~Stages() { nvtxRangePop(); }
+  Stages(const Stages &) = delete;
+  Stages &operator=(const Stages &) = delete;
+};
+
 // ------------------------------------------------------------------ setup
 void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_t *K,
                 const int32_t *const *perms, const int64_t *const *bps) {
   cudaStream_t s = c->stream;
   c->nsys = nsys;
+  Stages stage("cimmino.setup.validate");
   // ---- host-side validation and global layout
   int64_t N = 0, NNZ = 0;
   c->hsys.resize(nsys);
@@ -320,6 +336,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                        : "column indices not strictly increasing within a row";
     fail(CIMMINO_EINVAL, "malformed CSR: " + why);
   }
+  stage.next("cimmino.setup.scale");
   // ---- row and column equilibration (Section 3.1), in place on our own copy of A's values
   DBuf<double> rs;
   if (c->opts.ruiz_sweeps > 0) {
@@ -399,6 +416,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   v0.release();
   rs.release();
 
+  stage.next("cimmino.setup.aat");
   // ---- C = A A^T (Section 2.3)
   DBuf<int64_t> cntc;
   DBuf<int32_t> ovf;
@@ -497,6 +515,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   c->factor_bytes = off * (fp64 ? 8 : 4);
   c->t_setup_ms = tsetup.stop_ms(s);
 
+  stage.next("cimmino.setup.factor");
   // ---- batched Cholesky of all G_i
   Timer tfac;
   tfac.start(s);
@@ -626,6 +645,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->ccv.release();
     c->have_aat = false;
   }
+  stage.next("cimmino.setup.tables");
   // ---- vector-kernel CTA table (kVecRows rows per CTA, never straddling systems) and
   // the 32-row slices of the sliced-ELL copies of A and A^T
   std::vector<int64_t> hsrow0;
@@ -813,6 +833,7 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   cudaStream_t s = c->stream;
   IterArgs &a = c->args;
   a.tol = tol;
+  Stages stage("cimmino.solve.xi");
   Timer tsolve;
   tsolve.start(s);
   CUDA_TRY(cudaMemsetAsync(c->cnt.p, 0, sizeof(int32_t) * 4 * c->nsys, s));
@@ -825,6 +846,7 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   launch_spmv_t(a, c->y.p, c->psi.p, s);
   launch_cg_init(a, s);
   CUDA_TRY(cudaGetLastError());
+  stage.next("cimmino.solve.cg");
   const int32_t G = c->opts.check_every;
   const int32_t nl = c->nsys * nrhs;
   std::vector<LaneState> hl(nl);
@@ -880,6 +902,7 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
     if (!running) break;
     if (launched > limit) fail(CIMMINO_ETIMEOUT, "CG lanes still running past max_iter");
   }
+  stage.next("cimmino.solve.stats");
   // backward error gamma (Eq. 3.1) per lane
   launch_final_stats(a, c->Fin.p, c->rowabs.p, c->stats4.p, s);
   // the CG iterate lives in the column-scaled space y = diag(cs) x
