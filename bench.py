@@ -33,7 +33,7 @@ METRIC = "time to 1e-10 rel. residual & HBM GB/s per CG iter; FP32+refine vs FP6
 TOL = 1e-10
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (recipe table); the FMA probe measured 1.196
 # DRAM bytes per k_proj launch from one ncu capture of the current kernel (ncu
-# --set full, 64^3 workload, CG iteration 1; profiles/k_proj_convdiff3d_64.md)
+# --set full, 64^3 workload, CG iteration 1)
 PROJ_TRAFFIC = {"fp64": 659753728, "fp32": 726496512}
 
 

@@ -109,8 +109,9 @@ typedef struct cimmino_opts {
 
 /* Statistics of one right-hand side of one system. */
 typedef struct cimmino_stats {
-  int32_t status;             /* CIMMINO_OK, _ENOCONV, _EBREAKDOWN or _EINVAL (NaN  */
-                              /* or Inf in this right-hand side)                    */
+  int32_t status;             /* CIMMINO_OK, _ENOCONV, _EBREAKDOWN, _EINVAL (NaN or */
+                              /* Inf in this right-hand side) or _EUNSUPPORTED (its */
+                              /* squared 2-norm overflows FP64: entries > ~1e154)   */
   int32_t iters;              /* projection sums H p evaluated (xi excluded)       */
   double rel_res;             /* ||f - A x||_2 / ||f||_2 of the returned x          */
   double backward_err;        /* gamma of Eq. 3.1 for the returned x                */
@@ -166,7 +167,8 @@ int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
  *   stats      NULL or an array of nrhs entries.
  * Returns CIMMINO_OK when every right-hand side converged, else the first
  * failure (ENOCONV / EBREAKDOWN; X still holds the last iterates; EINVAL for a
- * right-hand side holding NaN or Inf, whose x stays 0). */
+ * right-hand side holding NaN or Inf and EUNSUPPORTED for one whose squared 2-norm
+ * overflows FP64, whose x stays 0; the other right-hand sides are still solved). */
 int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, double tol,
                   double *X, int32_t on_device, cimmino_stats *stats);
 
@@ -233,11 +235,13 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
                 int32_t *col_idx, double *val);
 
 /* C = A A^T into caller-owned DEVICE buffers without allocating any device memory.
- * The paper has no counterpart: this exists for callers that cannot allocate, such
- * as code running while a stream is captured into a CUDA graph (cudaMalloc is not
- * allowed there), embedders whose device memory belongs to another allocator or a
- * fixed budget, and latency-critical paths that must not block on the allocator.
- * It computes the same result as cimmino_aat() (same kernels, bitwise equal).
+ * The paper has no counterpart.  Some callers cannot let a library allocate: an
+ * embedder whose device memory is all reserved by its own allocator (a framework's
+ * caching pool) or capped by a fixed budget would see cudaMalloc fail or exceed that
+ * budget, and a latency-bound loop cannot afford cudaMalloc / cudaFree, which may block
+ * the host and synchronise the device.  For them this computes the same result as
+ * cimmino_aat() (same kernels, bitwise equal) with the working memory taken from a
+ * fixed static array instead.
  *   A         device CSR (A->on_device must be 1), n <= 262,144 and nnz <= 2,097,152,
  *             else CIMMINO_EUNSUPPORTED.
  *   stream    cudaStream_t for the work (NULL: legacy default stream).
@@ -249,11 +253,14 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
  * static device array of about 33 MB that every GPU loading this library keeps until
  * the process exits.  No cudaMalloc / cudaFree or allocating library call is made.
  * The first call on each device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All calls share
- * the array, so calls whose work overlaps on the GPU (other threads, other streams)
- * race and must be serialised by the caller; each call clears what must start at
- * zero.  The call synchronises `stream` before returning; the error message is
- * available from cimmino_last_error(NULL). */
+ * device current) and caches it for the life of the process, so the entry point must
+ * not be used on a device after cudaDeviceReset() (or any other re-creation of its
+ * primary context) in the same process.  All calls share the array, which keeps the
+ * last call's contents: each call clears what must start at zero, and calls whose
+ * work overlaps on the GPU (other host threads, other streams) race on the array and
+ * must be serialised by the caller.  The call is host-synchronous: it synchronises
+ * `stream` between its stages (to read counts back to the host) and before it
+ * returns.  The error message is available from cimmino_last_error(NULL). */
 int cimmino_aat_noalloc(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_ptr,
                         int32_t *col_idx, double *val, int64_t capacity);
 

@@ -261,9 +261,10 @@ class Solver:
         nrhs = Fm.shape[0]
         stats = (StatsStruct * nrhs)()
         st = L.cimmino_solve(self._h, _ptr(Fm), nrhs, self.n, float(tol), _ptr(X), int(dev), stats)
-        # EINVAL from a lane (a non-finite right-hand side) comes back with the other lanes'
-        # solutions; EINVAL from the arguments leaves every lane's stats untouched and raises
-        lane_einval = st == EINVAL and any(q.status == EINVAL for q in stats)
+        # EINVAL / EUNSUPPORTED from a lane (a non-finite right-hand side, or one whose squared
+        # norm overflows) comes back with the other lanes' solutions; the same codes from the
+        # arguments leave every lane's stats untouched and raise
+        lane_einval = st in (EINVAL, EUNSUPPORTED) and any(q.status == st for q in stats)
         if (st not in (OK, ENOCONV, EBREAKDOWN) and not lane_einval) or (raise_on_fail and st != OK):
             _check(L, st, self._h)
         two_d = F.dim() == 2 if dev else np.ndim(F) == 2
@@ -400,7 +401,7 @@ class BatchSolver:
         xarr = (C.c_void_p * nsys)(*[x.ctypes.data for x in Xh])
         stats = (StatsStruct * nsys)()
         st = self._L.cimmino_solve_batch(self._h, farr, float(tol), xarr, 0, stats)
-        lane_einval = st == EINVAL and any(q.status == EINVAL for q in stats)
+        lane_einval = st in (EINVAL, EUNSUPPORTED) and any(q.status == st for q in stats)
         if st not in (OK, ENOCONV, EBREAKDOWN) and not lane_einval:
             _check(self._L, st, self._h)
         return Xh, [s.as_dict() for s in stats], st

@@ -970,6 +970,21 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
   return ret;
 }
 
+// Message of the first failing right-hand side (its status code) of a solve.
+const char *lane_failure_message(int code) {
+  switch (code) {
+    case CIMMINO_ENOCONV:
+      return "max_iter reached before convergence";
+    case CIMMINO_EINVAL:
+      return "a right-hand side holds NaN or Inf";
+    case CIMMINO_EUNSUPPORTED:
+      return "the squared 2-norm of a right-hand side overflows FP64 (entries above about "
+             "1e154)";
+    default:
+      return "CG breakdown (p^T H p <= 0 or not finite)";
+  }
+}
+
 int set_error(cimmino_ctx *c, const Error &e) {
   if (c)
     c->err = e.msg;
@@ -1077,10 +1092,7 @@ int cimmino_solve(cimmino_ctx *ctx, const double *F, int32_t nrhs, int64_t ld, d
                                  N * sizeof(double), nrhs, cudaMemcpyDefault, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (ret != CIMMINO_OK)
-      ctx->err = ret == CIMMINO_ENOCONV ? "max_iter reached before convergence"
-                 : ret == CIMMINO_EINVAL  ? "a right-hand side holds NaN or Inf"
-                                          : "CG breakdown (p^T H p <= 0 or not finite)";
+    if (ret != CIMMINO_OK) ctx->err = lane_failure_message(ret);
     return ret;
   } catch (const Error &e) {
     return set_error(ctx, e);
@@ -1104,6 +1116,7 @@ int cimmino_solve_batch(cimmino_ctx *ctx, const double *const *F, double tol, do
     for (int32_t q = 0; q < ctx->nsys; ++q)
       d2h(X[q], ctx->x.p + ctx->hsys[q].row0, ctx->hsys[q].n, s);
     CUDA_TRY(cudaStreamSynchronize(s));
+    if (ret != CIMMINO_OK) ctx->err = lane_failure_message(ret);
     return ret;
   } catch (const Error &e) {
     return set_error(ctx, e);

@@ -1,11 +1,12 @@
 // cimmino_aat_noalloc: C = A A^T into caller device buffers without any device
-// allocation.  Callers that cannot allocate device memory -- code running while a
-// stream is being captured into a CUDA graph (where cudaMalloc is not permitted),
-// embedders whose device memory is owned by another allocator or fixed budget, or
-// real-time paths that must not block on the allocator -- can still build the row
-// inner-product graph.  The working arrays of the SpGEMM (transpose of A, row
-// counts, scan partials, overflow list) live in one file-scope device array of a
-// fixed size, which every GPU that loads this library holds until the process exits.
+// allocation.  Some callers cannot let a library allocate device memory: an embedder
+// whose device memory is reserved by its own caching allocator or capped by a fixed
+// budget, or a latency-bound loop that cannot afford cudaMalloc / cudaFree (which may
+// block the host and synchronise the device).  They can still build the row
+// inner-product graph here.  The working arrays of the SpGEMM (transpose of A, row
+// counts, scan partials, overflow list) live in one file-scope device array of a fixed
+// size, which every GPU that loads this library holds until the process exits.  The call
+// is host-synchronous: it reads counts back between its stages.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,7 +48,9 @@ unsigned char *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The host-side symbol
 // is only a stand-in, so the address is looked up once per device (with that device
-// current) and cached.
+// current) and cached for the life of the process; a cudaDeviceReset() would reload the
+// module at a possibly different address, so the entry point is documented as unusable
+// on a device after a reset.
 unsigned char *scratch_on_current_device() {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));

@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(kThreads)
     double f2 = 0.0;
     if (act) {
       double fo = Fin[(int64_t)k * a.N + r];  // original order row r (same system range)
-      f2 = fo * fo;
+      // a non-finite entry makes the sum NaN (squares of finite entries never do: at worst
+      // they overflow to +Inf), so the two failures stay apart after the reduction
+      f2 = isfinite(fo) ? fo * fo : __longlong_as_double(0x7ff8000000000000ll);
       a.fs[r * a.nrhs + k] = Fin[(int64_t)k * a.N + perm[r]] / a.d[r];
     }
     double s = block_sum(f2, red);
@@ -87,10 +89,13 @@ __global__ void __launch_bounds__(kThreads)
           L.t = 0;
           L.iters = 0;
           L.relres = f2 > 0.0 ? 1.0 : 0.0;
-          // a NaN or Inf right-hand side is an input error of that lane, not a zero one
-          L.status = !isfinite(f2) ? CIMMINO_EINVAL
-                     : f2 > 0.0    ? CIMMINO_RUNNING
-                                   : CIMMINO_CONVERGED;
+          // a NaN or Inf entry is an input error of that lane, not a zero right-hand side;
+          // finite entries whose squared norm overflows FP64 (above about 1e154) are beyond
+          // the solver's range
+          L.status = isnan(f2)   ? CIMMINO_EINVAL
+                     : isinf(f2) ? CIMMINO_EUNSUPPORTED
+                     : f2 > 0.0  ? CIMMINO_RUNNING
+                                 : CIMMINO_CONVERGED;
         }
       }
   }

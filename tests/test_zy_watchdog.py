@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: a device-side wait that nothing completes gives
 up after its budget, the host reads CIMMINO_ETIMEOUT with the device error word, and the
 CUDA context stays usable (a solve afterwards still matches the oracle); a non-finite
-right-hand side is reported as an input error.  Collected last."""
+right-hand side is reported as an input error, and one whose squared norm overflows FP64 as
+beyond the solver's range."""
 import time
 
 import numpy as np
@@ -40,5 +41,20 @@ def test_nonfinite_rhs_is_an_input_error():
     X, st, code = s.solve(F, tol=1e-10)
     assert code == g.EINVAL
     assert st[1]["status"] == g.EINVAL and not X[1].any()
+    for k in (0, 2):
+        assert st[k]["status"] == 0 and st[k]["rel_res"] <= 1e-10
+
+
+def test_overflowing_rhs_norm_is_reported_as_such():
+    """Finite entries of 1e160 overflow ||f||^2 in FP64: that lane stops with EUNSUPPORTED and
+    a message naming the overflow (not NaN / Inf), while the other lanes still converge."""
+    w = inputs.workload(1)
+    s = g.Solver(w.A, w.block_ptr)
+    F = np.stack([w.F[0], 1e160 * w.F[0], w.F[0]])
+    X, st, code = s.solve(F, tol=1e-10)
+    assert code == g.EUNSUPPORTED
+    assert st[1]["status"] == g.EUNSUPPORTED and not X[1].any()
+    msg = s._L.cimmino_last_error(s._h).decode()
+    assert "overflows" in msg and "NaN" not in msg, msg
     for k in (0, 2):
         assert st[k]["status"] == 0 and st[k]["rel_res"] <= 1e-10
