@@ -1,27 +1,35 @@
-"""Benchmark: time to a 1e-10 relative residual of the CG-accelerated block Cimmino
-solve (setup + solve) and HBM GB/s per CG iteration, FP64 vs FP32+refinement, on
-one GB300.
+"""Benchmark: time to a 1e-10 relative residual of the CG-accelerated block Cimmino solve
+(setup + solve) and HBM GB/s per CG iteration, FP64 vs FP32+refinement, on one GB300.
 
-Workload (default): 3D convection-diffusion 64^3 (n = 262,144), 7-point upwind
-stencil, b = (30, 20, 10), K = 128 contiguous blocks of 2048 rows, f = A x_true,
-x_true ~ U[-1, 1] (seed 2).  A step = one full pass of the hot path: row scaling +
-permutation, A^T, C = A A^T, Gram blocks, batched Cholesky, then Algorithm 2 to
-||f - A x|| <= 1e-10 ||f||, with A and f already resident in HBM.
+Workload (default, --config 3): a random sparse nonsymmetric system, n = 2^20, 8
+off-diagonal entries per row at uniform columns with N(0,1) values, diagonal = 1.2 x the
+row's absolute sum (seed 3), f = A x_true with x_true ~ U[-1, 1]; K = 512 blocks of
+exactly 2048 rows from the graph partition of the row inner-product graph (Section 2),
+computed once before the timed region.  A step = one full pass of the hot path: row
+scaling + permutation, A^T, C = A A^T, Gram blocks, batched Cholesky, then Algorithm 2 to
+||f - A x|| <= 1e-10 ||f||, with A and f already resident in HBM.  `value` is the FP64
+time to solution; FP32 factors + FP64 refinement are timed beside it on the same blocks.
+
+Further legs (each timed with CUDA events, clocks sampled): contiguous blocks of the same
+workload, the 64^3 convection-diffusion system against the stored oracle solution, and the
+128^3 system with 16 right-hand sides (one full FP32+refine solve, FP64 per iteration over
+a fixed window).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank solves its own copy of the workload (replicas
-only: the solve does not shard); rank 0 prints the JSON line.
+Under torchrun (N > 1) every rank solves its own copy of the workload (replicas only: the
+solve does not shard); rank 0 prints the JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
-import tempfile
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -31,10 +39,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 rel. residual & HBM GB/s per CG iter; FP32+refine vs FP64 on GB300"
 TOL = 1e-10
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (recipe table); the FMA probe measured 1.196
-# DRAM bytes per k_proj launch from one ncu capture of the current kernel (ncu
-# --set full, 64^3 workload, CG iteration 1)
-PROJ_TRAFFIC = {"fp64": 659753728, "fp32": 726496512}
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (nominal, 152 SMs at 2070 MHz)
+# DRAM bytes per launch from one ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum); None where the kernel changed since its capture
+TRAFFIC = {"k_proj_fp64_convdiff3d_64": 659753728, "k_proj_fp32_convdiff3d_64": 726496512}
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def peaks():
@@ -52,7 +61,7 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling (SM clock, throttle reasons) during the timed region."""
+    """nvidia-smi sampling (SM clock, throttle reasons) during a timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -60,11 +69,11 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.p = None
-        self.path = os.path.join(tempfile.gettempdir(), f"cimmino_clocks_{os.getpid()}_{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(),
+                                 f"cimmino_clocks_{os.getpid()}_{index}_{id(self)}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -94,11 +103,12 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "power_w_median": statistics.median(pw) if pw else None, "samples": len(rows)}
 
 
 def max_over_ranks(value, device=None):
@@ -113,24 +123,251 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
-def algorithmic_bytes(n, nnz, factor_bytes, w_factor, refine_mean, nnz_bd):
+def algorithmic_bytes(n, nnz, factor_bytes, refine_mean, nnz_gram):
     """Minimum bytes one CG iteration must move (1 right-hand side).
 
-    projection: one solve pass streams pass_bytes = 2 x factor_bytes (N tiles and
-      inv(L_II) for the forward solve, their transposed copies for the backward
-      solve), times (1 + refinement steps); each refinement step also reads the
-      exact Gram block (12 B per entry); u read, y written.
-    u = A p with the residual of x: CSR (12 B/entry + 8 B/row), p and x gathered,
-      f_s and d read, u written.
-    psi = A^T y with p^T psi: transpose (12 B/entry + 8 B/column), y gathered,
-      p read, psi written.
+    projection: one solve pass streams pass_bytes ~ 2 x factor_bytes (N tiles and
+      inv(L_II) for the forward solve, their transposed copies for the backward solve),
+      times (1 + refinement steps); each refinement step also reads the exact Gram blocks
+      (12 B per entry); u read, y written.
+    u = A p with the residual of x: CSR (12 B/entry + 8 B/row), p and x gathered, f_s and d
+      read, u written.
+    psi = A^T y with p^T psi: transpose (12 B/entry + 8 B/column), y gathered, p read, psi
+      written.
     x, r update (4 read, 2 written) and p update (2 read, 1 written).
     """
-    proj = (1 + refine_mean) * 2 * factor_bytes + refine_mean * 12 * nnz_bd + 16 * n
+    proj = (1 + refine_mean) * 2 * factor_bytes + refine_mean * 12 * nnz_gram + 16 * n
     spmv = 12 * nnz + 8 * n + 16 * n + 16 * n + 8 * n
     spmv_t = 12 * nnz + 8 * n + 8 * n + 8 * n + 8 * n
     upd = 6 * 8 * n + 3 * 8 * n
     return {"proj": proj, "iteration": proj + spmv + spmv_t + upd}
+
+
+# ------------------------------------------------------------------ workloads and partitions
+
+DEFAULT_PARTITION = {1: "contiguous", 2: "contiguous", 3: "graph", 5: "contiguous"}
+
+
+EXACT_BALANCE = (3, 5)  # blocks of exactly 2048 rows; the 64^3 system allows 5% imbalance
+
+
+def partition_of(w, partition, config, use_gpu=True):
+    """Blocks of the workload: its contiguous blocks, or the graph partition of its row
+    inner-product graph (Section 2) with the same K.  Caps: exact balance (n / K rows) for
+    the random and 128^3 workloads, 5% imbalance otherwise."""
+    import paper_1710_07769_gb300 as g
+    K = len(w.block_ptr) - 1
+    n = w.A.n
+    if partition == "contiguous":
+        return w.perm, w.block_ptr, {"partition": "contiguous", "cap": int(np.diff(w.block_ptr).max())}
+    cap = n // K if config in EXACT_BALANCE and n % K == 0 else int(math.floor(1.05 * n / K))
+    t0 = time.perf_counter()
+    if use_gpu:
+        C = g.aat(w.A)
+    else:
+        import oracle
+        C = oracle.aat_plain(w.A)
+    t_aat = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    perm, bp, cut = g.partition_rip(n, C, K, cap=cap, seed=0)
+    t_part = time.perf_counter() - t0
+    return perm, bp, {"partition": "graph", "cap": cap, "aat_s": round(t_aat, 3),
+                      "partition_s": round(t_part, 2), "cutsize": round(cut, 2),
+                      "block_rows_min": int(np.diff(bp).min()),
+                      "block_rows_max": int(np.diff(bp).max())}
+
+
+def config_dict(w, part, layout, args):
+    return {"workload": w.name, "n": int(w.A.n), "nnz": int(w.A.nnz),
+            "K": int(len(w.block_ptr) - 1), "partition": part["partition"], "cap": part["cap"],
+            "layout": layout, "tol": TOL, "precision": "fp64 (value); fp32_refine beside",
+            "x0": "zero", "l2": "flushed (512 MB write) before every timed step",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+# ------------------------------------------------------------------ our arm
+
+class DevCSR:
+    pass
+
+
+def to_device(A, dev):
+    import torch
+    d = DevCSR()
+    d.n = A.n
+    d.row_ptr = torch.from_numpy(A.row_ptr).to(dev)
+    d.col_idx = torch.from_numpy(A.col_idx).to(dev)
+    d.val = torch.from_numpy(A.val).to(dev)
+    return d
+
+
+class Runner:
+    """Timed steps of one workload and partition on the library's stream."""
+
+    def __init__(self, w, perm, bp, layout, dev, stream, flush):
+        import torch
+        self.w, self.perm, self.bp, self.layout = w, perm, bp, layout
+        self.dev, self.stream, self.flush = dev, stream, flush
+        self.dA = to_device(w.A, dev)
+        self.dF = torch.from_numpy(np.ascontiguousarray(w.F[0])).to(dev)
+        self.dX = torch.empty_like(self.dF)
+        torch.cuda.synchronize()
+
+    def step(self, precision, **kw):
+        import torch
+
+        import paper_1710_07769_gb300 as g
+        with torch.cuda.stream(self.stream):
+            s = g.Solver(self.dA, self.bp, perm=self.perm, precision=precision,
+                         layout=self.layout, **kw)
+            x, st, code = s.solve(self.dF, tol=TOL, X=self.dX)
+        return s, st[0], code
+
+    def timed(self, precision, k, warm, **kw):
+        """warm untimed steps, then k steps each bracketed by CUDA events on the stream (L2
+        flushed by a 512 MB write before each).  Returns (ms list, last (solver, stats, code))."""
+        import torch
+        for _ in range(warm):
+            s, st, code = self.step(precision, **kw)
+            s.close()
+        times, last = [], None
+        for _ in range(k):
+            with torch.cuda.stream(self.stream):
+                self.flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+            s, st, code = self.step(precision, **kw)
+            with torch.cuda.stream(self.stream):
+                e1.record(self.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if last is not None:
+                last[0].close()
+            last = (s, st, code)
+        return times, last
+
+    def x_host(self):
+        import torch
+        torch.cuda.synchronize()
+        return self.dX.cpu().numpy().copy()
+
+    def proj_live(self, precision):
+        """Average device time of the projection launches inside the CG loop of one more
+        solve (CUDA events on the library's stream around every projection launch,
+        iterations launched eagerly), and the isolated back-to-back figure beside it."""
+        s, st, code = self.step(precision, time_proj=True)
+        ms, nl = s.proj_timing()
+        kt = s.time_kernels(reps=10)
+        s.close()
+        kt["proj_ms_isolated"] = kt["proj_ms"]
+        kt["proj_ms"] = ms / max(1, nl)
+        kt["proj_launches_timed"] = nl
+        return kt
+
+
+def rel_err(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def leg_summary(r, st, times, kt, x, n, nnz, nblk):
+    launches = st["iters"] + 1
+    refine_mean = st["refine_steps_total"] / max(1, nblk * (launches + 1))
+    b = algorithmic_bytes(n, nnz, st["pass_bytes"] / 2, refine_mean, st["nnz_gram"])
+    it_ms = st["t_solve_ms"] / max(1, launches)
+    out = {"time_to_solution_ms": round(sum(times) / len(times), 3), "steps": len(times),
+           "iters": st["iters"], "rel_res": st["rel_res"], "backward_err": st["backward_err"],
+           "setup_ms": round(st["t_setup_ms"], 3), "factor_ms": round(st["t_factor_ms"], 3),
+           "cholesky_ms": round(st["t_chol_ms"], 3), "solve_ms": round(st["t_solve_ms"], 3),
+           "per_iter_ms": round(it_ms, 4),
+           "hbm_gbps_per_iter": round(b["iteration"] / (it_ms * 1e-3) / 1e9, 1),
+           "refine_steps_mean": round(refine_mean, 4), "fallbacks": st["fallbacks"],
+           "factor_bytes": st["factor_bytes"], "pass_bytes": st["pass_bytes"],
+           "factor_gflop": round(st["factor_flops"] / 1e9, 3),
+           "cholesky_tflops": round(st["factor_flops"] / (st["t_chol_ms"] * 1e-3) / 1e12, 4),
+           "kernel_launches": st["kernel_launches"],
+           "x_err_vs_true": rel_err(x, r.w.x_true[0])}
+    if kt is not None:
+        out.update({"proj_ms": round(kt["proj_ms"], 5),
+                    "proj_ms_isolated": round(kt["proj_ms_isolated"], 5),
+                    "proj_launches_timed": kt["proj_launches_timed"],
+                    "proj_bytes": round(b["proj"]),
+                    "proj_gbps": round(b["proj"] / (kt["proj_ms"] * 1e-3) / 1e9, 1)})
+    return out
+
+
+def leg_config2(dev, stream, flush, layout, local):
+    """The 64^3 convection-diffusion system, contiguous blocks: one warm-up and two timed
+    solves per precision; x against the stored oracle solution (tests/golden, written from
+    the oracle only) at its sample rows."""
+    import inputs
+    w = inputs.workload(2)
+    gold = json.load(open(os.path.join(GOLDEN, "config2_oracle.json")))
+    r = Runner(w, w.perm, w.block_ptr, layout, dev, stream, flush)
+    out = {"workload": w.name, "partition": "contiguous", "oracle_iters": gold["iters"]}
+    with Clocks(local) as ck:
+        for precision in ("fp64", "fp32_refine"):
+            times, (s, st, code) = r.timed(precision, 2, 1)
+            x = r.x_host()
+            s.close()
+            idx = np.asarray(gold["x_sample_idx"])
+            d = leg_summary(r, st, times, None, x, w.A.n, w.A.nnz, len(w.block_ptr) - 1)
+            d["status"] = code
+            d["x_err_vs_oracle_max"] = float(np.abs(x[idx] - np.asarray(gold["x_sample"])).max()
+                                             / gold["x_max_abs"])
+            out[precision] = d
+    out["clocks"] = ck.summary()
+    return out
+
+
+def leg_config5(dev, stream, flush, layout, local, window=64):
+    """The 128^3 system with 16 right-hand sides sharing the factors (contiguous blocks of
+    2048 rows): one full FP32+refine solve of all 16 lanes, and FP64 per CG iteration over a
+    fixed window of `window` iterations (its full solve would take minutes)."""
+    import torch
+
+    import inputs
+    import paper_1710_07769_gb300 as g
+    w = inputs.workload(5)
+    dA = to_device(w.A, dev)
+    dF = torch.from_numpy(np.ascontiguousarray(w.F)).to(dev)
+    dX = torch.empty_like(dF)
+    torch.cuda.synchronize()
+    out = {"workload": w.name, "partition": "contiguous", "nrhs": int(w.F.shape[0])}
+    with Clocks(local) as ck:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision="fp32_refine", layout=layout)
+            X, st, code = s.solve(dF, tol=TOL, X=dX)
+            e1.record(stream)
+        e1.synchronize()
+        t32 = e0.elapsed_time(e1)
+        s.close()
+        Xh = dX.cpu().numpy()
+        its = [q["iters"] for q in st]
+        out["fp32_refine"] = {
+            "time_to_solution_ms": round(t32, 3), "status": code,
+            "iters_min": min(its), "iters_max": max(its),
+            "rel_res_max": max(q["rel_res"] for q in st),
+            "setup_ms": round(st[0]["t_setup_ms"], 3), "factor_ms": round(st[0]["t_factor_ms"], 3),
+            "solve_ms": round(st[0]["t_solve_ms"], 3),
+            "per_iter_ms": round(st[0]["t_solve_ms"] / (max(its) + 1), 4),
+            "x_err_vs_true_max": max(rel_err(Xh[k], w.x_true[k]) for k in range(len(its)))}
+        with torch.cuda.stream(stream):
+            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision="fp64", layout=layout,
+                         max_iter=window)
+            X, st, code = s.solve(dF, tol=TOL, X=dX)
+        s.close()
+        out["fp64_window"] = {"iters": window, "status": code,
+                              "setup_ms": round(st[0]["t_setup_ms"], 3),
+                              "factor_ms": round(st[0]["t_factor_ms"], 3),
+                              "per_iter_ms": round(st[0]["t_solve_ms"] / (window + 1), 4)}
+    out["clocks"] = ck.summary()
+    del dA, dF, dX
+    return out
 
 
 def run_ours(args, rank, local):
@@ -141,51 +378,13 @@ def run_ours(args, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = inputs.workload(args.config)
-    A = w.A
-    n = A.n
     stream = torch.cuda.Stream(device=dev)
-
-    class DevCSR:
-        pass
-
-    dA = DevCSR()
-    dA.n = n
-    dA.row_ptr = torch.from_numpy(A.row_ptr).to(dev)
-    dA.col_idx = torch.from_numpy(A.col_idx).to(dev)
-    dA.val = torch.from_numpy(A.val).to(dev)
-    dF = torch.from_numpy(w.F[0]).to(dev)
-    dX = torch.empty_like(dF)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-    torch.cuda.synchronize()
-
-    def step(precision, relax=False, time_proj=False):
-        with torch.cuda.stream(stream):
-            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision=precision, layout=args.layout,
-                         refine_relax=relax, time_proj=time_proj)
-            x, st, code = s.solve(dF, tol=TOL, X=dX)
-        return s, st[0], code
-
-    def timed(precision, k, w_, relax=False):
-        for _ in range(w_):
-            s, st, code = step(precision, relax)
-            s.close()
-        times, last = [], None
-        for _ in range(k):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            s, st, code = step(precision, relax)
-            with torch.cuda.stream(stream):
-                e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            if last is not None:
-                last[0].close()
-            last = (s, st, code)
-        return times, last
+    w = inputs.workload(args.config)
+    partition = args.partition or DEFAULT_PARTITION.get(args.config, "contiguous")
+    perm, bp, part = partition_of(w, partition, args.config)
+    nblk = len(bp) - 1
+    r = Runner(w, perm, bp, args.layout, dev, stream, flush)
 
     if args.gpus > 1:
         torch.distributed.barrier()
@@ -193,195 +392,257 @@ def run_ours(args, rank, local):
     clocks = Clocks(local)
     t_wall0 = time.time()
     with clocks:
-        t64, (s64, st64, code64) = timed("fp64", args.steps, args.warmup)
+        t64, (s64, st64, code64) = r.timed("fp64", args.steps, args.warmup)
     torch.cuda.synchronize()
     wall = time.time() - t_wall0
+    x64 = r.x_host()
     ms_step = sum(t64) / len(t64)
     if args.gpus > 1:
         ms_step = max_over_ranks(ms_step, dev)
         torch.distributed.barrier()
-    def proj_live(precision):
-        """Average device time of the projection launches inside the CG loop of one more
-        solve of the same workload (CUDA events on the library's stream around every
-        projection launch, iterations launched eagerly), and the isolated back-to-back
-        figure beside it."""
-        s, st, code = step(precision, time_proj=True)
-        ms, nl = s.proj_timing()
-        kt = s.time_kernels(reps=10)
-        s.close()
-        kt["proj_ms_isolated"] = kt["proj_ms"]
-        kt["proj_ms"] = ms / max(1, nl)
-        kt["proj_launches_timed"] = nl
-        return kt
-
-    kt64 = proj_live("fp64")
-    # FP32 + refinement on the same workload (fewer steps, same rules)
-    t32, (s32, st32, code32) = timed("fp32_refine", max(1, min(args.steps, 2)), 1)
-    kt32 = proj_live("fp32_refine")
+    s64.close()
+    kt64 = r.proj_live("fp64")
+    # FP32 + refinement on the same blocks (at least 3 timed steps, same rules)
+    clocks32 = Clocks(local)
+    with clocks32:
+        t32, (s32, st32, code32) = r.timed("fp32_refine", max(3, min(args.steps, 5)), 1)
+    x32 = r.x_host()
+    s32.close()
+    kt32 = r.proj_live("fp32_refine")
     # FP32 with the relaxed inner tolerance refine_tol / relres_t (an inexact-Krylov variant:
     # same stopping test, a few more iterations, fewer second factor passes)
-    tr, (sr, str_, coder) = timed("fp32_refine", max(1, min(args.steps, 2)), 1, relax=True)
-
+    tr, (sr, str_, coder) = r.timed("fp32_refine", 2, 1, refine_relax=True)
+    xr = r.x_host()
+    sr.close()
     if rank != 0:
-        s64.close()
-        s32.close()
-        sr.close()
-        return None
+        return None, (None, None, None)
+
+    r64 = leg_summary(r, st64, t64, kt64, x64, w.A.n, w.A.nnz, nblk)
+    r32 = leg_summary(r, st32, t32, kt32, x32, w.A.n, w.A.nnz, nblk)
+    r32["x_err_vs_fp64"] = rel_err(x32, x64)
+    r32["clocks"] = clocks32.summary()
+    rrx = {"time_to_solution_ms": round(sum(tr) / len(tr), 3), "iters": str_["iters"],
+           "rel_res": str_["rel_res"], "status": coder, "solve_ms": round(str_["t_solve_ms"], 3),
+           "refine_steps_total": str_["refine_steps_total"],
+           "inner_solves": nblk * (str_["iters"] + 1), "x_err_vs_true": rel_err(xr, w.x_true[0]),
+           "x_err_vs_fp64": rel_err(xr, x64)}
 
     # e2e: host CSR and host f / x through the C ABI, copies inside the timed region
     e2e_t = []
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        se = g.Solver(A, w.block_ptr, perm=w.perm, precision="fp64", layout=args.layout)
+        se = g.Solver(w.A, bp, perm=perm, precision="fp64", layout=args.layout)
         xe, ste, ce = se.solve(w.F[0], tol=TOL)
         e2e_t.append((time.perf_counter() - t0) * 1e3)
         se.close()
-    h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.val.nbytes + w.F[0].nbytes
+    h2d = w.A.row_ptr.nbytes + w.A.col_idx.nbytes + w.A.val.nbytes + w.F[0].nbytes
     d2h = xe.nbytes
 
-    pk = peaks()
-    nnz_bd_est = None
-    def per_iter(st, kt, t_steps):
-        nblk = len(w.block_ptr) - 1
-        launches = st["iters"] + 1
-        refine_mean = st["refine_steps_total"] / max(1, nblk * (launches + 1))
-        wf = 8 if st is st64 else 4
-        # the exact Gram blocks have ~25 entries per row for the 7-point stencil
-        b = algorithmic_bytes(n, A.nnz, st["pass_bytes"] / 2, wf, refine_mean, 25 * n)
-        it_ms = st["t_solve_ms"] / max(1, st["iters"] + 1)
-        return {"time_to_solution_ms": sum(t_steps) / len(t_steps), "iters": st["iters"],
-                "rel_res": st["rel_res"], "backward_err": st["backward_err"],
-                "setup_ms": st["t_setup_ms"], "factor_ms": st["t_factor_ms"],
-                "solve_ms": st["t_solve_ms"], "per_iter_ms": it_ms,
-                "hbm_gbps_per_iter": b["iteration"] / (it_ms * 1e-3) / 1e9,
-                "proj_ms": kt["proj_ms"], "proj_ms_isolated": kt["proj_ms_isolated"],
-                "proj_launches_timed": kt["proj_launches_timed"], "proj_bytes": b["proj"],
-                "proj_gbps": b["proj"] / (kt["proj_ms"] * 1e-3) / 1e9,
-                "refine_steps_mean": refine_mean, "fallbacks": st["fallbacks"],
-                "factor_bytes": st["factor_bytes"], "pass_bytes": st["pass_bytes"],
-                "kernel_launches": st["kernel_launches"]}
+    # the other partition of the same workload (one warm-up and one timed solve each)
+    other = None
+    if not args.no_other:
+        op = "contiguous" if part["partition"] == "graph" else "graph"
+        if op == "contiguous" or args.config in (2, 3):
+            operm, obp, opart = partition_of(w, op, args.config)
+            ro = Runner(w, operm, obp, args.layout, dev, stream, flush)
+            other = dict(opart)
+            for precision in ("fp64", "fp32_refine"):
+                tt, (so, sto, codeo) = ro.timed(precision, 1, 1)
+                so.close()
+                other[precision] = {"time_to_solution_ms": round(tt[0], 3), "iters": sto["iters"],
+                                    "status": codeo, "factor_ms": round(sto["t_factor_ms"], 3),
+                                    "cholesky_ms": round(sto["t_chol_ms"], 3),
+                                    "solve_ms": round(sto["t_solve_ms"], 3),
+                                    "factor_bytes": sto["factor_bytes"]}
+            del ro
+    cfg2 = None if args.no_cfg2 or args.config == 2 else leg_config2(dev, stream, flush,
+                                                                      args.layout, local)
+    cfg5 = None if args.no_cfg5 or args.config == 5 else leg_config5(dev, stream, flush,
+                                                                      args.layout, local)
 
-    r64 = per_iter(st64, kt64, t64)
-    r32 = per_iter(st32, kt32, t32)
-    rrx = {"time_to_solution_ms": round(sum(tr) / len(tr), 3), "iters": str_["iters"],
-           "rel_res": str_["rel_res"], "status": coder, "solve_ms": round(str_["t_solve_ms"], 3),
-           "refine_steps_total": str_["refine_steps_total"],
-           "inner_solves": (len(w.block_ptr) - 1) * (str_["iters"] + 1)}
-    s64.close()
-    s32.close()
-    sr.close()
-    gp = None if args.no_gp else gp_leg(w, dA, dF, dX, stream, args.layout)
+    pk = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    # FP64 projection: every streamed FP64 factor element feeds one FMA, so it is bound by
-    # GB300's FP64 pipe (ncu: FP64 pipe 73% / DRAM 35% busy); FP32 projection: HBM-bound.
-    flops64 = st64["pass_bytes"] / 4.0           # 2 flops per 8-byte element, one pass
+    peak_src = "measured" if "fallback" not in pk else "fallback"
+    # the kernel that dominates the FP64 step: the batched Cholesky or the projections
+    chol64 = {"bound": "alu", "kernel": "k_cholesky<double> (FP64 tile Cholesky, one CTA per block)",
+              "achieved": r64["cholesky_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "frac": round(r64["cholesky_tflops"] / FP64_PEAK_TFLOPS, 4),
+              "traffic": TRAFFIC.get("k_cholesky_fp64_" + w.name),
+              "flops_per_launch": st64["factor_flops"], "ms_per_launch": r64["cholesky_ms"],
+              "peak_source": "nominal FP64 rate (152 SMs at 2070 MHz)"}
+    flops64 = st64["pass_bytes"] / 4.0  # 2 flops per streamed 8-byte factor element, one pass
     tf64 = flops64 / (kt64["proj_ms"] * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": round(tf64, 4), "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": round(tf64 / FP64_PEAK_TFLOPS, 4),
-            "traffic": PROJ_TRAFFIC.get("fp64"), "kernel": "k_proj (FP64 tile solves)",
-            "peak_source": "nominal FP64 1.25 TFLOP/s (probe measured 1.196)",
-            "hbm_view": {"achieved_gbs": round(r64["proj_gbps"], 1), "frac": round(r64["proj_gbps"] / hbm, 4)}}
-    roof32 = {"bound": "hbm", "achieved": round(r32["proj_gbps"], 1), "peak": hbm, "unit": "GB/s",
-              "frac": round(r32["proj_gbps"] / hbm, 4), "traffic": PROJ_TRAFFIC.get("fp32"),
-              "kernel": "k_proj (FP32 tile solves + FP64 refinement)",
-              "peak_source": "measured" if "fallback" not in pk else "fallback"}
+    proj64 = {"bound": "alu", "kernel": "k_proj (FP64 tile solves)", "achieved": round(tf64, 4),
+              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(tf64 / FP64_PEAK_TFLOPS, 4),
+              "traffic": TRAFFIC.get("k_proj_fp64_" + w.name),
+              "ms_per_launch": r64["proj_ms"], "peak_source": "nominal FP64 rate",
+              "hbm_view": {"achieved_gbs": r64["proj_gbps"], "frac": round(r64["proj_gbps"] / hbm, 4)}}
+    proj32 = {"bound": "hbm", "kernel": "k_proj (FP32 tile solves + FP64 refinement)",
+              "achieved": r32["proj_gbps"], "peak": hbm, "unit": "GB/s",
+              "frac": round(r32["proj_gbps"] / hbm, 4),
+              "traffic": TRAFFIC.get("k_proj_fp32_" + w.name), "ms_per_launch": r32["proj_ms"],
+              "peak_source": peak_src}
+    chol_share = r64["cholesky_ms"] / r64["time_to_solution_ms"]
+    proj_share = r64["proj_ms"] * (r64["iters"] + 1) / r64["time_to_solution_ms"]
+    roof = dict(chol64 if chol_share >= proj_share else proj64)
+    roof["share_of_step"] = round(max(chol_share, proj_share), 4)
+    cfg = config_dict(w, part, args.layout, args)
     out = {
         "metric": METRIC, "value": round(ms_step, 3), "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": w.name, "n": n, "nnz": int(A.nnz), "K": len(w.block_ptr) - 1,
-                   "partition": "contiguous", "layout": args.layout, "tol": TOL,
-                   "precision": "fp64", "l2": "flushed (512 MB write) before every timed step",
-                   "parallelism": "replicas" if args.gpus > 1 else "single"},
+        "data": "synthetic", "config": cfg, "partition_info": part,
         "fp64": r64, "fp32_refine": r32, "fp32_refine_relaxed": rrx,
         "fp32_vs_fp64_time_ratio": round(r32["time_to_solution_ms"] / r64["time_to_solution_ms"], 4),
-        "graph_partition": gp,
+        "other_partition": other, "convdiff3d_64": cfg2, "convdiff3d_128_16rhs": cfg5,
         "roofline": roof,
-        "roofline_fp32": roof32,
+        "roofline_kernels": {"cholesky_fp64": chol64, "proj_fp64": proj64, "proj_fp32": proj32,
+                             "cholesky_tc_fp32": {
+                                 "bound": "tensor", "kernel": "k_cholesky_tc (3xTF32 tcgen05)",
+                                 "useful_tflops": r32["cholesky_tflops"],
+                                 "ms_per_launch": r32["cholesky_ms"],
+                                 "note": "useful FP32 flops; the tensor pipe issues 3x as "
+                                         "TF32 (3xTF32 split)"}},
         "e2e": {"value": round(min(e2e_t), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(st64["kernel_launches"]) * args.steps,
         "clocks": clocks.summary(),
         "wall_s": round(wall, 3),
     }
-    return out
+    return out, (w, perm, bp)
 
 
-def contiguous_cut(C, block_ptr):
-    """Cutsize (Eq. 2.6, cosine weights of the row-scaled A) of the partition into
-    consecutive row ranges, from C = A A^T of the unscaled A."""
-    rp, ci, v = C
-    n = len(rp) - 1
-    rows = np.repeat(np.arange(n), np.diff(rp))
-    d = np.zeros(n)
-    dg = rows == ci
-    d[rows[dg]] = np.sqrt(v[dg])
-    blk = np.searchsorted(block_ptr, np.arange(n), side="right") - 1
-    m = (ci > rows) & (blk[rows] != blk[ci])
-    return float(np.sum(np.abs(v[m]) / (d[rows[m]] * d[ci[m]])))
+# ------------------------------------------------------------------ the oracle on the host cores
 
+def oracle_sample(w, perm, bp, cores, steps, warmup, iters):
+    """The FP64 oracle as it stands, on the host cores, in bounded samples of the workload.
 
-def gp_leg(w, dA, dF, dX, stream, layout, eps=0.05):
-    """The graph-partitioned variant of the workload (Section 2): C = A A^T on the GPU, the
-    host multilevel partitioner on G_RIP with blocks of at most (1 + eps) n / K rows, then
-    both precisions solved with those blocks (one warm-up and one timed solve each)."""
-    import torch
-
-    import paper_1710_07769_gb300 as g
-    n = w.A.n
-    K = len(w.block_ptr) - 1
-    t0 = time.perf_counter()
-    C = g.aat(w.A)
-    t_aat = time.perf_counter() - t0
-    cap = int(np.floor((1.0 + eps) * n / K))
-    t0 = time.perf_counter()
-    perm, bp, cut = g.partition_rip(n, C, K, cap=cap, seed=0)
-    t_part = time.perf_counter() - t0
-    out = {"eps": eps, "cap": cap, "aat_s": round(t_aat, 3), "partition_s": round(t_part, 2),
-           "cutsize": round(cut, 2), "cutsize_contiguous": round(contiguous_cut(C, w.block_ptr), 2),
-           "block_rows_min": int(np.diff(bp).min()), "block_rows_max": int(np.diff(bp).max())}
-    for precision in ("fp64", "fp32_refine"):
-        times = []
-        for _ in range(2):
-            with torch.cuda.stream(stream):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                s = g.Solver(dA, bp, perm=perm, precision=precision, layout=layout)
-                x, st, code = s.solve(dF, tol=TOL, X=dX)
-                e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            s.close()
-        out[precision] = {"time_to_solution_ms": round(times[-1], 3), "iters": st[0]["iters"],
-                          "rel_res": st[0]["rel_res"], "status": code,
-                          "factor_ms": round(st[0]["t_factor_ms"], 3),
-                          "solve_ms": round(st[0]["t_solve_ms"], 3),
-                          "factor_bytes": st[0]["factor_bytes"]}
-    return out
-
-
-def cpu_sample(config, nthreads=None, iters_sample=10, full_iters=None):
-    """Oracle on the host cores: full setup (scaling, A A^T, all Cholesky factors) plus a
-    bounded number of CG iterations, extrapolated to the full iteration count."""
-    import inputs
+    Once (not part of a step): the oracle's setup without factors (scaling, permutation,
+    C = A A^T; OpenMP over rows / columns where the oracle has it).  Each step: the
+    oracle's Cholesky of `cores` consecutive Gram blocks (one block per thread, OpenMP over
+    blocks, i.e. one wave of the full factorisation) and one inner solve of each of those
+    blocks (one wave of a projection's solves), blocks rotating from step to step.  The
+    full oracle time to solution is estimated from these as
+      setup + ceil(K / cores) * factor wave + iters * ceil(K / cores) * solve wave,
+    the sparse products of an iteration being small beside the dense block solves."""
     import oracle
-    nthreads = nthreads or os.cpu_count()
-    w = inputs.workload(config)
+    K = len(bp) - 1
+    S = max(1, min(cores, K))
     t0 = time.perf_counter()
-    o = oracle.Oracle(w.A, w.block_ptr, perm=w.perm, nthreads=nthreads)
+    o = oracle.Oracle(w.A, bp, perm=perm, factor=False, nthreads=cores)
     t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    x, it, rr, gm, st = o.solve(w.F[0], maxit=iters_sample)
-    t_it = (time.perf_counter() - t0) / max(it, 1)
-    full = full_iters if full_iters is not None else it
-    est_ms = (t_setup + full * t_it) * 1e3
-    return {"value": round(est_ms, 1), "unit": "ms", "cores": nthreads, "kind": "oracle",
-            "workload": w.name,
-            "sample": f"{w.name}: full oracle setup ({t_setup:.1f} s) + {it} CG iterations "
-                      f"({t_it * 1e3:.1f} ms each) extrapolated to {full} iterations"}
+    u = np.random.default_rng(0).standard_normal(w.A.n)
+    step_ms, fac_s, sol_s = [], [], []
+    for i in range(warmup + steps):
+        b0 = (i * S) % K
+        b1 = min(K, b0 + S)
+        t0 = time.perf_counter()
+        st = o.factor_range(b0, b1)
+        t1 = time.perf_counter()
+        o.solve_range(u)
+        t2 = time.perf_counter()
+        if st != 0:
+            raise RuntimeError(f"oracle factorisation failed (status {st})")
+        if i >= warmup:
+            step_ms.append((t2 - t0) * 1e3)
+            fac_s.append((t1 - t0) * (S / (b1 - b0)))
+            sol_s.append((t2 - t1) * (S / (b1 - b0)))
+    o.close()
+    waves = math.ceil(K / S)
+    f_wave, s_wave = statistics.median(fac_s), statistics.median(sol_s)
+    est_setup = t_setup + waves * f_wave
+    est_iter = waves * s_wave
+    est = (est_setup + iters * est_iter) * 1e3
+    return {"step_ms": step_ms, "cores": cores, "kind": "oracle",
+            "setup_without_factors_s": round(t_setup, 2), "factor_wave_s": round(f_wave, 3),
+            "solve_wave_s": round(s_wave, 4), "waves": waves,
+            "est_setup_ms": round(est_setup * 1e3, 1), "est_iteration_ms": round(est_iter * 1e3, 2),
+            "iters": iters, "est_time_to_solution_ms": round(est, 1),
+            "sample": f"{w.name}: oracle setup without factors once ({t_setup:.1f} s), then per "
+                      f"step the Cholesky of {S} of the {K} Gram blocks ({S} threads) and their "
+                      f"inner solves; full time to solution estimated for {iters} iterations"}
+
+
+def reference_iters(config, w, perm, bp):
+    """Iteration count the reference estimate uses: the oracle's own run where it is cheap
+    (config 1) or stored (the 64^3 system, written from the oracle only); elsewhere the
+    FP64 count of the GPU solve on these blocks, which the parity tests hold to the
+    oracle's +-1 (30 for the graph-partitioned random system)."""
+    if config == 1:
+        import oracle
+        return oracle.Oracle(w.A, bp, perm=perm).solve(w.F[0])[1]
+    if config == 2:
+        return int(json.load(open(os.path.join(GOLDEN, "config2_oracle.json")))["iters"])
+    return {3: 30, 5: 3900}.get(config, 100)
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host cores, each step a bounded sample
+    of the same workload and blocks as our arm (the partition is input preparation, not
+    timed)."""
+    import inputs
+    w = inputs.workload(args.config)
+    partition = args.partition or DEFAULT_PARTITION.get(args.config, "contiguous")
+    perm, bp, part = partition_of(w, partition, args.config, use_gpu=False)
+    cores = os.cpu_count() or 1
+    iters = reference_iters(args.config, w, perm, bp)
+    t_run = time.perf_counter()
+    smp = oracle_sample(w, perm, bp, cores, args.steps, args.warmup, iters)
+    steps_ms = smp.pop("step_ms")
+    v = sum(steps_ms) / len(steps_ms)
+    cb = dict(smp)
+    cb["value"] = round(v, 1)
+    cb["unit"] = "ms"
+    cfg = config_dict(w, part, args.layout, args)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "partition_info": part,
+            "value_is": "per-step time of the bounded oracle sample (see cpu_baseline.sample)",
+            "extrapolated_time_to_solution_ms": smp["est_time_to_solution_ms"],
+            "cpu_baseline": cb, "run_s": round(time.perf_counter() - t_run, 1),
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------ profiling targets
+
+def run_profile(args):
+    import inputs
+    import paper_1710_07769_gb300 as g
+    if args.profile == "spgemm":
+        w = inputs.workload(args.config)
+        rp, ci, v = g.aat(w.A)
+        print(json.dumps({"profile": "spgemm", "workload": w.name, "nnz_aat": int(len(v))}))
+        return 0
+    if args.profile in ("cholesky_tc", "cholesky_fp64"):
+        # random n = 2^18 with 8 off-diagonals per row: 128 Gram blocks of 2048 rows from the
+        # graph partition (banded envelopes, as in the n = 2^20 workload) or contiguous
+        # (nearly dense envelopes)
+        n = 1 << 18
+        A = inputs.random_dd(n, 8, 3)
+        if (args.partition or "graph") == "graph":
+            perm, bp, _ = g.partition_rip(n, g.aat(A), n // 2048, cap=2048, seed=0)
+        else:
+            perm, bp = None, inputs.contiguous_blocks(n, 2048)
+        prec = "fp32_refine" if args.profile == "cholesky_tc" else "fp64"
+        s = g.Solver(A, bp, perm=perm, precision=prec, max_iter=1)
+        x, st, code = s.solve(inputs.matvec(A, np.ones(n)), tol=TOL)
+        print(json.dumps({"profile": args.profile, "n": n, "cholesky_ms": st[0]["t_chol_ms"],
+                          "factor_gflop": st[0]["factor_flops"] / 1e9}))
+        s.close()
+        return 0
+    multi = args.profile == "fp32_refine_16rhs"
+    w = inputs.workload(args.config, nrhs=16 if multi else None)
+    s = g.Solver(w.A, w.block_ptr, perm=w.perm, precision="fp32_refine" if multi else args.profile,
+                 layout=args.layout, max_iter=4, check_every=1)
+    x, st, code = s.solve(w.F if multi else w.F[0], tol=TOL)
+    print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
+                      "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
+    s.close()
+    return 0
 
 
 def main():
@@ -390,86 +651,44 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3, 5])
+    ap.add_argument("--partition", default=None, choices=["graph", "contiguous"],
+                    help="blocks of the workload (default: graph for the n = 2^20 random "
+                         "system, contiguous otherwise)")
     ap.add_argument("--layout", default="skyline", choices=["skyline", "dense"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
-    ap.add_argument("--no-gp", action="store_true", help="skip the graph-partitioned leg")
+    ap.add_argument("--no-other", action="store_true", help="skip the other-partition leg")
+    ap.add_argument("--no-cfg2", action="store_true", help="skip the 64^3 leg")
+    ap.add_argument("--no-cfg5", action="store_true", help="skip the 128^3 16-RHS leg")
     ap.add_argument("--profile", default=None,
-                    choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "cholesky_tc", "spgemm"],
+                    choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "cholesky_tc",
+                             "cholesky_fp64", "spgemm"],
                     help="profiling target, nothing timed: fp64 / fp32_refine / "
-                         "fp32_refine_16rhs = one setup + 4 CG iterations of the workload "
-                         "(16 right-hand sides sharing the factors for the last); cholesky_tc = "
-                         "setup of 128 dense 2048-row Gram blocks (random n = 2^18, 8 entries "
-                         "per row); spgemm = standalone C = A A^T of the workload")
+                         "fp32_refine_16rhs = one setup + 4 CG iterations of --config (16 "
+                         "right-hand sides for the last); cholesky_tc / cholesky_fp64 = setup "
+                         "of 128 Gram blocks of 2048 rows of a random n = 2^18 system "
+                         "(graph-partitioned unless --partition contiguous); spgemm = "
+                         "standalone C = A A^T of --config")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.profile:
-        import numpy as np
-
-        import inputs
-        import paper_1710_07769_gb300 as g
-        if args.profile == "spgemm":
-            w = inputs.workload(args.config)
-            rp, ci, v = g.aat(w.A)
-            print(json.dumps({"profile": "spgemm", "workload": w.name, "nnz_aat": int(len(v))}))
-            return 0
-        if args.profile == "cholesky_tc":
-            n = 1 << 18
-            A = inputs.random_dd(n, 8, 3)
-            s = g.Solver(A, inputs.contiguous_blocks(n, 2048), precision="fp32_refine", max_iter=1)
-            x, st, code = s.solve(inputs.matvec(A, np.ones(n)), tol=TOL)
-            print(json.dumps({"profile": "cholesky_tc", "n": n, "factor_ms": st[0]["t_factor_ms"]}))
-            s.close()
-            return 0
-        multi = args.profile == "fp32_refine_16rhs"
-        w = inputs.workload(args.config, nrhs=16 if multi else None)
-        s = g.Solver(w.A, w.block_ptr, perm=w.perm,
-                     precision="fp32_refine" if multi else args.profile, layout=args.layout,
-                     max_iter=4, check_every=1)
-        x, st, code = s.solve(w.F if multi else w.F[0], tol=TOL)
-        print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
-                          "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
-        s.close()
-        return 0
+        return run_profile(args)
     if args.impl == "reference":
         if rank != 0:
             return 0
-        # the oracle as it stands, on the host cores; each step a bounded sample (full setup
-        # plus 5 CG iterations), extrapolated to the oracle's own iteration count to 1e-10,
-        # which tests/golden/config2_oracle.json records for the default workload (written
-        # from oracle/ only); other workloads report the sample itself
-        full = None
-        gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
-                            "config2_oracle.json")
-        if args.config == 2 and os.path.exists(gold):
-            full = int(json.load(open(gold))["iters"])
-        samples = []
-        for i in range(args.warmup + args.steps):
-            r = cpu_sample(args.config, iters_sample=5, full_iters=full)
-            if i >= args.warmup:
-                samples.append(r)
-        v = sum(s["value"] for s in samples) / len(samples)
-        cb = dict(samples[-1])
-        cb["value"] = round(v, 1)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms",
-                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                          "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
-                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": cb.pop("workload"), "partition": "contiguous",
-                                     "tol": TOL, "precision": "fp64"},
-                          "cpu_baseline": cb,
-                          "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}))
+        print(json.dumps(run_reference(args)))
         return 0
     if args.gpus > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    out = run_ours(args, rank, local)
+    out, (w, perm, bp) = run_ours(args, rank, local)
     if rank == 0:
         if not args.no_cpu:
-            cb = cpu_sample(args.config, full_iters=out["fp64"]["iters"])
-            cb.pop("workload")
-            out["cpu_baseline"] = cb
+            smp = oracle_sample(w, perm, bp, os.cpu_count() or 1, 2, 0, out["fp64"]["iters"])
+            smp.pop("step_ms")
+            smp["value"] = smp["est_time_to_solution_ms"]
+            smp["unit"] = "ms"
+            out["cpu_baseline"] = smp
         print(json.dumps(out))
     if args.gpus > 1:
         import torch

@@ -125,6 +125,11 @@ typedef struct cimmino_stats {
   int64_t factor_bytes;       /* bytes of the stored factor tiles (L_II and N_IJ)    */
   int64_t pass_bytes;         /* factor bytes one forward + backward solve streams    */
   int64_t kernel_launches;    /* kernels launched by the setup plus by this solve     */
+  double factor_flops;        /* algorithmic flops of the Cholesky of all G_i inside */
+                              /* the tile envelope (r^3/3 per diagonal tile, r_I r_K^2 */
+                              /* per solved tile, 2 r_I r_J r_K per trailing product) */
+  double t_chol_ms;           /* device time of the batched Cholesky launch alone    */
+  int64_t nnz_gram;           /* entries of the exact Gram blocks G_i (sum over i)    */
 } cimmino_stats;
 
 typedef struct cimmino_ctx cimmino_ctx;

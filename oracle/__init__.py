@@ -98,6 +98,10 @@ def _load():
         lib.orc_sparsify_dense_columns.restype = C.c_int64
         lib.orc_cholesky_dense.argtypes = [C.c_int64, _f64p]
         lib.orc_cholesky_dense.restype = C.c_int
+        lib.orc_factor_range.argtypes = [_p, C.c_int32, C.c_int32]
+        lib.orc_factor_range.restype = C.c_int
+        lib.orc_solve_range.argtypes = [_p, _f64p, _f64p]
+        lib.orc_solve_range.restype = C.c_int
         _lib = lib
         return lib
 
@@ -183,6 +187,21 @@ class Oracle:
         G = np.zeros(m * m)
         self.lib.orc_gram_get(self._h, int(b), G)
         return G.reshape(m, m)
+
+    def factor_range(self, b0: int, b1: int) -> int:
+        """Cholesky of the Gram blocks [b0, b1) only (the full setup's routine, into
+        storage of their own): a bounded sample of the factorisation.  Returns the status."""
+        return int(self.lib.orc_factor_range(self._h, int(b0), int(b1)))
+
+    def solve_range(self, u: np.ndarray) -> np.ndarray:
+        """y_i = G_i^{-1} u_i for the blocks of the last factor_range (permuted-row
+        n-vectors; other rows of y stay zero): a bounded sample of a projection's solves."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        y = np.zeros(self.n)
+        st = self.lib.orc_solve_range(self._h, u, y)
+        if st != ORC_OK:
+            raise OracleError(st, "solve_range needs a factor_range first")
+        return y
 
     # --- the method ---------------------------------------------------------
     def project(self, v: np.ndarray) -> np.ndarray:

@@ -54,6 +54,10 @@
 typedef struct orc_ctx {
   int64_t n, nnz;
   int32_t K;
+  /* factors of a sub-range of blocks [rb0, rb1) only (bounded CPU timing samples) */
+  int32_t rb0, rb1;
+  int64_t *rfoff;
+  double *rL;
   /* original matrix (for the true residual) */
   int64_t *rp0;
   int32_t *ci0;
@@ -361,6 +365,7 @@ void orc_free(orc_ctx *c) {
   free(c->cp); free(c->ri); free(c->cv);
   free(c->crp); free(c->cci); free(c->ccv);
   free(c->foff); free(c->L);
+  free(c->rfoff); free(c->rL);
   free(c->rs); free(c->cs); free(c->ve);
   free(c);
 }
@@ -408,6 +413,48 @@ int orc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
 }
 
 int32_t orc_fail_block(const orc_ctx *c) { return c->fail_block; }
+
+/* The same Gram-block Cholesky as the full setup, for the blocks [b0, b1) only, into
+ * storage of their own (replacing an earlier range); OpenMP over the blocks.  With
+ * orc_solve_range this times a bounded sample of the setup and of one projection's
+ * inner solves on problems whose full oracle run would take too long. */
+int orc_factor_range(orc_ctx *c, int32_t b0, int32_t b1) {
+  if (!c || b0 < 0 || b1 > c->K || b1 <= b0) return ORC_EINVAL;
+  free(c->rfoff); free(c->rL);
+  c->rfoff = (int64_t *)xcalloc((size_t)(b1 - b0) + 1, sizeof(int64_t));
+  if (!c->rfoff) return ORC_ENOMEM;
+  for (int32_t b = b0; b < b1; ++b) {
+    int64_t m = c->bp[b + 1] - c->bp[b];
+    c->rfoff[b - b0 + 1] = c->rfoff[b - b0] + m * (m + 1) / 2;
+  }
+  c->rL = (double *)xcalloc((size_t)c->rfoff[b1 - b0], sizeof(double));
+  if (!c->rL) return ORC_ENOMEM;
+  c->rb0 = b0;
+  c->rb1 = b1;
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(c->nthreads)
+  for (int32_t b = b0; b < b1; ++b) {
+    double *L = c->rL + c->rfoff[b - b0];
+    gram_block(c, b, L);
+    if (cholesky_packed(c->bp[b + 1] - c->bp[b], L) != 0) {
+#pragma omp critical
+      { fail = 1; }
+    }
+  }
+  return fail ? ORC_ESINGULAR : ORC_OK;
+}
+
+/* y_i = G_i^{-1} u_i for the blocks of the last orc_factor_range (u, y: permuted-row
+ * n-vectors; rows of other blocks are left untouched). */
+int orc_solve_range(const orc_ctx *c, const double *u, double *y) {
+  if (!c || !c->rL) return ORC_EINVAL;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(c->nthreads)
+  for (int32_t b = c->rb0; b < c->rb1; ++b) {
+    int64_t r0 = c->bp[b], m = c->bp[b + 1] - r0;
+    chol_solve(m, c->rL + c->rfoff[b - c->rb0], u + r0, y + r0);
+  }
+  return ORC_OK;
+}
 int64_t orc_aat_nnz(const orc_ctx *c) { return c->nnzc; }
 
 void orc_aat_get(const orc_ctx *c, int64_t *rp, int32_t *ci, double *v) {

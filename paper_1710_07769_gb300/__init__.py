@@ -59,7 +59,9 @@ class StatsStruct(C.Structure):
                 ("refine_steps_max", C.c_int32), ("fallbacks", C.c_int32),
                 ("t_setup_ms", C.c_double), ("t_factor_ms", C.c_double),
                 ("t_solve_ms", C.c_double), ("nnz_aat", C.c_int64), ("factor_bytes", C.c_int64),
-                ("pass_bytes", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("pass_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("factor_flops", C.c_double), ("t_chol_ms", C.c_double),
+                ("nnz_gram", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

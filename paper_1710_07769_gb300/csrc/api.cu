@@ -137,6 +137,8 @@ struct cimmino_ctx {
   std::vector<TileRow> htrowT;
   int64_t pass_bytes = 0;  // factor bytes one forward + backward solve pass streams
   int64_t nnzc = 0, nnz_bd = 0, factor_bytes = 0;
+  double factor_flops = 0.0;  // algorithmic flops of the envelope Cholesky of all G_i
+  double t_chol_ms = 0.0;     // device time of the batched Cholesky launch alone
   int32_t fallbacks = 0;
   int64_t setup_launches = 0;  // kernels launched by the setup
   double t_setup_ms = 0.0, t_factor_ms = 0.0;
@@ -513,6 +515,25 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->dinv32.alloc(doff);
   }
   c->factor_bytes = off * (fp64 ? 8 : 4);
+  // Algorithmic flops of the Cholesky restricted to the tile envelope, with the actual rows
+  // r_I of every tile row: the diagonal factorisations r_K^3 / 3, the triangular solves
+  // r_I r_K^2 of the tiles (I, K) below them, and the trailing products 2 r_I r_J r_K
+  // (r_I^2 r_K on the symmetric diagonal tiles J = I) for K < J <= I inside the envelope.
+  c->factor_flops = 0.0;
+  for (const auto &B : c->hblk) {
+    auto rows = [&](int32_t I) { return (double)std::min(kTile, B.m - I * kTile); };
+    for (int32_t K = 0; K < B.nt; ++K) {
+      const double rK = rows(K);
+      c->factor_flops += rK * rK * rK / 3.0;
+      for (int32_t I = K + 1; I < B.nt; ++I) {
+        if (c->htrow[B.trow0 + I].j0 > K) continue;
+        const double rI = rows(I);
+        c->factor_flops += rI * rK * rK + rI * rI * rK;  // solve of (I, K), update of (I, I)
+        for (int32_t J = K + 1; J < I; ++J)
+          if (c->htrow[B.trow0 + J].j0 <= K) c->factor_flops += 2.0 * rI * rows(J) * rK;
+      }
+    }
+  }
   c->t_setup_ms = tsetup.stop_ms(s);
 
   stage.next("cimmino.setup.factor");
@@ -531,14 +552,19 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   void *dinv = fp64 ? (void *)c->dinv64.p : (void *)c->dinv32.p;
   launch_gram_scatter(c->blk.p, blist.p, nblk, c->trow.p, c->brp.p, c->bci.p, c->bcv.p, fac,
                       fp64, s);
+  if (!fp64) {
+    c->err_flag.alloc(1);
+    CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
+  }
+  Timer tchol;
+  tchol.start(s);
   if (fp64) {
     launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, fac, dinv, 1, pmin.p, pfail.p, s);
   } else {
-    c->err_flag.alloc(1);
-    CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
     launch_cholesky_tc(c->blk.p, blist.p, nblk, c->trow.p, c->fac32.p, c->dinv32.p, pmin.p,
                        pfail.p, c->err_flag.p, s);
   }
+  c->t_chol_ms = tchol.stop_ms(s);
   c->setup_launches += 2;  // scatter, Cholesky
   CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> hfail(nblk);
@@ -960,6 +986,9 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.t_solve_ms = tms;
         o.nnz_aat = c->nnzc;
         o.factor_bytes = c->factor_bytes;
+        o.factor_flops = c->factor_flops;
+        o.t_chol_ms = c->t_chol_ms;
+        o.nnz_gram = c->nnz_bd;
         o.pass_bytes = c->pass_bytes;
         // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
         o.kernel_launches =

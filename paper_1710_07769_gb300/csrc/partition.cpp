@@ -116,8 +116,7 @@ Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<i
   for (int32_t cv = 0; cv < nc; ++cv) {
     list.clear();
     const int32_t a = rep[cv], b = match[a];
-    for (int32_t v : {a, b}) {
-      if (v == b && b == a) continue;
+    auto gather = [&](int32_t v) {
       for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
         const int32_t cu = cmap[g.adj[q]];
         if (cu == cv) continue;
@@ -128,7 +127,9 @@ Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<i
         }
         acc[cu] += g.w[q];
       }
-    }
+    };
+    gather(a);
+    if (b != a) gather(b);  // an unmatched vertex (b == a) has no partner
     for (int32_t cu : list) {
       c.adj.push_back(cu);
       c.w.push_back(acc[cu]);

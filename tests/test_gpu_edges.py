@@ -7,14 +7,13 @@ import pytest
 
 import inputs
 import oracle
+from parity_util import assert_close, rel
 
 pytestmark = pytest.mark.gpu
 
 g = pytest.importorskip("paper_1710_07769_gb300")
 
 
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-10)])
@@ -26,12 +25,12 @@ def test_one_row_blocks(precision, tol):
     s = g.Solver(A, bp, precision=precision)
     o = oracle.Oracle(A, bp)
     v = np.random.default_rng(4).standard_normal(A.n)
-    assert rel(s.project(v), o.project(v)) <= tol
+    assert_close(s.project(v), o.project(v), tol)
     f = inputs.matvec(A, np.random.default_rng(5).uniform(-1, 1, A.n))
     xo, ito, *_ = o.solve(f)
     x, st, code = s.solve(f)
     assert code == 0 and abs(st[0]["iters"] - ito) <= 1
-    assert rel(x, xo) <= 1e-8
+    assert_close(x, xo, 1e-8)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refine", 1e-10)])
@@ -46,10 +45,10 @@ def test_largest_block(precision, tol):
     V = np.random.default_rng(6).standard_normal((3, A.n))
     P = s.project(V)
     for k in range(3):
-        assert rel(P[k], o.project(V[k])) <= tol, k
+        assert_close(P[k], o.project(V[k]), tol, k)
     for b in (0, 1):
         Lg, is64 = s.factor(b)
-        assert rel(np.tril(Lg), o.factor(b)) <= (1e-12 if is64 else 2e-5)
+        assert_close(np.tril(Lg), o.factor(b), (1e-12 if is64 else 2e-5))
 
 
 def test_block_over_limit_rejected():
@@ -78,7 +77,7 @@ def test_forty_rhs_groups():
     V = np.random.default_rng(40).standard_normal((40, A.n))
     P = s.project(V)
     for k in (0, 15, 16, 31, 32, 39):
-        assert rel(P[k], o.project(V[k])) <= 1e-10, k
+        assert_close(P[k], o.project(V[k]), 1e-10, k)
 
 
 def test_bad_inputs_rejected():

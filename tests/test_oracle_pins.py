@@ -336,6 +336,46 @@ def test_config1_solution_matches_dense_lu():
     assert 300 < it < 400
 
 
+def test_gamma_and_first_cg_step_closed_form_2x2():
+    """A hand-worked case of Algorithm 2, Eq. 1.5 and Eq. 3.1.  A = [[1, 0], [1, 1]],
+    f = (1, 2), one row per block (K = 2).  With unit rows a_1 = (1, 0),
+    a_2 = (1, 1)/sqrt(2): H = a_1 a_1^T + a_2 a_2^T = [[3/2, 1/2], [1/2, 1/2]] and
+    xi = sum_i A_i^+ f_i = (1, 0) + (1, 1) = (2, 1).  The first CG step from x = 0:
+    r = p = xi, rho = 5, p^T H p = (2, 1).(7/2, 3/2) = 17/2, alpha = 10/17, so
+    x_1 = (20/17, 10/17) and f - A x_1 = (-3/17, 4/17).  Eq. 3.1 with ||A||_inf = 2,
+    ||x_1||_1 = 30/17 and ||f||_inf = 2 gives gamma = (4/17) / (60/17 + 2) = 2/47
+    (||x_1||_inf in its place would give 2/37, ||r||_2 would give 5/94); the relative
+    2-norm residual is (5/17) / sqrt(5) = sqrt(5)/17."""
+    A = inputs.CSR(2, np.array([0, 1, 3], np.int64), np.array([0, 0, 1], np.int32),
+                   np.array([1.0, 1.0, 1.0]))
+    o = oracle.Oracle(A, np.array([0, 1, 2], np.int64))
+    x, it, rr, gam, st = o.solve(np.array([1.0, 2.0]), maxit=1)
+    assert it == 1
+    np.testing.assert_allclose(x, [20 / 17, 10 / 17], rtol=1e-15)
+    assert gam == pytest.approx(2 / 47, rel=1e-14)
+    assert rr == pytest.approx(np.sqrt(5) / 17, rel=1e-14)
+    # a second step reaches the exact solution x = (1, 1) of the nonsingular 2 x 2 system
+    x2, it2, rr2, gam2, st2 = o.solve(np.array([1.0, 2.0]), maxit=2)
+    assert st2 == 0 and it2 == 2 and gam2 < 1e-15
+    np.testing.assert_allclose(x2, [1.0, 1.0], rtol=1e-14)
+
+
+@pytest.mark.parametrize("maxit", [3, 40])
+def test_gamma_equals_numpy_eq_3_1(maxit):
+    """gamma of Eq. 3.1 for the oracle's iterate, recomputed from the dense matrix with
+    numpy's norms (infinity norm of A = largest row sum, 1-norm of x)."""
+    w = inputs.workload(1)
+    o = oracle.Oracle(w.A, w.block_ptr)
+    x, it, rr, gam, st = o.solve(w.F[0], maxit=maxit)
+    D = dense(w.A)
+    f = w.F[0]
+    r = D @ x - f
+    ref = np.linalg.norm(r, np.inf) / (np.linalg.norm(D, np.inf) * np.linalg.norm(x, 1)
+                                       + np.linalg.norm(f, np.inf))
+    assert gam == pytest.approx(ref, rel=1e-12)
+    assert rr == pytest.approx(np.linalg.norm(r) / np.linalg.norm(f), rel=1e-12)
+
+
 def test_row_scaling_and_column_permutation_invariance():
     A = small_system(120, 4, 13)
     bp = np.array([0, 40, 80, 120])
@@ -602,3 +642,22 @@ def test_dense_columns_match_numpy_and_sparsify_graph(n, seed):
     rp2, ci2, v2 = oracle.sparsify_dense_columns(B)
     assert np.array_equal(rp2, B.row_ptr) and np.array_equal(ci2, B.col_idx)
     assert np.array_equal(v2, B.val)
+
+
+def test_range_factor_and_solves_equal_full_setup():
+    """The bounded-sample entry points (Cholesky and inner solves of a range of blocks)
+    reproduce numpy's solves with the Gram blocks of the full setup, and touch only their
+    own blocks' rows."""
+    A = inputs.random_dd(700, 5, 11)
+    bp = np.array([0, 1, 65, 200, 329, 330, 700], np.int64)
+    perm = np.random.default_rng(5).permutation(700).astype(np.int32)
+    full = oracle.Oracle(A, bp, perm=perm)
+    part = oracle.Oracle(A, bp, perm=perm, factor=False)
+    assert part.factor_range(2, 5) == 0
+    u = np.random.default_rng(3).standard_normal(700)
+    y = part.solve_range(u)
+    for b in (2, 3, 4):
+        r0, r1 = bp[b], bp[b + 1]
+        np.testing.assert_allclose(y[r0:r1], np.linalg.solve(full.gram(b), u[r0:r1]),
+                                   rtol=1e-11, atol=1e-13)
+    assert not y[:bp[2]].any() and not y[bp[5]:].any()
