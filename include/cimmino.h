@@ -25,8 +25,9 @@
  *    With opts.stream == NULL the context creates, and later destroys, a
  *    non-blocking stream of its own.  Every call returns after its results are
  *    complete, i.e. calls synchronise that stream before returning.
- *  - A context may be used by one host thread at a time.  There is no global
- *    mutable state: independent contexts may be used concurrently.
+ *  - A context may be used by one host thread at a time.  Independent contexts
+ *    may be used concurrently; the only state they share is the library's
+ *    per-device memory pool (see cimmino_opts.alloc), which is thread-safe.
  */
 #ifndef CIMMINO_H
 #define CIMMINO_H
@@ -75,6 +76,14 @@ typedef struct cimmino_csr {
   int32_t on_device;      /* 1: the three arrays are device pointers, 0: host       */
 } cimmino_csr;
 
+/* Caller-supplied device allocator (opts.alloc / opts.free): alloc returns `bytes` of
+ * device memory of the context's device usable in stream order on `stream` (a
+ * cudaStream_t), or NULL when it cannot (the call then fails with CIMMINO_ENOMEM); free
+ * takes back a pointer alloc returned, with the same size and stream.  `user` is
+ * opts.alloc_user.  The library calls them from the thread of the API call. */
+typedef void *(*cimmino_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*cimmino_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
 typedef struct cimmino_opts {
   int32_t precision;      /* CIMMINO_FP64 (default) or CIMMINO_FP32_REFINE           */
   int32_t layout;         /* CIMMINO_LAYOUT_SKYLINE (default) or _DENSE              */
@@ -104,7 +113,16 @@ typedef struct cimmino_opts {
                           /* the CG iterations for cimmino_proj_timing(); the       */
                           /* iterations are then launched eagerly, not as a graph   */
                           /* (events inside a graph cannot be timed); 0 (default)   */
-  void *stream;           /* cudaStream_t for all device work (NULL: own stream)   */
+  void *stream;           /* cudaStream_t for all device work (NULL: own stream);  */
+                          /* a caller stream must stay valid until cimmino_free()   */
+  cimmino_alloc_fn alloc; /* device memory of the context: NULL (default) takes it   */
+  cimmino_free_fn free;   /* from a per-device pool of the library, allocated and    */
+  void *alloc_user;       /* freed in stream order on opts.stream (cudaMallocAsync-  */
+                          /* style; freed blocks stay in the pool for the next      */
+                          /* context, so a new context allocates without cudaMalloc */
+                          /* once the pool is warm); set both alloc and free to use */
+                          /* the caller's allocator (e.g. a framework's caching     */
+                          /* allocator), else EINVAL                                 */
 } cimmino_opts;
 
 /* Statistics of one right-hand side of one system. */

@@ -44,13 +44,42 @@ class CSRStruct(C.Structure):
                 ("col_idx", C.c_void_p), ("val", C.c_void_p), ("on_device", C.c_int32)]
 
 
+# caller device allocator of a context (cimmino_opts.alloc / .free)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
 class OptsStruct(C.Structure):
     _fields_ = [("precision", C.c_int32), ("layout", C.c_int32), ("tile", C.c_int32),
                 ("refine_max", C.c_int32), ("refine_tol", C.c_double),
                 ("pivot_ratio_min", C.c_double), ("max_iter", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
                 ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32),
-                ("ruiz_sweeps", C.c_int32), ("time_proj", C.c_int32), ("stream", C.c_void_p)]
+                ("ruiz_sweeps", C.c_int32), ("time_proj", C.c_int32), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+def torch_allocator():
+    """(alloc, free) callbacks that take a context's device memory from torch's caching
+    allocator on the context's stream.  Keep the returned objects alive as long as the
+    context (the Solver classes do)."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 class StatsStruct(C.Structure):
@@ -155,7 +184,7 @@ def _check(L, code: int, ctx=None):
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
           keep_aat=False, refine_relax=None, multi_rhs=None, ruiz_sweeps=None,
-          time_proj=None, stream=None) -> OptsStruct:
+          time_proj=None, stream=None, allocator=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -182,6 +211,8 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
     if time_proj is not None:
         o.time_proj = int(bool(time_proj))
     o.stream = stream
+    if allocator is not None:
+        o.alloc, o.free = allocator
     return o
 
 
@@ -206,10 +237,22 @@ def _csr(A, keep: list) -> CSRStruct:
                      _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), int(dev))
 
 
-class Solver:
-    """One system A x = f split into row blocks; FP64 or FP32+refinement factors."""
+def _allocator(name):
+    if name in (None, "pool"):
+        return None
+    if name == "torch":
+        return torch_allocator()
+    raise ValueError(f"allocator must be 'pool' or 'torch', not {name!r}")
 
-    def __init__(self, A, block_ptr, perm=None, precision="fp64", layout="skyline", **kw):
+
+class Solver:
+    """One system A x = f split into row blocks; FP64 or FP32+refinement factors.
+
+    allocator: "pool" (default) takes device memory from the library's stream-ordered
+    pool; "torch" from torch's caching allocator on the context's stream."""
+
+    def __init__(self, A, block_ptr, perm=None, precision="fp64", layout="skyline",
+                 allocator=None, **kw):
         L = load()
         self._L = L
         keep: list = []
@@ -219,7 +262,9 @@ class Solver:
         self.block_ptr = _host(block_ptr, np.int64)
         self.K = len(self.block_ptr) - 1
         self.perm = None if perm is None else _host(perm, np.int32)
-        opts = _opts(L, precision, layout, stream=_torch_stream(self.on_device), **kw)
+        self._alloc = _allocator(allocator)  # kept alive with the context
+        opts = _opts(L, precision, layout, stream=_torch_stream(self.on_device),
+                     allocator=self._alloc, **kw)
         h = C.c_void_p()
         st = L.cimmino_setup(C.byref(csr), self.K,
                              None if self.perm is None else self.perm.ctypes.data,
@@ -363,7 +408,7 @@ class BatchSolver:
     """Many independent systems solved together (one launch per stage)."""
 
     def __init__(self, As: Sequence, block_ptrs: Sequence, perms: Optional[Sequence] = None,
-                 precision="fp32_refine", layout="skyline", **kw):
+                 precision="fp32_refine", layout="skyline", allocator=None, **kw):
         L = load()
         self._L = L
         keep: list = []
@@ -377,7 +422,9 @@ class BatchSolver:
                                                   for p in perms]
         parr = None if self._perms is None else (C.c_void_p * nsys)(
             *[None if p is None else p.ctypes.data for p in self._perms])
-        opts = _opts(L, precision, layout, stream=_torch_stream(bool(csrs[0].on_device)), **kw)
+        self._alloc = _allocator(allocator)
+        opts = _opts(L, precision, layout, stream=_torch_stream(bool(csrs[0].on_device)),
+                     allocator=self._alloc, **kw)
         h = C.c_void_p()
         st = L.cimmino_setup_batch(nsys, csrs, Ks.ctypes.data, parr, bparr, C.byref(opts),
                                    C.byref(h))

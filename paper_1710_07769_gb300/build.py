@@ -53,7 +53,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nv, *_flags(extra), "-c", os.path.join(SRC, src), "-o", obj]
+        # host-only C++ (the partitioner) runs on OpenMP threads, without contraction so
+        # that its floating-point decisions are the same on every host architecture
+        host = ["-Xcompiler", "-fopenmp,-ffp-contract=off"] if src.endswith(".cpp") else []
+        cmd = [nv, *_flags(extra), *host, "-c", os.path.join(SRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -64,7 +67,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"]
+    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lgomp", "-ldl", "-lrt",
+           "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

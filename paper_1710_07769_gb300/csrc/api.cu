@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,31 +28,102 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Stream-ordered pool of device memory per device, owned by the library: freed blocks stay
+// in the pool (release threshold: never) and serve the next context's allocations without a
+// cudaMalloc, the way a framework's caching allocator does.
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+
+cudaMemPool_t library_pool() {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kPoolDevices) fail(CIMMINO_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
+// Device memory of one context or one standalone call: the caller's allocator when
+// opts.alloc / opts.free are set, else the library pool, ordered on `stream`.
+struct Allocator {
+  cimmino_alloc_fn fa = nullptr;
+  cimmino_free_fn ff = nullptr;
+  void *user = nullptr;
+  cudaStream_t stream = nullptr;
+
+  void *get(size_t bytes) {
+    void *p = nullptr;
+    if (fa) {
+      p = fa(bytes, stream, user);
+      if (!p)
+        fail(CIMMINO_ENOMEM, "the caller's allocator returned NULL for " +
+                                 std::to_string(bytes) + " bytes");
+      return p;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(), stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(e == cudaErrorMemoryAllocation ? CIMMINO_ENOMEM : CIMMINO_ECUDA,
+           "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+               cudaGetErrorString(e));
+    }
+    return p;
+  }
+  void put(void *p, size_t bytes) {
+    if (!p) return;
+    if (ff)
+      ff(p, bytes, stream, user);
+    else
+      cudaFreeAsync(p, stream);
+  }
+};
+
+// The allocator of the API call in progress on this host thread (set by AllocScope).
+thread_local Allocator *t_alloc = nullptr;
+struct AllocScope {
+  Allocator *prev;
+  explicit AllocScope(Allocator *a) : prev(t_alloc) { t_alloc = a; }
+  ~AllocScope() { t_alloc = prev; }
+  AllocScope(const AllocScope &) = delete;
+  AllocScope &operator=(const AllocScope &) = delete;
+};
+
+// A device buffer from the allocator in scope at alloc() time, returned to the same
+// allocator (which must outlive the buffer) on release.
 template <typename T>
 struct DBuf {
   T *p = nullptr;
   size_t n = 0;
+  Allocator *a = nullptr;
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
   ~DBuf() { release(); }
   void alloc(size_t count) {
     release();
+    if (!t_alloc) fail(CIMMINO_ECUDA, "internal: device allocation outside an allocator scope");
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      fail(e == cudaErrorMemoryAllocation ? CIMMINO_ENOMEM : CIMMINO_ECUDA,
-           "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
-               cudaGetErrorString(e));
-    }
+    p = static_cast<T *>(t_alloc->get(count * sizeof(T)));
+    a = t_alloc;
     n = count;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) a->put(p, n * sizeof(T));
     p = nullptr;
     n = 0;
+    a = nullptr;
   }
 };
 
@@ -104,7 +176,18 @@ __global__ void k_cols_to_interleaved(const double *__restrict__ v, int64_t N, i
 
 }  // namespace
 
+// The context's own stream, destroyed after every buffer of the context has been returned
+// (members are destroyed in reverse order, so this one is declared first).
+struct OwnedStream {
+  cudaStream_t s = nullptr;
+  ~OwnedStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 struct cimmino_ctx {
+  OwnedStream owned;
+  Allocator mem;  // declared before every DBuf member: outlives them
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -161,7 +244,6 @@ struct cimmino_ctx {
   ~cimmino_ctx() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : pev) cudaEventDestroy(e);
-    if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -184,6 +266,9 @@ void opts_default(cimmino_opts *o) {
   o->ruiz_sweeps = 0;
   o->time_proj = 0;
   o->stream = nullptr;
+  o->alloc = nullptr;
+  o->free = nullptr;
+  o->alloc_user = nullptr;
 }
 
 void check_opts(const cimmino_opts &o) {
@@ -200,6 +285,8 @@ void check_opts(const cimmino_opts &o) {
   if (o.ruiz_sweeps < 0 || o.ruiz_sweeps > 100)
     fail(CIMMINO_EINVAL, "opts.ruiz_sweeps not in [0,100]");
   if (o.time_proj != 0 && o.time_proj != 1) fail(CIMMINO_EINVAL, "opts.time_proj must be 0 or 1");
+  if ((o.alloc == nullptr) != (o.free == nullptr))
+    fail(CIMMINO_EINVAL, "opts.alloc and opts.free must be set together");
 }
 
 // One NVTX range per stage (header-only NVTX 3: a no-op unless a profiler attaches), so
@@ -520,19 +607,24 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   // r_I r_K^2 of the tiles (I, K) below them, and the trailing products 2 r_I r_J r_K
   // (r_I^2 r_K on the symmetric diagonal tiles J = I) for K < J <= I inside the envelope.
   c->factor_flops = 0.0;
-  for (const auto &B : c->hblk) {
+  std::vector<double> blk_flops(nblk, 0.0);
+  for (int32_t b = 0; b < nblk; ++b) {
+    const BlockDesc &B = c->hblk[b];
     auto rows = [&](int32_t I) { return (double)std::min(kTile, B.m - I * kTile); };
+    double f = 0.0;
     for (int32_t K = 0; K < B.nt; ++K) {
       const double rK = rows(K);
-      c->factor_flops += rK * rK * rK / 3.0;
+      f += rK * rK * rK / 3.0;
       for (int32_t I = K + 1; I < B.nt; ++I) {
         if (c->htrow[B.trow0 + I].j0 > K) continue;
         const double rI = rows(I);
-        c->factor_flops += rI * rK * rK + rI * rI * rK;  // solve of (I, K), update of (I, I)
+        f += rI * rK * rK + rI * rI * rK;  // solve of (I, K), update of (I, I)
         for (int32_t J = K + 1; J < I; ++J)
-          if (c->htrow[B.trow0 + J].j0 <= K) c->factor_flops += 2.0 * rI * rows(J) * rK;
+          if (c->htrow[B.trow0 + J].j0 <= K) f += 2.0 * rI * rows(J) * rK;
       }
     }
+    blk_flops[b] = f;
+    c->factor_flops += f;
   }
   c->t_setup_ms = tsetup.stop_ms(s);
 
@@ -540,8 +632,12 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   // ---- batched Cholesky of all G_i
   Timer tfac;
   tfac.start(s);
+  // one CTA per block, launched in order of decreasing work (longest first): the blocks
+  // that take longest start in the first wave and the short ones fill in behind them
   std::vector<int32_t> hlist(nblk);
   for (int32_t b = 0; b < nblk; ++b) hlist[b] = b;
+  std::stable_sort(hlist.begin(), hlist.end(),
+                   [&](int32_t x, int32_t y) { return blk_flops[x] > blk_flops[y]; });
   DBuf<int32_t> blist, pfail;
   DBuf<double> pmin;
   blist.alloc(nblk);
@@ -549,7 +645,6 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   pmin.alloc(nblk);
   h2d(blist.p, hlist.data(), nblk, s);
   void *fac = fp64 ? (void *)c->fac64.p : (void *)c->fac32.p;
-  void *dinv = fp64 ? (void *)c->dinv64.p : (void *)c->dinv32.p;
   launch_gram_scatter(c->blk.p, blist.p, nblk, c->trow.p, c->brp.p, c->bci.p, c->bcv.p, fac,
                       fp64, s);
   if (!fp64) {
@@ -559,7 +654,8 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   Timer tchol;
   tchol.start(s);
   if (fp64) {
-    launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, fac, dinv, 1, pmin.p, pfail.p, s);
+    launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, c->fac64.p, c->dinv64.p, pmin.p,
+                    pfail.p, s);
   } else {
     launch_cholesky_tc(c->blk.p, blist.p, nblk, c->trow.p, c->fac32.p, c->dinv32.p, pmin.p,
                        pfail.p, c->err_flag.p, s);
@@ -605,7 +701,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
       launch_gram_scatter(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->brp.p, c->bci.p,
                           c->bcv.p, c->fac64.p, 1, s);
       launch_cholesky(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
-                      c->dinv64.p, 1, pmin.p, pfail.p, s);
+                      c->dinv64.p, pmin.p, pfail.p, s);
       c->setup_launches += 2;
       d2h(hfail.data(), pfail.p, nblk, s);
       CUDA_TRY(cudaStreamSynchronize(s));
@@ -746,6 +842,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
 // ------------------------------------------------------------------ solve
 void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   if (c->nrhs == nrhs) return;
+  AllocScope scope(&c->mem);
   const int64_t N = c->N;
   const int64_t V = N * nrhs;
   c->lane.alloc((size_t)c->nsys * nrhs);
@@ -1056,9 +1153,15 @@ int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
     if (c->opts.stream) {
       c->stream = static_cast<cudaStream_t>(c->opts.stream);
     } else {
-      CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->owned.s, cudaStreamNonBlocking));
+      c->stream = c->owned.s;
       c->own_stream = true;
     }
+    c->mem.fa = c->opts.alloc;
+    c->mem.ff = c->opts.free;
+    c->mem.user = c->opts.alloc_user;
+    c->mem.stream = c->stream;
+    AllocScope scope(&c->mem);
     setup_impl(c, nsys, A, K, perm, block_ptr);
   } catch (const Error &e) {
     int code = set_error(nullptr, e);
@@ -1186,10 +1289,14 @@ int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word) {
     return CIMMINO_EINVAL;
   }
   try {
+    OwnedStream os;  // destroyed after the buffer below has been returned
+    CUDA_TRY(cudaStreamCreateWithFlags(&os.s, cudaStreamNonBlocking));
+    const cudaStream_t s = os.s;
+    Allocator mem;
+    mem.stream = s;
+    AllocScope scope(&mem);
     DBuf<int32_t> err;
     err.alloc(1);
-    cudaStream_t s = nullptr;
-    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaError_t e = cudaMemsetAsync(err.p, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) {
       launch_wait_selftest((uint64_t)limit_us * 1000ull, err.p, s);
@@ -1197,7 +1304,6 @@ int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word) {
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(err_word, err.p, sizeof(int32_t), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
     CUDA_TRY(e);
     if (*err_word) {
       g_last_error = "the self-test wait ran out of its budget (error word " +
@@ -1444,6 +1550,9 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
     const int64_t N = A->n, NNZ = A->nnz;
     if (N <= 0 || NNZ < 0 || !A->row_ptr || !A->col_idx || (NNZ > 0 && !A->val))
       fail(CIMMINO_EINVAL, "bad CSR header");
+    Allocator mem;  // the library pool, ordered on the caller's stream
+    mem.stream = s;
+    AllocScope scope(&mem);
     DBuf<int64_t> rp, cp, work, tmp, cnt, crp;
     DBuf<int32_t> ci, ri, ovf, flag, cci;
     DBuf<double> va, cv, ccv;

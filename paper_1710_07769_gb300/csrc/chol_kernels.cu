@@ -1,4 +1,4 @@
-// Batched Cholesky G_i = L_i L_i^T of the Gram blocks, in place on the tiled
+// Batched Cholesky G_i = L_i L_i^T of the Gram blocks in FP64, in place on the tiled
 // factor layout (tile rows J0(I)..I, T x T row-major tiles).  One CTA per block,
 // right-looking over tile columns K:
 //   1. factor the diagonal tile (unblocked, in shared memory), record the pivots;
@@ -11,8 +11,14 @@
 // diagonal tiles keep L_II and dinv keeps inv(L_II).
 // Pivot monitoring: min_j of the pivots L_jj^2 (G_jj = 1 after the unit row
 // scaling) and a failure flag for a non-positive or non-finite pivot; a failed
-// pivot is replaced by 1 so that the block finishes without NaNs and can be
-// refactored in FP64.
+// pivot is replaced by 1 so that the block finishes without NaNs.
+//
+// GB300's FP64 pipe (about 2 FMA lanes per cycle per SM) bounds this kernel, so every
+// tile product is split into 16 x 16 output units, one warp per unit, and the units skip
+// the work that is zero by structure: the symmetric update of a diagonal tile computes
+// its 10 lower units only, and products with the triangular inv(L_KK) stop the k loop
+// where the triangle ends (k <= column for G inv^T, k <= row for inv L).  Work is then
+// close to the algorithmic count (plus the N transform).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,65 +30,95 @@ namespace {
 
 constexpr int T = kTile;
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int LD = T + 2;   // k-major operand rows (doubles): 16-byte aligned, staggered banks
+constexpr int LDS = T + 1;  // padded row-major diagonal tile
 
-template <typename W>
-struct Pad {
-  static constexpr int v = 16 / sizeof(W);  // keeps k-major rows 16-byte aligned
-};
-
-template <typename W>
-__device__ __forceinline__ W *tile_ptr(W *fac, const TileRow &tr, int J) {
+__device__ __forceinline__ double *tile_ptr(double *fac, const TileRow &tr, int J) {
   return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
 }
 
 // Load a row-major global tile into k-major shared storage At[k][r] = tile(r, k).
-template <typename W>
-__device__ __forceinline__ void load_kmajor(const W *__restrict__ g, W *At) {
-  constexpr int LD = T + Pad<W>::v;
+__device__ __forceinline__ void load_kmajor(const double *__restrict__ g, double *At) {
   for (int e = threadIdx.x; e < T * T; e += kThreads) {
-    int r = e / T, k = e % T;
+    const int r = e / T, k = e % T;
     At[k * LD + r] = g[e];
   }
 }
-
-// acc(r, c) for the thread's 4 x 4 block: sum_k At[k][r] * Bt[k][c]
-template <typename W>
-__device__ __forceinline__ void mma_4x4(const W *At, const W *Bt, W acc[4][4]) {
-  constexpr int LD = T + Pad<W>::v;
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
-#pragma unroll 8
-  for (int k = 0; k < T; ++k) {
-    W a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = At[k * LD + tr * 4 + i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) b[j] = Bt[k * LD + tc * 4 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+// Load a row-major global tile into row-major shared storage Bt[k][c] = tile(k, c).
+__device__ __forceinline__ void load_rowmajor(const double *__restrict__ g, double *Bt) {
+  for (int e = threadIdx.x; e < T * T / 2; e += kThreads) {
+    const int k = e / (T / 2), c = 2 * (e % (T / 2));
+    *reinterpret_cast<double2 *>(Bt + k * LD + c) = *reinterpret_cast<const double2 *>(g + k * T + c);
   }
 }
 
-template <typename W>
+// Output unit (R, C) of a 16 x 16 grid of a tile: lane (lr, lc) = (lane / 4, lane % 4) owns
+// rows 16R + 2lr, +1 and columns 16C + 4lc .. +3.  acc = sum_{k < kend} At[k][r] Bt[k][c].
+__device__ __forceinline__ void unit_product(const double *At, const double *Bt, int R, int C,
+                                             int kend, double (&acc)[2][4]) {
+  const int lane = threadIdx.x & 31, lr = lane >> 2, lc = lane & 3;
+  const double *a = At + 16 * R + 2 * lr;
+  const double *b = Bt + 16 * C + 4 * lc;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < kend; ++k) {
+    const double2 av = *reinterpret_cast<const double2 *>(a + k * LD);
+    const double2 b0 = *reinterpret_cast<const double2 *>(b + k * LD);
+    const double2 b1 = *reinterpret_cast<const double2 *>(b + k * LD + 2);
+    const double ar[2] = {av.x, av.y}, br[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(ar[i], br[j], acc[i][j]);
+  }
+}
+
+// The 10 lower units (R >= C) of a symmetric tile, in the order R = 0..3, C = 0..R.
+__device__ __forceinline__ void lower_unit(int u, int &R, int &C) {
+  R = u >= 6 ? 3 : u >= 3 ? 2 : u >= 1 ? 1 : 0;
+  C = u - R * (R + 1) / 2;
+}
+
+// out(r, c) = acc (mode 0) or out(r, c) -= acc (mode 1) for the lane's elements of unit (R, C)
+// of a row-major global tile.
+__device__ __forceinline__ void unit_store(double *out, int R, int C, const double (&acc)[2][4],
+                                           bool subtract) {
+  const int lane = threadIdx.x & 31, lr = lane >> 2, lc = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double2 *p = reinterpret_cast<double2 *>(out + (16 * R + 2 * lr + i) * T + 16 * C + 4 * lc);
+    if (subtract) {
+      const double2 x0 = p[0], x1 = p[1];
+      p[0] = make_double2(x0.x - acc[i][0], x0.y - acc[i][1]);
+      p[1] = make_double2(x1.x - acc[i][2], x1.y - acc[i][3]);
+    } else {
+      p[0] = make_double2(acc[i][0], acc[i][1]);
+      p[1] = make_double2(acc[i][2], acc[i][3]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_cholesky(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
-               const TileRow *__restrict__ trow, W *__restrict__ fac, W *__restrict__ dinv,
-               double *__restrict__ pivmin, int32_t *__restrict__ pivfail) {
-  constexpr int LDS = T + 1;            // padded row-major diagonal tile
-  constexpr int LD = T + Pad<W>::v;     // k-major operand tiles
+               const TileRow *__restrict__ trow, double *__restrict__ fac,
+               double *__restrict__ dinv, double *__restrict__ pivmin,
+               int32_t *__restrict__ pivfail) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  W *At = reinterpret_cast<W *>(smem_raw);  // [T][LD]
-  W *Bt = At + T * LD;                      // [T][LD]
-  W *S = Bt + T * LD;                       // [T][LDS]
-  W *Di = S + T * LDS;                      // [T][LDS]
+  double *At = reinterpret_cast<double *>(smem_raw);  // [T][LD]
+  double *Bt = At + T * LD;                            // [T][LD]
+  double *S = Bt + T * LD;                             // [T][LDS]
+  double *Di = S + T * LDS;                            // [T][LDS]
   __shared__ double s_pmin;
   __shared__ int s_fail;
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
   const TileRow *tr = trow + B.trow0;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int tr4 = tid / 16, tc4 = tid % 16;
   if (tid == 0) {
     s_pmin = 1e300;
@@ -92,77 +128,88 @@ __global__ void __launch_bounds__(kThreads)
 
   for (int K = 0; K < B.nt; ++K) {
     const TileRow TK = tr[K];
-    W *gKK = tile_ptr(fac, TK, K);
-    // ---- 1. diagonal tile: unblocked right-looking Cholesky in shared memory
+    double *gKK = tile_ptr(fac, TK, K);
+    // ---- 1. diagonal tile, right-looking with the column scaling deferred: step j
+    // subtracts S_ij S_kj / d_j from the trailing triangle (one barrier per column);
+    // afterwards L_jj = sqrt(d_j) and L_ij = S_ij / sqrt(d_j)
     for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
     __syncthreads();
     for (int j = 0; j < T; ++j) {
-      if (tid == 0) {
-        W dj = S[j * LDS + j];
-        if (K * T + j < B.m) s_pmin = fmin(s_pmin, (double)dj);
-        if (!(dj > W(0)) || !isfinite((double)dj)) {
-          s_fail = 1;
-          dj = W(1);
-        }
-        S[j * LDS + j] = sqrt(dj);
+      double dj = S[j * LDS + j];
+      if (tid == 0 && K * T + j < B.m) s_pmin = fmin(s_pmin, dj);
+      if (!(dj > 0.0) || !isfinite(dj)) {
+        if (tid == 0) s_fail = 1;
+        dj = 1.0;
       }
-      __syncthreads();
-      const W ljj = S[j * LDS + j];
-      for (int i = j + 1 + tid; i < T; i += kThreads) S[i * LDS + j] = S[i * LDS + j] / ljj;
-      __syncthreads();
-      const int w = T - j - 1;
-      for (int e = tid; e < w * w; e += kThreads) {
-        int i = j + 1 + e / w, k = j + 1 + e % w;
-        if (k <= i) S[i * LDS + k] = fma(-S[i * LDS + j], S[k * LDS + j], S[i * LDS + k]);
+      const double inv = 1.0 / dj;
+      for (int i = j + 1 + tr4; i < T; i += 16) {
+        const double t = S[i * LDS + j] * inv;
+        for (int k = j + 1 + tc4; k <= i; k += 16) S[i * LDS + k] = fma(-t, S[k * LDS + j], S[i * LDS + k]);
       }
       __syncthreads();
     }
-    // ---- 2. Di = inv(L_KK), column by column (forward substitution on unit vectors)
-    if (tid < T) {
-      const int c = tid;
-      for (int i = 0; i < c; ++i) Di[i * LDS + c] = W(0);
-      Di[c * LDS + c] = W(1) / S[c * LDS + c];
-      for (int i = c + 1; i < T; ++i) {
-        W s = W(0);
-        for (int k = c; k < i; ++k) s = fma(S[i * LDS + k], Di[k * LDS + c], s);
-        Di[i * LDS + c] = -s / S[i * LDS + i];
-      }
+    for (int e = tid; e < T * T; e += kThreads) {
+      const int i = e / T, j = e % T;
+      if (j > i) continue;
+      double dj = S[j * LDS + j];
+      if (!(dj > 0.0) || !isfinite(dj)) dj = 1.0;
+      Di[i * LDS + j] = i == j ? sqrt(dj) : S[i * LDS + j] / sqrt(dj);  // L_KK, staged in Di
     }
     __syncthreads();
-    // write L_KK (upper part zeroed) and inv(L_KK)
-    W *dK = dinv + B.dinv_off + (int64_t)K * T * T;
     for (int e = tid; e < T * T; e += kThreads) {
-      int r = e / T, c = e % T;
-      gKK[e] = c <= r ? S[r * LDS + c] : W(0);
-      dK[e] = c <= r ? Di[r * LDS + c] : W(0);
+      const int i = e / T, j = e % T;
+      S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.0;
+    }
+    __syncthreads();
+    // ---- 2. inv(L_KK) by rows: Di_ic = (delta_ic - sum_{c<=k<i} L_ik Di_kc) / L_ii; row i
+    // depends on rows < i only, so all columns c of a row run in parallel (4 threads per
+    // column split the sum, fixed-order shuffle reduction)
+    {
+      const int c = tid >> 2, q = tid & 3;
+      for (int i = 0; i < T; ++i) {
+        double acc = 0.0;
+        if (c < i)
+          for (int k = c + q; k < i; k += 4) acc = fma(S[i * LDS + k], Di[k * LDS + c], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (q == 0) {
+          const double lii = S[i * LDS + i];
+          Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.0 / lii : 0.0);
+        }
+        __syncthreads();
+      }
+    }
+    // write L_KK (upper part zeroed) and inv(L_KK)
+    double *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+    for (int e = tid; e < T * T; e += kThreads) {
+      const int r = e / T, c = e % T;
+      gKK[e] = c <= r ? S[r * LDS + c] : 0.0;
+      dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
     }
     // Row K is final now: store N_KJ = inv(L_KK) L_KJ in place of L_KJ (J < K), so that
-    // the solves see L = diag(L_II) (I + N) and their sequential chains need no
-    // diagonal solve.  At[k][r] = Di(r, k), Bt[k][c] = L_KJ(k, c).
+    // the solves see L = diag(L_II) (I + N) and their sequential chains need no diagonal
+    // solve.  At[k][r] = Di(r, k) (lower: unit row block R needs k < 16 (R + 1)).
     for (int e = tid; e < T * T; e += kThreads) {
-      int k = e / T, r = e % T;
+      const int k = e / T, r = e % T;
       At[k * LD + r] = Di[r * LDS + k];
     }
     for (int J = TK.j0; J < K; ++J) {
-      W *gKJ = tile_ptr(fac, TK, J);
+      double *gKJ = tile_ptr(fac, TK, J);
       __syncthreads();  // At ready / previous use of Bt finished
-      for (int e = tid; e < T * T; e += kThreads) Bt[(e / T) * LD + (e % T)] = gKJ[e];
+      load_rowmajor(gKJ, Bt);
       __syncthreads();
-      W acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = W(0);
-      mma_4x4(At, Bt, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) gKJ[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+      for (int u = warp; u < 16; u += kWarps) {
+        const int R = u >> 2, C = u & 3;
+        double acc[2][4];
+        unit_product(At, Bt, R, C, 16 * (R + 1), acc);
+        unit_store(gKJ, R, C, acc, false);
+      }
     }
     __syncthreads();
-    // Bt[k][c] = Di(c, k) for the TRSM below
+    // Bt[k][c] = Di(c, k) for the TRSM below (upper triangle: unit column block C needs
+    // k < 16 (C + 1))
     for (int e = tid; e < T * T; e += kThreads) {
-      int k = e / T, c = e % T;
+      const int k = e / T, c = e % T;
       Bt[k * LD + c] = Di[c * LDS + k];
     }
     __syncthreads();
@@ -170,22 +217,19 @@ __global__ void __launch_bounds__(kThreads)
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
-      W *gIK = tile_ptr(fac, TI, K);
+      double *gIK = tile_ptr(fac, TI, K);
       load_kmajor(gIK, At);
       __syncthreads();
-      W acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = W(0);
-      mma_4x4(At, Bt, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) gIK[(tr4 * 4 + i) * T + tc4 * 4 + j] = acc[i][j];
+      for (int u = warp; u < 16; u += kWarps) {
+        const int R = u >> 2, C = u & 3;
+        double acc[2][4];
+        unit_product(At, Bt, R, C, 16 * (C + 1), acc);
+        unit_store(gIK, R, C, acc, false);
+      }
       __syncthreads();
     }
-    // ---- 4. trailing update G_IJ -= L_IK L_JK^T
+    // ---- 4. trailing update G_IJ -= L_IK L_JK^T; a diagonal tile (J = I) is symmetric and
+    // only its lower units are updated (the upper triangle of G_II is never read)
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
@@ -196,20 +240,23 @@ __global__ void __launch_bounds__(kThreads)
         __syncthreads();  // previous use of Bt finished
         load_kmajor(tile_ptr(fac, TJ, K), Bt);
         __syncthreads();
-        W *gIJ = tile_ptr(fac, TI, J);
-        W acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = W(0);
-        mma_4x4(At, Bt, acc);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            W *p = gIJ + (tr4 * 4 + i) * T + tc4 * 4 + j;
-            *p = *p - acc[i][j];
+        double *gIJ = tile_ptr(fac, TI, J);
+        if (J < I) {
+          for (int u = warp; u < 16; u += kWarps) {
+            const int R = u >> 2, C = u & 3;
+            double acc[2][4];
+            unit_product(At, Bt, R, C, T, acc);
+            unit_store(gIJ, R, C, acc, true);
           }
+        } else {
+          for (int u = warp; u < 10; u += kWarps) {
+            int R, C;
+            lower_unit(u, R, C);
+            double acc[2][4];
+            unit_product(At, Bt, R, C, T, acc);
+            unit_store(gIJ, R, C, acc, true);
+          }
+        }
       }
       __syncthreads();
     }
@@ -329,30 +376,17 @@ __global__ void __launch_bounds__(kThreads)
                            f.dinvT32, reinterpret_cast<float *>(sm));
 }
 
-template <typename W>
-int chol_smem() {
-  return (int)(sizeof(W) * (2 * T * (T + Pad<W>::v) + 2 * T * (T + 1)));
-}
+constexpr int kCholSmem = (int)sizeof(double) * (2 * T * LD + 2 * T * LDS);
 
 }  // namespace
 
 void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                     const TileRow *trow, void *fac, void *dinv, int prec64, double *pivmin,
+                     const TileRow *trow, double *fac, double *dinv, double *pivmin,
                      int32_t *pivfail, cudaStream_t s) {
   if (nlist <= 0) return;
-  if (prec64) {
-    int sm = chol_smem<double>();
-    cudaFuncSetAttribute(k_cholesky<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    k_cholesky<double><<<(unsigned)nlist, kThreads, sm, s>>>(
-        blk, blist, trow, static_cast<double *>(fac), static_cast<double *>(dinv), pivmin,
-        pivfail);
-  } else {
-    int sm = chol_smem<float>();
-    cudaFuncSetAttribute(k_cholesky<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    k_cholesky<float><<<(unsigned)nlist, kThreads, sm, s>>>(
-        blk, blist, trow, static_cast<float *>(fac), static_cast<float *>(dinv), pivmin,
-        pivfail);
-  }
+  cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
+  k_cholesky<<<(unsigned)nlist, kThreads, kCholSmem, s>>>(blk, blist, trow, fac, dinv, pivmin,
+                                                         pivfail);
 }
 
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,

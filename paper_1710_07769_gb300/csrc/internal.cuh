@@ -217,8 +217,9 @@ void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlis
 // chol_kernels.cu
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
                              const TileRow *trowT, const FactorPtrs &f, cudaStream_t s);
+// FP64 blocks (FP64 precision and the FP64 refactorisation of FP32 blocks)
 void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                     const TileRow *trow, void *fac, void *dinv, int prec64, double *pivmin,
+                     const TileRow *trow, double *fac, double *dinv, double *pivmin,
                      int32_t *pivfail, cudaStream_t s);
 
 // solve_kernels.cu

@@ -12,7 +12,15 @@
 //   satisfies the cap.  Inside every part the rows are ordered by reverse Cuthill-McKee
 //   on the part's subgraph (the order inside a block row is arbitrary, Section 2.2), which
 //   keeps the envelope of the Gram blocks, and hence the skyline factors, small.
+//
+// Host threads (OpenMP) split the per-vertex work of every phase; the result does not
+// depend on the thread count: parallel loops only compute per-vertex proposals from the
+// state of the previous round, and every decision that depends on other decisions (which
+// matches stand, which moves are applied) is taken in a fixed order.
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <algorithm>
 #include <cmath>
@@ -43,18 +51,22 @@ Graph build_rip(int64_t n, const int64_t *crp, const int32_t *cci, const double 
   Graph g;
   g.n = (int32_t)n;
   std::vector<double> d(n, 1.0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i)
     for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
       if (cci[q] == i && ccv[q] > 0) d[i] = std::sqrt(ccv[q]);
   g.xadj.assign(n + 1, 0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     int64_t c = 0;
     for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
       if (cci[q] != i && ccv[q] != 0.0) ++c;
-    g.xadj[i + 1] = g.xadj[i] + c;
+    g.xadj[i + 1] = c;
   }
+  for (int64_t i = 0; i < n; ++i) g.xadj[i + 1] += g.xadj[i];
   g.adj.resize(g.xadj[n]);
   g.w.resize(g.xadj[n]);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     int64_t o = g.xadj[i];
     for (int64_t q = crp[i]; q < crp[i + 1]; ++q)
@@ -68,73 +80,126 @@ Graph build_rip(int64_t n, const int64_t *crp, const int32_t *cci, const double 
   return g;
 }
 
-// heavy-edge matching; cmap[v] = coarse vertex of v
-Graph coarsen(const Graph &g, int32_t maxvw, std::mt19937_64 &rng, std::vector<int32_t> &cmap) {
+// Tie-break of equal edge weights in the matching: a hash of the (unordered) edge and the
+// level's seed, so that the choice is random-like but the same for both end points.
+inline uint64_t edge_hash(uint64_t a, uint64_t b, uint64_t seed) {
+  if (a > b) std::swap(a, b);
+  uint64_t x = (a * 0x9E3779B97F4A7C15ull) ^ (b + 0x632BE59BD9B4E019ull) ^ seed;
+  x ^= x >> 31;
+  x *= 0xBF58476D1CE4E5B9ull;
+  x ^= x >> 29;
+  return x;
+}
+
+// Heavy-edge matching by rounds of mutual proposals: every unmatched vertex proposes to its
+// heaviest unmatched neighbour that keeps the coarse weight under maxvw (ties broken by the
+// edge hash); mutual proposals are matched.  cmap[v] = coarse vertex of v.
+Graph coarsen(const Graph &g, int32_t maxvw, uint64_t seed, std::vector<int32_t> &cmap) {
   const int32_t n = g.n;
-  std::vector<int32_t> order(n), match(n, -1);
-  std::iota(order.begin(), order.end(), 0);
-  std::shuffle(order.begin(), order.end(), rng);
-  for (int32_t v : order) {
-    if (match[v] != -1) continue;
-    int32_t best = -1;
-    double bw = -1.0;
-    for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
-      const int32_t u = g.adj[q];
-      if (match[u] == -1 && u != v && g.vw[u] + g.vw[v] <= maxvw && g.w[q] > bw) {
-        bw = g.w[q];
-        best = u;
+  std::vector<int32_t> match(n, -1), prop(n, -1);
+  for (int round = 0; round < 6; ++round) {
+    int64_t open = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(+ : open)
+    for (int32_t v = 0; v < n; ++v) {
+      prop[v] = -1;
+      if (match[v] != -1) continue;
+      int32_t best = -1;
+      double bw = -1.0;
+      uint64_t bh = 0;
+      for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+        const int32_t u = g.adj[q];
+        if (g.w[q] < bw || match[u] != -1 || u == v || g.vw[u] + g.vw[v] > maxvw) continue;
+        if (g.w[q] > bw) {
+          bw = g.w[q];
+          bh = edge_hash((uint64_t)u, (uint64_t)v, seed);
+          best = u;
+        } else {  // equal weights: the edge hash decides
+          const uint64_t h = edge_hash((uint64_t)u, (uint64_t)v, seed);
+          if (h > bh) {
+            bh = h;
+            best = u;
+          }
+        }
       }
+      prop[v] = best;
+      open += best >= 0;
     }
-    if (best >= 0) {
-      match[v] = best;
-      match[best] = v;
-    } else {
-      match[v] = v;
+    if (!open) break;
+#pragma omp parallel for schedule(static)
+    for (int32_t v = 0; v < n; ++v) {
+      const int32_t u = prop[v];
+      if (u >= 0 && prop[u] == v) match[v] = u;  // both ends write the same pair
     }
   }
   cmap.assign(n, -1);
   int32_t nc = 0;
-  for (int32_t v = 0; v < n; ++v)
+  std::vector<int32_t> rep;
+  rep.reserve(n / 2 + 1);
+  for (int32_t v = 0; v < n; ++v) {
+    if (match[v] == -1) match[v] = v;
     if (cmap[v] == -1) {
       cmap[v] = nc;
       cmap[match[v]] = nc;
+      rep.push_back(v);
       ++nc;
     }
+  }
   Graph c;
   c.n = nc;
   c.vw.assign(nc, 0);
-  std::vector<int32_t> rep(nc, -1);
-  for (int32_t v = 0; v < n; ++v) {
-    c.vw[cmap[v]] += g.vw[v];
-    if (rep[cmap[v]] == -1) rep[cmap[v]] = v;
+#pragma omp parallel for schedule(static)
+  for (int32_t cv = 0; cv < nc; ++cv) {
+    const int32_t a = rep[cv], b = match[a];
+    c.vw[cv] = g.vw[a] + (b != a ? g.vw[b] : 0);
+  }
+  // coarse adjacency: chunks of coarse vertices in parallel into per-chunk buffers (the
+  // edge order of a coarse vertex is that of the sequential program), then concatenated
+  constexpr int32_t kChunk = 8192;
+  const int32_t nchunk = (nc + kChunk - 1) / kChunk;
+  std::vector<std::vector<int32_t>> cadj(nchunk);
+  std::vector<std::vector<double>> cw(nchunk);
+  std::vector<int64_t> deg(nc, 0);
+#pragma omp parallel
+  {
+    std::vector<int32_t> mark(nc, -1), list;
+    std::vector<double> acc(nc, 0.0);
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t ch = 0; ch < nchunk; ++ch) {
+      const int32_t c0 = ch * kChunk, c1 = std::min(nc, c0 + kChunk);
+      for (int32_t cv = c0; cv < c1; ++cv) {
+        list.clear();
+        const int32_t a = rep[cv], b = match[a];
+        auto gather = [&](int32_t v) {
+          for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+            const int32_t cu = cmap[g.adj[q]];
+            if (cu == cv) continue;
+            if (mark[cu] != cv) {
+              mark[cu] = cv;
+              acc[cu] = 0.0;
+              list.push_back(cu);
+            }
+            acc[cu] += g.w[q];
+          }
+        };
+        gather(a);
+        if (b != a) gather(b);  // an unmatched vertex (b == a) has no partner
+        for (int32_t cu : list) {
+          cadj[ch].push_back(cu);
+          cw[ch].push_back(acc[cu]);
+        }
+        deg[cv] = (int64_t)list.size();
+      }
+    }
   }
   c.xadj.assign(nc + 1, 0);
-  c.adj.reserve(g.adj.size());
-  c.w.reserve(g.adj.size());
-  std::vector<int32_t> mark(nc, -1), list;
-  std::vector<double> acc(nc, 0.0);
-  for (int32_t cv = 0; cv < nc; ++cv) {
-    list.clear();
-    const int32_t a = rep[cv], b = match[a];
-    auto gather = [&](int32_t v) {
-      for (int64_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
-        const int32_t cu = cmap[g.adj[q]];
-        if (cu == cv) continue;
-        if (mark[cu] != cv) {
-          mark[cu] = cv;
-          acc[cu] = 0.0;
-          list.push_back(cu);
-        }
-        acc[cu] += g.w[q];
-      }
-    };
-    gather(a);
-    if (b != a) gather(b);  // an unmatched vertex (b == a) has no partner
-    for (int32_t cu : list) {
-      c.adj.push_back(cu);
-      c.w.push_back(acc[cu]);
-    }
-    c.xadj[cv + 1] = (int64_t)c.adj.size();
+  for (int32_t cv = 0; cv < nc; ++cv) c.xadj[cv + 1] = c.xadj[cv] + deg[cv];
+  c.adj.resize(c.xadj[nc]);
+  c.w.resize(c.xadj[nc]);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t ch = 0; ch < nchunk; ++ch) {
+    const int64_t o = c.xadj[(int64_t)ch * kChunk];
+    std::copy(cadj[ch].begin(), cadj[ch].end(), c.adj.begin() + o);
+    std::copy(cw[ch].begin(), cw[ch].end(), c.w.begin() + o);
   }
   return c;
 }
@@ -249,8 +314,11 @@ void bisect(const Graph &g, const std::vector<int32_t> &vs, double target0, int3
   }
 }
 
+// Parts k0 .. k0 + K - 1 of the vertex subset vs.  The two halves touch disjoint vertices
+// and draw from generators of their own (seeded by the part range), so they run as
+// independent tasks and the result does not depend on the schedule.
 void recursive_bisection(const Graph &g, const std::vector<int32_t> &vs, int32_t k0, int32_t K,
-                         std::vector<int32_t> &part, std::mt19937_64 &rng) {
+                         std::vector<int32_t> &part, uint64_t seed) {
   if (K <= 1 || vs.empty()) {
     for (int32_t v : vs) part[v] = k0;
     return;
@@ -258,54 +326,74 @@ void recursive_bisection(const Graph &g, const std::vector<int32_t> &vs, int32_t
   const int32_t K1 = K / 2;
   double w = 0;
   for (int32_t v : vs) w += g.vw[v];
+  std::mt19937_64 rng(seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(k0 + 1)) ^ (uint64_t)K << 40);
   bisect(g, vs, w * K1 / K, k0, k0 + K1, part, rng);
   std::vector<int32_t> a, b;
   for (int32_t v : vs) (part[v] == k0 ? a : b).push_back(v);
-  recursive_bisection(g, a, k0, K1, part, rng);
-  recursive_bisection(g, b, k0 + K1, K - K1, part, rng);
+#pragma omp task shared(g, part) firstprivate(a) if (a.size() > 4096)
+  recursive_bisection(g, a, k0, K1, part, seed);
+#pragma omp task shared(g, part) firstprivate(b) if (b.size() > 4096)
+  recursive_bisection(g, b, k0 + K1, K - K1, part, seed);
+#pragma omp taskwait
 }
 
-// balance-constrained greedy k-way refinement of the boundary
+// Balance-constrained greedy k-way refinement of the boundary.  Each pass: every vertex
+// proposes its best move (largest gain in edge weight kept inside its part) from the current
+// assignment, in parallel; then the proposals are applied in vertex order, each after its
+// gain is recomputed against the assignment as it stands and the cap is checked.
 void refine_kway(const Graph &g, std::vector<int32_t> &part, int32_t K, double cap,
-                 std::mt19937_64 &rng, int passes) {
+                 int passes) {
   std::vector<double> size(K, 0.0);
   for (int32_t v = 0; v < g.n; ++v) size[part[v]] += g.vw[v];
-  std::vector<int32_t> order(g.n);
-  std::iota(order.begin(), order.end(), 0);
+  std::vector<int32_t> prop(g.n, -1);
+  auto best_move = [&](int32_t v, std::vector<double> &conn, std::vector<int32_t> &touched,
+                       bool check_cap, double &gain) {
+    const int32_t pv = part[v];
+    touched.clear();
+    bool boundary = false;
+    for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+      const int32_t p = part[g.adj[e]];
+      if (conn[p] == 0.0) touched.push_back(p);
+      conn[p] += g.w[e];
+      boundary |= p != pv;
+    }
+    int32_t best = -1;
+    double bgain = 0.0;
+    if (boundary)
+      for (int32_t p : touched) {
+        if (p == pv || (check_cap && size[p] + g.vw[v] > cap)) continue;
+        const double gn = conn[p] - conn[pv];
+        if (gn > bgain || (gn == bgain && best >= 0 && p < best)) {
+          bgain = gn;
+          best = p;
+        }
+      }
+    for (int32_t p : touched) conn[p] = 0.0;
+    gain = bgain;
+    return best;
+  };
   std::vector<double> conn(K, 0.0);
   std::vector<int32_t> touched;
   for (int pass = 0; pass < passes; ++pass) {
-    std::shuffle(order.begin(), order.end(), rng);
-    int moved = 0;
-    for (int32_t v : order) {
+#pragma omp parallel
+    {
+      std::vector<double> lconn(K, 0.0);
+      std::vector<int32_t> ltouched;
+      double gn;
+#pragma omp for schedule(dynamic, 4096)
+      for (int32_t v = 0; v < g.n; ++v) prop[v] = best_move(v, lconn, ltouched, true, gn);
+    }
+    int64_t moved = 0;
+    for (int32_t v = 0; v < g.n; ++v) {
+      if (prop[v] < 0) continue;
+      double gn;
+      const int32_t best = best_move(v, conn, touched, true, gn);
+      if (best < 0) continue;
       const int32_t pv = part[v];
-      touched.clear();
-      bool boundary = false;
-      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
-        const int32_t p = part[g.adj[e]];
-        if (conn[p] == 0.0) touched.push_back(p);
-        conn[p] += g.w[e];
-        boundary |= p != pv;
-      }
-      if (boundary) {
-        int32_t best = -1;
-        double bgain = 0.0;
-        for (int32_t p : touched) {
-          if (p == pv || size[p] + g.vw[v] > cap) continue;
-          const double gain = conn[p] - conn[pv];
-          if (gain > bgain) {
-            bgain = gain;
-            best = p;
-          }
-        }
-        if (best >= 0) {
-          part[v] = best;
-          size[pv] -= g.vw[v];
-          size[best] += g.vw[v];
-          ++moved;
-        }
-      }
-      for (int32_t p : touched) conn[p] = 0.0;
+      part[v] = best;
+      size[pv] -= g.vw[v];
+      size[best] += g.vw[v];
+      ++moved;
     }
     if (moved <= g.n / 2000) break;  // converged: further passes gain little
   }
@@ -318,8 +406,6 @@ void refine_kway(const Graph &g, std::vector<int32_t> &part, int32_t K, double c
 void enforce_cap(const Graph &g, std::vector<int32_t> &part, int32_t K, int32_t cap) {
   std::vector<int64_t> size(K, 0);
   for (int32_t v = 0; v < g.n; ++v) size[part[v]] += 1;
-  std::vector<double> conn(K, 0.0);
-  std::vector<int32_t> touched;
   struct Move {
     double loss;
     int32_t v, to;
@@ -330,25 +416,37 @@ void enforce_cap(const Graph &g, std::vector<int32_t> &part, int32_t K, int32_t 
     for (int32_t k = 0; k < K; ++k) over |= size[k] > cap;
     if (!over) return;
     cand.clear();
-    for (int32_t v = 0; v < g.n; ++v) {
-      const int32_t pv = part[v];
-      if (size[pv] <= cap) continue;
-      touched.clear();
-      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
-        const int32_t p = part[g.adj[e]];
-        if (conn[p] == 0.0) touched.push_back(p);
-        conn[p] += g.w[e];
-      }
-      int32_t best = -1;
-      double bl = 1e300;
-      for (int32_t p : touched)
-        if (p != pv && size[p] < cap && conn[pv] - conn[p] < bl) {
-          bl = conn[pv] - conn[p];
-          best = p;
+    std::vector<int32_t> to(g.n, -1);
+    std::vector<double> loss(g.n, 0.0);
+#pragma omp parallel
+    {
+      std::vector<double> lconn(K, 0.0);
+      std::vector<int32_t> ltouched;
+#pragma omp for schedule(dynamic, 4096)
+      for (int32_t v = 0; v < g.n; ++v) {
+        const int32_t pv = part[v];
+        if (size[pv] <= cap) continue;
+        ltouched.clear();
+        for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+          const int32_t p = part[g.adj[e]];
+          if (lconn[p] == 0.0) ltouched.push_back(p);
+          lconn[p] += g.w[e];
         }
-      if (best >= 0) cand.push_back({bl, v, best});
-      for (int32_t p : touched) conn[p] = 0.0;
+        int32_t best = -1;
+        double bl = 1e300;
+        for (int32_t p : ltouched)
+          if (p != pv && size[p] < cap &&
+              (lconn[pv] - lconn[p] < bl || (lconn[pv] - lconn[p] == bl && p < best))) {
+            bl = lconn[pv] - lconn[p];
+            best = p;
+          }
+        to[v] = best;
+        loss[v] = bl;
+        for (int32_t p : ltouched) lconn[p] = 0.0;
+      }
     }
+    for (int32_t v = 0; v < g.n; ++v)
+      if (to[v] >= 0) cand.push_back({loss[v], v, to[v]});
     if (cand.empty()) break;
     std::stable_sort(cand.begin(), cand.end(),
                      [](const Move &a, const Move &b) { return a.loss < b.loss; });
@@ -435,7 +533,6 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
       (int64_t)cap * K < n)
     return CIMMINO_EINVAL;
   try {
-    std::mt19937_64 rng(seed);
     std::vector<Graph> levels;
     std::vector<std::vector<int32_t>> maps;
     levels.push_back(build_rip(n, crp, cci, ccv));
@@ -443,7 +540,7 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
     const int32_t maxvw = std::max(1, cap / 32);
     while (levels.back().n > std::max<int64_t>(40LL * K, 2000)) {
       std::vector<int32_t> cmap;
-      Graph c = coarsen(levels.back(), maxvw, rng, cmap);
+      Graph c = coarsen(levels.back(), maxvw, seed + 0x51ED2700ull * levels.size(), cmap);
       if (c.n > 0.92 * levels.back().n) break;
       maps.push_back(std::move(cmap));
       levels.push_back(std::move(c));
@@ -452,12 +549,14 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
     const Graph &gc = levels.back();
     std::vector<int32_t> part(gc.n, 0), all(gc.n);
     std::iota(all.begin(), all.end(), 0);
-    recursive_bisection(gc, all, 0, K, part, rng);
+#pragma omp parallel
+#pragma omp single
+    recursive_bisection(gc, all, 0, K, part, seed);
     // uncoarsen with refinement; the cap loosens toward the coarse levels
     for (int lvl = (int)levels.size() - 1; lvl >= 0; --lvl) {
       const Graph &g = levels[lvl];
       const double slack = lvl == 0 ? 1.0 : 1.0 + 0.03 * lvl;
-      refine_kway(g, part, K, cap * slack, rng, 8);
+      refine_kway(g, part, K, cap * slack, 8);
       if (lvl > 0) {
         std::vector<int32_t> fine(levels[lvl - 1].n);
         for (int32_t v = 0; v < levels[lvl - 1].n; ++v) fine[v] = part[maps[lvl - 1][v]];
@@ -466,7 +565,7 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
     }
     const Graph &g = levels.front();
     enforce_cap(g, part, K, cap);
-    refine_kway(g, part, K, cap, rng, 4);
+    refine_kway(g, part, K, cap, 4);
     // every part must hold at least one row: borrow from the largest parts
     std::vector<int64_t> size(K, 0);
     for (int64_t v = 0; v < n; ++v) ++size[part[v]];
@@ -485,13 +584,17 @@ extern "C" int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_
     // decode: parts in order, RCM inside each part
     std::vector<std::vector<int32_t>> members(K);
     for (int64_t v = 0; v < n; ++v) members[part[v]].push_back((int32_t)v);
-    std::vector<int32_t> local(n, -1), ord;
-    int64_t o = 0;
     block_ptr[0] = 0;
-    for (int32_t k = 0; k < K; ++k) {
-      rcm_order(g, members[k], ord, local);
-      for (int32_t v : ord) perm[o++] = v;
-      block_ptr[k + 1] = o;
+    for (int32_t k = 0; k < K; ++k) block_ptr[k + 1] = block_ptr[k] + (int64_t)members[k].size();
+    // parts are ordered independently (a local index array per thread)
+#pragma omp parallel
+    {
+      std::vector<int32_t> local(n, -1), ord;
+#pragma omp for schedule(dynamic, 1)
+      for (int32_t k = 0; k < K; ++k) {
+        rcm_order(g, members[k], ord, local);
+        std::copy(ord.begin(), ord.end(), perm + block_ptr[k]);
+      }
     }
     return CIMMINO_OK;
   } catch (...) {

@@ -99,3 +99,23 @@ def test_bad_inputs_rejected():
     with pytest.raises(g.CimminoError) as e:
         g.Solver(Z, np.array([0, 100, 200], np.int64))
     assert e.value.code == g.ESINGULAR
+
+
+def test_torch_caching_allocator_callbacks():
+    """opts.alloc / opts.free: the context's device memory comes from torch's caching
+    allocator (visible in torch's statistics while the context lives, returned on close), and
+    the solve equals the one with the library's pool bit for bit."""
+    import torch
+    w = inputs.workload(1)
+    x0, st0, _ = g.Solver(w.A, w.block_ptr, precision="fp32_refine").solve(w.F[0])
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    s = g.Solver(w.A, w.block_ptr, precision="fp32_refine", allocator="torch")
+    x1, st1, code = s.solve(w.F[0])
+    torch.cuda.synchronize()
+    held = torch.cuda.memory_allocated() - before
+    assert code == 0 and held >= st1[0]["factor_bytes"]
+    s.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    assert st1[0]["iters"] == st0[0]["iters"] and np.array_equal(x1, x0)
