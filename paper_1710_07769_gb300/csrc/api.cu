@@ -211,6 +211,7 @@ struct cimmino_ctx {
   DBuf<int32_t> acol, tcol;
   DBuf<double> aval, tval;
   DBuf<BlockDesc> blk;
+  DBuf<int32_t> border;  // projection launch order (longest first)
   DBuf<TileRow> trow;
   DBuf<SysDesc> sys;
   DBuf<CtaDesc> cta;
@@ -531,7 +532,8 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   CUDA_TRY(cudaStreamSynchronize(s));
   c->cci.alloc(c->nnzc);
   c->ccv.alloc(c->nnzc);
-  spgemm_fill(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, N, c->crp.p, c->cci.p, c->ccv.p, s);
+  spgemm_fill(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, c->cv.p, N, c->crp.p, c->cci.p,
+              c->ccv.p, s);
   c->setup_launches += 1;
   if (novf > 0)
     spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p,
@@ -740,6 +742,21 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
           (t * TT + 2 * (int64_t)B.nt * (B.prec64 ? kPackTile : kBPackTile)) * (B.prec64 ? 8 : 4);
     }
     (void)ntiles;
+    // projection launch order: blocks with the most streamed tiles first
+    {
+      std::vector<int64_t> work(nblk, 0);
+      for (int32_t b = 0; b < nblk; ++b) {
+        const BlockDesc &B = c->hblk[b];
+        for (int32_t I = 0; I < B.nt; ++I)
+          work[b] += (I - c->htrow[B.trow0 + I].j0) + (c->htrowT[B.trow0 + I].j0 - I) + 2;
+      }
+      std::vector<int32_t> order(nblk);
+      for (int32_t b = 0; b < nblk; ++b) order[b] = b;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int32_t x, int32_t y) { return work[x] > work[y]; });
+      c->border.alloc(nblk);
+      h2d(c->border.p, order.data(), nblk, s);
+    }
     c->trowT.alloc(ntrow);
     h2d(c->trowT.p, c->htrowT.data(), ntrow, s);
     if (oT32) c->facT32.alloc(oT32);
@@ -882,6 +899,7 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.scol = c->scol.p;
   a.sval = c->sval.p;
   a.blk = c->blk.p;
+  a.border = c->border.p;
   a.trow = c->trow.p;
   a.trowT = c->trowT.p;
   a.fac32 = c->fac32.p;
@@ -1599,7 +1617,7 @@ int cimmino_aat(const cimmino_csr *A, void *stream, int64_t *nnz, int64_t *row_p
     if (col_idx && val) {
       cci.alloc(nc);
       ccv.alloc(nc);
-      spgemm_fill(rp.p, ci.p, va.p, cp.p, ri.p, N, crp.p, cci.p, ccv.p, s);
+      spgemm_fill(rp.p, ci.p, va.p, cp.p, ri.p, cv.p, N, crp.p, cci.p, ccv.p, s);
       if (novf > 0)
         spgemm_overflow(rp.p, ci.p, va.p, cp.p, ri.p, ovf.p + 1, novf, cnt.p, crp.p, cci.p,
                         ccv.p, flag.p + 1, s);

@@ -167,9 +167,10 @@ void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, con
                      const int32_t *ri, const int32_t *ovf, int32_t novf, int64_t *cnt,
                      const int64_t *crp, int32_t *cci, double *ccv, int32_t *flag,
                      cudaStream_t s);
+// cv: values of the transpose (CSC of A), aligned with ri
 void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
-                 const int32_t *ri, int64_t N, const int64_t *crp, int32_t *cci, double *ccv,
-                 cudaStream_t s);
+                 const int32_t *ri, const double *cv, int64_t N, const int64_t *crp,
+                 int32_t *cci, double *ccv, cudaStream_t s);
 void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s);
 void bd_count(const int64_t *crp, const int32_t *cci, const BlockDesc *blk, const int32_t *rowblk,
               int64_t N, int64_t *cnt, cudaStream_t s);
@@ -245,6 +246,8 @@ struct IterArgs {
   const int16_t *scol;   //   block-local columns
   const double *sval;    //   values
   const BlockDesc *blk;
+  const int32_t *border;  // launch order of the blocks in the projection kernels: most
+                          // streamed tiles first, so that the long ones start in wave one
   const TileRow *trow;
   const TileRow *trowT;  // upper (transposed) tile rows: off, j0 field = J1(I)
   const float *fac32;

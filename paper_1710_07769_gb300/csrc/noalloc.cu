@@ -123,7 +123,7 @@ int cimmino_aat_noalloc(const cimmino_csr *A, void *stream, int64_t *nnz, int64_
       if (capacity < nc)
         fail(CIMMINO_EINVAL, "capacity " + std::to_string(capacity) + " < nnz(C) = " +
                                  std::to_string(nc));
-      spgemm_fill(A->row_ptr, A->col_idx, A->val, cp, ri, N, row_ptr, col_idx, val, s);
+      spgemm_fill(A->row_ptr, A->col_idx, A->val, cp, ri, cv, N, row_ptr, col_idx, val, s);
       if (novf > 0)
         spgemm_overflow(A->row_ptr, A->col_idx, A->val, cp, ri, ovf + 1, novf, cnt, row_ptr,
                         col_idx, val, flag + 1, s);

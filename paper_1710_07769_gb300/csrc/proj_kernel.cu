@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
   __shared__ double red[8];
   __shared__ int s_again, s_abort;
   extern __shared__ __align__(128) unsigned char dsm[];
-  const BlockDesc B = a.blk[blockIdx.x];
+  const BlockDesc B = a.blk[a.border[blockIdx.x]];  // longest blocks first
   const int mpmax = a.max_mp;
   Ring R;
   R.base = dsm;

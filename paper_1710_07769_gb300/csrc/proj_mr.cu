@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
   __shared__ double tmp[8 * RG], un2[RG], e2[RG];
   __shared__ int s_again, s_abort;
   extern __shared__ __align__(128) unsigned char dsm[];
-  const BlockDesc B = a.blk[blockIdx.x];
+  const BlockDesc B = a.blk[a.border[blockIdx.x]];  // longest blocks first
   Ring R;
   R.base = dsm;
   R.full = full;

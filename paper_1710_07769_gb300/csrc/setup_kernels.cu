@@ -398,16 +398,95 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
   if (lane == 0) cnt[i] = u;
 }
 
+// Rows of C with at most kFillFast candidates are filled by Gustavson's scheme: every
+// (candidate row r, column j) pair of row i carries its product a_ij a_rj, the pairs are
+// sorted by (r, position of j in row i), and each run of equal r is summed in increasing j,
+// the order of the row-wise definition (explicitly rounded products and sums, so the values
+// are those of a sequential loop).  Longer rows take the dot-product path below.
+constexpr int kFillFast = kSpgemmWarpCap / 4;  // 16-byte pairs in the warp's 4 KB buffer
+
+__device__ void bitonic_sort_kv(uint64_t *key, double *val, int U, int lane) {
+  int P = 1;
+  while (P < U) P <<= 1;
+  for (int t = U + lane; t < P; t += 32) key[t] = ~0ull;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < P; t += 32) {
+        const int ixj = t ^ j;
+        if (ixj > t) {
+          const uint64_t a = key[t], b = key[ixj];
+          const bool up = (t & k) == 0;
+          if ((a > b) == up) {
+            key[t] = b;
+            key[ixj] = a;
+            const double va = val[t];
+            val[t] = val[ixj];
+            val[ixj] = va;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kSpgemmWarps * 32)
     k_spgemm_fill_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                        const double *__restrict__ va, const int64_t *__restrict__ cp,
-                       const int32_t *__restrict__ ri, int64_t N, const int64_t *__restrict__ crp,
-                       int32_t *__restrict__ cci, double *__restrict__ ccv) {
-  __shared__ int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
+                       const int32_t *__restrict__ ri, const double *__restrict__ cv, int64_t N,
+                       const int64_t *__restrict__ crp, int32_t *__restrict__ cci,
+                       double *__restrict__ ccv) {
+  __shared__ __align__(16) int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
   int32_t *buf = sbuf[warp];
+  const int64_t q0 = rp[i];
+  const int nq = (int)(rp[i + 1] - q0);
+  int64_t U64 = 0;
+  for (int qq = lane; qq < nq; qq += 32) {
+    const int32_t j = ci[q0 + qq];
+    U64 += cp[j + 1] - cp[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) U64 += __shfl_xor_sync(0xffffffffu, U64, o);
+  if (U64 <= kFillFast) {
+    const int U = (int)U64;
+    uint64_t *key = reinterpret_cast<uint64_t *>(buf);
+    double *val = reinterpret_cast<double *>(buf) + kFillFast;
+    int base = 0;
+    for (int qq = 0; qq < nq; ++qq) {
+      const int32_t j = ci[q0 + qq];
+      const double a = va[q0 + qq];
+      const int64_t s0 = cp[j];
+      const int len = (int)(cp[j + 1] - s0);
+      for (int t = lane; t < len; t += 32) {
+        key[base + t] = ((uint64_t)(uint32_t)ri[s0 + t] << 32) | (uint32_t)qq;
+        val[base + t] = __dmul_rn(a, cv[s0 + t]);
+      }
+      base += len;
+    }
+    __syncwarp();
+    bitonic_sort_kv(key, val, U, lane);
+    const int64_t w = crp[i];
+    int total = 0;
+    for (int b0 = 0; b0 < U; b0 += 32) {
+      const int t = b0 + lane;
+      const bool head = t < U && (t == 0 || (key[t] >> 32) != (key[t - 1] >> 32));
+      const unsigned m = __ballot_sync(0xffffffffu, head);
+      if (head) {
+        const uint64_t r = key[t] >> 32;
+        double acc = val[t];
+        for (int u = t + 1; u < U && (key[u] >> 32) == r; ++u) acc = __dadd_rn(acc, val[u]);
+        const int pos = total + __popc(m & ((1u << lane) - 1u));
+        cci[w + pos] = (int32_t)r;
+        ccv[w + pos] = acc;
+      }
+      total += __popc(m);
+    }
+    return;
+  }
   int U = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
   if (U > kSpgemmWarpCap) return;  // CTA variant fills this row
   bitonic_sort<32>(buf, U, lane);
@@ -703,10 +782,10 @@ void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, con
 }
 
 void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
-                 const int32_t *ri, int64_t N, const int64_t *crp, int32_t *cci, double *ccv,
-                 cudaStream_t s) {
-  k_spgemm_fill_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(rp, ci, va, cp, ri,
-                                                                            N, crp, cci, ccv);
+                 const int32_t *ri, const double *cv, int64_t N, const int64_t *crp,
+                 int32_t *cci, double *ccv, cudaStream_t s) {
+  k_spgemm_fill_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(
+      rp, ci, va, cp, ri, cv, N, crp, cci, ccv);
 }
 
 void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s) {
