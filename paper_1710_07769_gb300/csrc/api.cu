@@ -653,14 +653,20 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->err_flag.alloc(1);
     CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
   }
+  DBuf<float> tc_scratch;  // the split operand copy of L (FP32 blocks), freed after setup
+  DBuf<int32_t> tc_rowblk;
+  if (!fp64) {
+    tc_scratch.alloc(cholesky_tc_scratch_floats(off));
+    tc_rowblk.alloc(ntrow);
+  }
   Timer tchol;
   tchol.start(s);
   if (fp64) {
     launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, c->fac64.p, c->dinv64.p, pmin.p,
                     pfail.p, s);
   } else {
-    launch_cholesky_tc(c->blk.p, blist.p, nblk, c->trow.p, c->fac32.p, c->dinv32.p, pmin.p,
-                       pfail.p, c->err_flag.p, s);
+    launch_cholesky_tc(c->blk.p, blist.p, nblk, nblk, ntrow, c->trow.p, c->fac32.p, c->dinv32.p,
+                       tc_scratch.p, off, tc_rowblk.p, pmin.p, pfail.p, c->err_flag.p, s);
   }
   c->t_chol_ms = tchol.stop_ms(s);
   c->setup_launches += 2;  // scatter, Cholesky

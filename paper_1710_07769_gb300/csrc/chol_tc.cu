@@ -1,19 +1,30 @@
-// Batched Cholesky of FP32 Gram blocks with the trailing update on the tensor cores.
+// Batched Cholesky of FP32 Gram blocks on the tensor cores, left-looking.
 //
-// Same right-looking tile algorithm (and the same stored form L = diag(L_II)(I + N)) as
-// the CUDA-core kernel in chol_kernels.cu; only step 4, the trailing update
-//     G_IJ -= L_IK L_JK^T     for K < J <= I,
-// the one dense contraction of the method, runs as tcgen05 MMAs:
-//   * A = [L_{I0,K}; L_{I0+1,K}] (128 x 64, two tile rows), B = [L_{J0,K}; L_{J0+1,K}]
-//     (128 x 64, two tile columns), D = A B^T (128 x 128, FP32) in tensor memory;
-//   * 3xTF32 for FP32-level accuracy: x = hi + lo with hi = x rounded to TF32 and
-//     lo = x - hi, D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the TF32 operands are
-//     read from shared memory in the canonical no-swizzle K-major layout: 8-row x
-//     16-byte core matrices, 128 bytes apart along K, 2048 bytes apart along rows);
-//   * one thread issues the 24 MMAs (K = 8 each) and commits them to an mbarrier; the
-//     8 warps read D back with tcgen05.ld (warp w: lanes 32 (w mod 4).., half of the
-//     columns) and subtract it from the tiles in global memory.
-// Tiles outside the envelope read as zero and are never written.
+// One CTA per block; for every tile column K (the panel) of L_i:
+//   1. accumulate  D_I = sum_{J < K} L_IJ L_KJ^T  for every panel row I >= K inside the
+//      envelope, in tensor memory: rows are taken in pairs (M = 128: tiles I0, I1), the
+//      panel is one tile wide (N = 64), K-dimension 64 per tile J;
+//   2. factor the diagonal tile: L_KK L_KK^T = G_KK - D_K (CUDA cores), and invert L_KK;
+//   3. L_IK = (G_IK - D_I) inv(L_KK)^T for the other panel rows (tensor cores again).
+// The trailing matrix is never written back: every L tile is written once (to the factor
+// and, split for the tensor cores, to a scratch copy), every G tile read once.  Row K of L
+// is turned into N_KJ = inv(L_KK) L_KJ afterwards by a separate kernel (all tiles are
+// independent there), which gives the stored form L = diag(L_II)(I + N).
+//
+// FP32 accuracy from TF32 tensor cores by the 3xTF32 split: x = hi + lo, hi = x rounded to
+// TF32, lo = x - hi, and A B^T = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.  The scratch copy
+// holds every finished L tile as its hi and lo parts in the canonical no-swizzle K-major
+// layout of the MMA operands (8-row x 16-byte core matrices, 128 bytes apart along K, 1024
+// bytes apart along rows), cut into two K-halves of 32 columns: one bulk copy per 8 KB
+// piece fills an operand stage.
+//
+// Roles (192 threads): warps 0-3 read and write tensor memory (thread t = accumulator row t)
+// and do the CUDA-core work; warp 4 issues the bulk copies of the operand ring (two A stages
+// of 32 KB: a row pair's K-half, hi and lo; two B stages of 16 KB: tile L_KJ's K-half); warp
+// 5 issues the MMAs.  About 96 KB of shared memory and 256 tensor-memory columns (four
+// 128 x 64 accumulators) per CTA, so two CTAs (two blocks) share an SM.  Every wait is
+// bounded by %globaltimer: after about 2 s a role sets the abort flag and bit 4 of the error
+// word, and every later wait returns at once, so the kernel always ends.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,15 +35,19 @@ namespace cimmino {
 namespace {
 
 constexpr int T = kTile;
-constexpr int kThreads = 256;
-constexpr int LDS = T + 1;  // padded row-major diagonal tile
-constexpr int LD = T + 1;   // k-major operand tiles of the CUDA-core steps (odd: the
-                            // transposed stores hit 32 distinct banks)
-constexpr uint32_t kCoreK = 128;    // bytes between core matrices along K
-constexpr uint32_t kCoreRow = 2048; // bytes between 8-row groups (16 core matrices of K = 64)
-constexpr uint32_t kTmemCols = 128;
-constexpr int kDstLd = 132;  // padded row of the epilogue staging area (floats)
+constexpr int kEpi = 128;                 // epilogue / CUDA-core threads (warps 0-3)
+constexpr int kThreads = kEpi + 64;       // + producer warp + MMA warp
+constexpr int kPairsMax = 4;              // accumulators per pass
+constexpr uint32_t kTmemCols = 64 * kPairsMax;
+constexpr uint32_t kHalf = 8192;          // bytes of one K-half image (64 rows x 32 x 4 B)
+constexpr uint32_t kAStage = 4 * kHalf;   // [I0 hi][I1 hi][I0 lo][I1 lo]
+constexpr uint32_t kBStage = 2 * kHalf;   // [hi][lo]
+constexpr uint32_t kRing = 2 * kAStage + 2 * kBStage;  // 96 KB
+constexpr int LDS = T + 1;
 constexpr uint64_t kWaitNs = 2000000000ull;
+// D f32, A/B tf32, K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
+                            ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -42,168 +57,112 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// no-swizzle K-major operand descriptor: core matrices 128 B apart along K (leading byte
+// offset), 8-row groups `sbo` bytes apart (stride byte offset)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(kCoreK >> 4) << 16;    // leading (K) byte offset
-  d |= (uint64_t)(kCoreRow >> 4) << 32;  // stride (row) byte offset
-  d |= (uint64_t)1 << 46;                // descriptor version; no swizzle
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(sbo >> 4) << 32;
+  d |= (uint64_t)1 << 46;
   return d;
 }
-// D f32, A/B tf32, both K-major, M = 128, N = 128 (trailing update) or 64 (TRSM)
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) |
-                            ((128u >> 4) << 24);
-constexpr uint32_t kIdescN64 = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) |
-                               ((128u >> 4) << 24);
-constexpr int kStLd = T + 4;  // padded row of the TRSM epilogue staging area (floats)
-
-// byte offset of element (r, k) of a 128 x 64 operand in the canonical layout
-__device__ __forceinline__ uint32_t canon(int r, int k) {
-  return (uint32_t)((r >> 3) * kCoreRow + (k >> 2) * kCoreK + (r & 7) * 16 + (k & 3) * 4);
-}
-
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t h;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
   return __uint_as_float(h);
 }
-
-// Fill a 128 x 64 hi/lo operand pair from two row-major tiles (rows 0..63 from g0, rows
-// 64..127 from g1; a null tile reads as zeros).  A warp handles 8 rows x 4 16-byte chunks
-// per unit: lane l takes row 8 rg + (l & 7), chunk 4 cq + (l >> 3), so each quarter-warp
-// stores one whole 128-byte core matrix (conflict-free) and reads 8 rows x 64 contiguous
-// bytes from global memory.  All 8 loads of a lane are issued before the first store.
-__device__ __forceinline__ void load_split2(const float *__restrict__ g0,
-                                            const float *__restrict__ g1, unsigned char *hi,
-                                            unsigned char *lo) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int U = 32 / (kThreads / 32);  // units per warp and tile
-  float4 x[2][U];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const float *g = h ? g1 : g0;
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int u = warp + (kThreads / 32) * j;
-      const int r = 8 * (u >> 2) + (lane & 7), kc = 4 * (u & 3) + (lane >> 3);
-      x[h][j] = g ? *reinterpret_cast<const float4 *>(g + r * T + 4 * kc)
-                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int u = warp + (kThreads / 32) * j;
-      const int r = 8 * (u >> 2) + (lane & 7), kc = 4 * (u & 3) + (lane >> 3);
-      const float4 v = x[h][j];
-      const float4 t = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-      const uint32_t o =
-          (uint32_t)(((64 * h + r) >> 3) * kCoreRow + kc * kCoreK + (r & 7) * 16);
-      *reinterpret_cast<float4 *>(hi + o) = t;
-      *reinterpret_cast<float4 *>(lo + o) = make_float4(v.x - t.x, v.y - t.y, v.z - t.z, v.w - t.w);
-    }
+// byte offset of (row r, column k) in an image of 32-column K-halves (row groups 1024 B
+// apart); `half_bytes` separates the two K-halves
+__device__ __forceinline__ uint32_t half_off(int r, int k) {
+  return (uint32_t)((k >> 5) * kHalf + (r >> 3) * 1024 + ((k & 31) >> 2) * 128 + (r & 7) * 16 +
+                    (k & 3) * 4);
+}
+// byte offset of (row r, column k) in a full-K image (row groups 2048 B apart)
+__device__ __forceinline__ uint32_t full_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 2048 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
-// Transposed operand layout (second canonical no-swizzle K-major form): core matrices of
-// 8 rows x 16 bytes, 8-row groups 128 bytes apart, K chunks of 4 values 2048 bytes apart.
-constexpr uint32_t kTCoreK = 2048;  // bytes between core matrices along K
-constexpr uint32_t kTCoreRow = 128; // bytes between 8-row groups
-__device__ __forceinline__ uint64_t smem_desc_t(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(kTCoreK >> 4) << 16;
-  d |= (uint64_t)(kTCoreRow >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
+               : "memory");
 }
-
-// B operand rows 0..63 = columns of g0, rows 64..127 = columns of g1 (B[n][k] = g[k][n]),
-// hi/lo split, in the transposed layout: in every step a warp stores 8 rows x 4 k values,
-// 32 consecutive words (conflict-free); the loads read 4 rows x 32 contiguous bytes.
-__device__ __forceinline__ void load_split2_t(const float *__restrict__ g0,
-                                              const float *__restrict__ g1, unsigned char *hi,
-                                              unsigned char *lo) {
-  const int tid = threadIdx.x, kk = tid & 3;
-  constexpr int IT = 128 * T / kThreads;  // 32 values per thread
-#pragma unroll 4
-  for (int h = 0; h < IT; h += 8) {
-    float x[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int it = h + j, k4 = it & 15, n = (tid >> 2) + 64 * (it >> 4);
-      const float *g = n < 64 ? g0 : g1;
-      x[j] = g ? g[(4 * k4 + kk) * T + (n & 63)] : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int it = h + j, k4 = it & 15, n = (tid >> 2) + 64 * (it >> 4);
-      const uint32_t o = (uint32_t)(k4 * kTCoreK + (n >> 3) * kTCoreRow + (n & 7) * 16 + kk * 4);
-      const float t = tf32_hi(x[j]);
-      *reinterpret_cast<float *>(hi + o) = t;
-      *reinterpret_cast<float *>(lo + o) = x[j] - t;
-    }
-  }
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-
-__device__ __forceinline__ float *tile_ptr(float *fac, const TileRow &tr, int J) {
-  return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
 }
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc,
-                                         uint32_t idesc = kIdesc) {
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+struct Ctl {
+  uint64_t full_a[2], empty_a[2], full_b[2], empty_b[2];
+  uint64_t acc_ready, trsm_ready, trsm_done;
+  uint32_t tmem_base;
+  int abort;
+  int fail;
+  double pmin;
+};
+
+// Bounded wait on a barrier phase; gives up (and makes every later wait give up) after
+// about 2 s or once another role has given up.
+__device__ __forceinline__ bool wait_phase(Ctl *c, uint64_t *b, uint32_t parity, int32_t *err) {
+  if (*(volatile int *)&c->abort) return false;
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < (1u << 30); ++i) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (*(volatile int *)&c->abort) return false;
+    if (global_ns() - t0 > kWaitNs) break;
+  }
+  *(volatile int *)&c->abort = 1;
+  atomicOr(err, 4);
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 
-// One thread issues D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K = 64 (3xTF32, 24
-// MMAs) and commits them to mbar; every thread then waits for the commit (bounded: about
-// 2 s, after which s_err and bit 4 of the error word are set and the kernel winds down).
-// BT: B is in the transposed layout (smem_desc_t, K chunks kTCoreK apart).
-template <bool BT = false>
-__device__ __forceinline__ void mma_3xtf32(uint32_t tmem, const unsigned char *Ahi,
-                                           const unsigned char *Alo, const unsigned char *Bhi,
-                                           const unsigned char *Blo, uint32_t idesc,
-                                           uint64_t *mbar, uint32_t &phase, int *s_err,
-                                           int32_t *err) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (threadIdx.x == 0) {
-    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-    for (int s = 0; s < T / 8; ++s) {
-      const uint32_t ko = s * 2 * kCoreK;  // K = 8 per MMA: two core matrices
-      const uint32_t kb = s * 2 * (BT ? kTCoreK : kCoreK);
-      const uint64_t bdh = BT ? smem_desc_t(bh + kb) : smem_desc(bh + kb);
-      const uint64_t bdl = BT ? smem_desc_t(bl + kb) : smem_desc(bl + kb);
-      mma_tf32(tmem, smem_desc(ah + ko), bdh, s > 0, idesc);
-      mma_tf32(tmem, smem_desc(ah + ko), bdl, 1, idesc);
-      mma_tf32(tmem, smem_desc(al + ko), bdh, 1, idesc);
-    }
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(mbar))
-        : "memory");
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 3xTF32 product over `ksteps` steps of K = 8: D (+)= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.
+// A: 128 rows, B: 64 rows; hi/lo parts at the given shared addresses; sbo = row-group stride.
+__device__ __forceinline__ void mma_3x(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh,
+                                       uint32_t bl, uint32_t sbo, int ksteps, bool accumulate) {
+  for (int s = 0; s < ksteps; ++s) {
+    const uint32_t ko = s * 256;  // K = 8: two core matrices
+    mma_tf32(tmem, smem_desc(ah + ko, sbo), smem_desc(bh + ko, sbo), accumulate || s > 0);
+    mma_tf32(tmem, smem_desc(ah + ko, sbo), smem_desc(bl + ko, sbo), 1);
+    mma_tf32(tmem, smem_desc(al + ko, sbo), smem_desc(bh + ko, sbo), 1);
   }
-  uint32_t ok = 0;
-  const uint64_t t0 = global_ns();
-  while (!ok) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(phase)
-        : "memory");
-    if (!ok && global_ns() - t0 > kWaitNs) {
-      *s_err = 1;
-      atomicOr(err, 4);
-      break;
-    }
-  }
-  phase ^= 1u;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
@@ -229,42 +188,58 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
   for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// The panel of column K: rows I >= K whose envelope reaches column K, in pairs.
+struct Panel {
+  int rows[2 * 64];
+  int n;
+};
+
+__device__ __forceinline__ int64_t tile_index(const TileRow &tr, int J) {
+  return tr.off + (int64_t)(J - tr.j0) * T * T;  // element offset of tile (I, J)
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
     k_cholesky_tc(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
                   const TileRow *__restrict__ trow, float *__restrict__ fac,
-                  float *__restrict__ dinv, double *__restrict__ pivmin,
+                  float *__restrict__ dinv, float *__restrict__ lc,
+                  const float *__restrict__ zero_img, double *__restrict__ pivmin,
                   int32_t *__restrict__ pivfail, int32_t *__restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *Ahi = smem_raw;          // 128 x 64 TF32 operands, 32 KB each
-  unsigned char *Alo = Ahi + 32768;
-  unsigned char *Bhi = Alo + 32768;
-  unsigned char *Blo = Bhi + 32768;
-  float *At = reinterpret_cast<float *>(Blo + 32768);  // [T][LD]
-  float *Bt = At + T * LD;                             // [T][LD]
-  float *S = Bt + T * LD;                              // [T][LDS]
-  float *Di = S + T * LDS;                             // [T][LDS]
-  float *Dst = reinterpret_cast<float *>(Bhi);  // [128][kDstLd] epilogue staging (B, At)
-  float *St = At;  // [128][kStLd] TRSM epilogue staging (At, Bt, S)
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  __shared__ double s_pmin;
-  __shared__ int s_fail, s_err;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ Ctl ctl;
+  __shared__ int s_rows[T];  // panel rows (a block has at most 64 tile rows)
+  __shared__ int s_nrows;
+  unsigned char *ringA = smem;                  // 2 x 32 KB
+  unsigned char *ringB = smem + 2 * kAStage;    // 2 x 16 KB
+  // outside the accumulation (ring idle): diagonal factor scratch, then TRSM operands
+  float *S = reinterpret_cast<float *>(smem);              // [T][LDS]
+  float *Di = S + T * LDS;                                 // [T][LDS]
+  unsigned char *Ax = smem;                                // 128 x 64 hi (32 KB) + lo (32 KB)
+  unsigned char *Binv = smem + 2 * kAStage;                // 64 x 64 hi (16 KB) + lo (16 KB)
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
   const TileRow *tr = trow + B.trow0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tr4 = tid / 16, tc4 = tid % 16;
   if (tid == 0) {
-    s_pmin = 1e300;
-    s_fail = 0;
-    s_err = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&ctl.full_a[s], 1);
+      mbar_init(&ctl.empty_a[s], 1);
+      mbar_init(&ctl.full_b[s], 1);
+      mbar_init(&ctl.empty_b[s], 1);
+    }
+    mbar_init(&ctl.acc_ready, 1);
+    mbar_init(&ctl.trsm_ready, kEpi);
+    mbar_init(&ctl.trsm_done, 1);
+    ctl.abort = 0;
+    ctl.fail = 0;
+    ctl.pmin = 1e300;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base)),
+                     smem_u32(&ctl.tmem_base)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -272,225 +247,304 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-  uint32_t phase = 0;
+  const uint32_t tmem = ctl.tmem_base;
 
-  for (int K = 0; K < B.nt && !s_err; ++K) {
-    const TileRow TK = tr[K];
-    float *gKK = tile_ptr(fac, TK, K);
-    // ---- 1. diagonal tile (CUDA cores), right-looking with the column scaling deferred:
-    // step j subtracts S_ij S_kj / d_j from the trailing triangle (one barrier per column);
-    // afterwards L_jj = sqrt(d_j) and L_ij = S_ij / sqrt(d_j)
-    for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
-    __syncthreads();
-    for (int j = 0; j < T; ++j) {
-      float dj = S[j * LDS + j];
-      if (tid == 0 && K * T + j < B.m) s_pmin = fmin(s_pmin, (double)dj);
-      if (!(dj > 0.f) || !isfinite(dj)) {
-        if (tid == 0) s_fail = 1;
-        dj = 1.f;
-      }
-      const float inv = 1.f / dj;
-      for (int i = j + 1 + tr4; i < T; i += 16) {
-        const float t = S[i * LDS + j] * inv;
-        for (int k = j + 1 + tc4; k <= i; k += 16) S[i * LDS + k] = fmaf(-t, S[k * LDS + j], S[i * LDS + k]);
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int i = e / T, j = e % T;
-      if (j > i) continue;
-      float dj = S[j * LDS + j];
-      if (!(dj > 0.f) || !isfinite(dj)) dj = 1.f;
-      Di[i * LDS + j] = i == j ? sqrtf(dj) : S[i * LDS + j] / sqrtf(dj);  // L_KK, staged in Di
+  // phase / stage counters (each role keeps its own copy of the ones it uses)
+  uint32_t na = 0, nb = 0;              // A / B stages issued (producer) or consumed (MMA)
+  uint32_t ph_acc = 0, ph_ready = 0, ph_done = 0;
+
+  for (int K = 0; K < B.nt; ++K) {
+    // panel rows, computed by every thread alike (tile rows are few)
+    if (tid == 0) {
+      int n = 0;
+      for (int I = K; I < B.nt; ++I)
+        if (tr[I].j0 <= K) s_rows[n++] = I;
+      s_nrows = n;
     }
     __syncthreads();
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int i = e / T, j = e % T;
-      S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.f;
-    }
-    __syncthreads();
-    // ---- 2. inv(L_KK) by rows: Di_ic = (delta_ic - sum_{c<=k<i} L_ik Di_kc) / L_ii; row i
-    // depends on rows < i only, so all columns c of a row run in parallel (4 threads per
-    // column split the sum, fixed-order shuffle reduction)
-    {
-      const int c = tid >> 2, q = tid & 3;
-      for (int i = 0; i < T; ++i) {
-        float acc = 0.f;
-        if (c < i)
-          for (int k = c + q; k < i; k += 4) acc = fmaf(S[i * LDS + k], Di[k * LDS + c], acc);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (q == 0) {
-          const float lii = S[i * LDS + i];
-          Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.f / lii : 0.f);
+    const int nrows = s_nrows;
+    const int npairs = (nrows + 1) / 2;
+    const int jlo = tr[K].j0;  // row K's envelope: L_KJ != 0 for jlo <= J < K
+    for (int p0 = 0; p0 < npairs; p0 += kPairsMax) {
+      const int np = min(kPairsMax, npairs - p0);
+      // rows of pair p of this pass (I1 < 0: single tile)
+      auto pair_rows = [&](int p, int &I0, int &I1) {
+        I0 = s_rows[2 * (p0 + p)];
+        I1 = 2 * (p0 + p) + 1 < nrows ? s_rows[2 * (p0 + p) + 1] : -1;
+      };
+      auto pair_has = [&](int I0, int I1, int J) {
+        return tr[I0].j0 <= J || (I1 >= 0 && tr[I1].j0 <= J);
+      };
+      auto pass_has = [&](int J) {
+        for (int p = 0; p < np; ++p) {
+          int I0, I1;
+          pair_rows(p, I0, I1);
+          if (pair_has(I0, I1, J)) return true;
         }
-        __syncthreads();
-      }
-    }
-    float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
-    for (int e = tid; e < T * T; e += kThreads) {
-      int r = e / T, c = e % T;
-      gKK[e] = c <= r ? S[r * LDS + c] : 0.f;
-      dK[e] = c <= r ? Di[r * LDS + c] : 0.f;
-    }
-    // N_KJ = inv(L_KK) L_KJ for the final row K on the tensor cores, pairs of tiles:
-    // D (128 x 128) = [inv(L_KK); 0] [L_KJ0 L_KJ1] (rows 64..127 of A are zero, so half of
-    // D is unused), A = inv(L_KK) read back from dK, B row n = column n of the pair in the
-    // transposed layout; rows 0..63 of D go through the padded staging area (At, Bt, S)
-    __syncthreads();  // dK is complete
-    if (TK.j0 < K) load_split2(dK, nullptr, Ahi, Alo);
-    for (int J0 = TK.j0; J0 < K && !s_err; J0 += 2) {
-      const bool has1 = J0 + 1 < K;
-      float *g0 = tile_ptr(fac, TK, J0);
-      float *g1 = has1 ? tile_ptr(fac, TK, J0 + 1) : nullptr;
-      load_split2_t(g0, g1, Bhi, Blo);
-      mma_3xtf32<true>(tmem, Ahi, Alo, Bhi, Blo, kIdesc, &mbar, phase, &s_err, err);
-      if ((warp & 3) < 2) {  // TMEM lanes 0..63 (warps 0, 1, 4, 5), column half warp / 4
-        const int rr = 32 * (warp & 3) + lane, jh = warp >> 2;
-        float v[64];
-        tmem_ld64(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * jh), v);
-        float *st = St + rr * kDstLd + 64 * jh;
-#pragma unroll
-        for (int c = 0; c < 64; c += 4)
-          *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-      }
-      __syncthreads();
-      if (!s_err) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float *gq = q ? g1 : g0;
-          if (!gq) continue;
-          for (int e = tid; e < T * T / 4; e += kThreads) {
-            const int r = e >> 4, c = 4 * (e & 15);
-            *reinterpret_cast<float4 *>(gq + r * T + c) =
-                *reinterpret_cast<const float4 *>(St + r * kDstLd + 64 * q + c);
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    // ---- 3. L_IK = G_IK inv(L_KK)^T on the tensor cores, pairs of tile rows:
-    // D (128 x 64) = [G_I0K; G_I1K] inv(L_KK)^T, i.e. B = inv(L_KK) (K-major rows, read
-    // back from dK); D goes through a padded staging area (the CUDA-core scratch At, Bt,
-    // S, free by now) into coalesced 16-byte stores
-    __syncthreads();  // dK is complete
-    load_split2(dK, nullptr, Bhi, Blo);
-    for (int I0 = K + 1; I0 < B.nt && !s_err; I0 += 2) {
-      const int I1 = I0 + 1;
-      const bool has0 = tr[I0].j0 <= K;
-      const bool has1 = I1 < B.nt && tr[I1].j0 <= K;
-      if (!has0 && !has1) continue;
-      float *g0 = has0 ? tile_ptr(fac, tr[I0], K) : nullptr;
-      float *g1 = has1 ? tile_ptr(fac, tr[I1], K) : nullptr;
-      load_split2(g0, g1, Ahi, Alo);
-      mma_3xtf32(tmem, Ahi, Alo, Bhi, Blo, kIdescN64, &mbar, phase, &s_err, err);
-      if (warp < 4) {  // warp w reads TMEM lanes 32 w .. 32 w + 31, columns 0..63
-        const int rr = 32 * warp + lane;
-        float v[64];
-        tmem_ld64(tmem + ((uint32_t)(32 * warp) << 16), v);
-        float *st = St + rr * kStLd;
-#pragma unroll
-        for (int c = 0; c < 64; c += 4)
-          *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-      }
-      __syncthreads();
-      if (!s_err) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float *gq = q ? g1 : g0;
-          if (!gq) continue;
-          for (int e = tid; e < T * T / 4; e += kThreads) {
-            const int r = e >> 4, c = 4 * (e & 15);
-            *reinterpret_cast<float4 *>(gq + r * T + c) =
-                *reinterpret_cast<const float4 *>(St + (64 * q + r) * kStLd + c);
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    // ---- 4. trailing update on the tensor cores: pairs of tile rows x pairs of tile columns
-    for (int I0 = K + 1; I0 < B.nt && !s_err; I0 += 2) {
-      const int I1 = I0 + 1;
-      const bool has0 = tr[I0].j0 <= K;
-      const bool has1 = I1 < B.nt && tr[I1].j0 <= K;
-      if (!has0 && !has1) continue;
-      load_split2(has0 ? tile_ptr(fac, tr[I0], K) : nullptr,
-                  has1 ? tile_ptr(fac, tr[I1], K) : nullptr, Ahi, Alo);
-      const int jmax = has1 ? I1 : I0;
-      for (int J0 = K + 1; J0 <= jmax && !s_err; J0 += 2) {
-        const int J1 = J0 + 1;
-        const bool hj0 = tr[J0].j0 <= K;
-        const bool hj1 = J1 <= jmax && J1 < B.nt && tr[J1].j0 <= K;
-        if (!hj0 && !hj1) continue;
-        load_split2(hj0 ? tile_ptr(fac, tr[J0], K) : nullptr,
-                    hj1 ? tile_ptr(fac, tr[J1], K) : nullptr, Bhi, Blo);
-        mma_3xtf32(tmem, Ahi, Alo, Bhi, Blo, kIdesc, &mbar, phase, &s_err, err);
-        // epilogue: warp w reads lanes 32 (w mod 4).. and column half w / 4 of D into the
-        // staging area (the B operands, free once the MMAs completed; rows padded to 132
-        // floats so that a quarter-warp's 16-byte stores hit 8 distinct bank groups), then
-        // all threads update the four global tiles with coalesced 16-byte read-modify-writes
-        {
-          const int rowq = warp & 3, jh = warp >> 2;
-          const int rr = 32 * rowq + lane;  // row of D
-          float v[64];
-          tmem_ld64(tmem + ((uint32_t)(32 * rowq) << 16) + (uint32_t)(64 * jh), v);
-          float *st = Dst + rr * kDstLd + 64 * jh;
-#pragma unroll
-          for (int c = 0; c < 64; c += 4)
-            *reinterpret_cast<float4 *>(st + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-        }
-        __syncthreads();
-        if (!s_err) {
-          // tile (I, J) of quadrant q: q & 1 -> I1, q >> 1 -> J1; all 16 loads of a thread
-          // are in flight before the first subtraction
-          constexpr int R = T * T / 4 / kThreads;  // 16-byte chunks per thread and tile
-          float *gq[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int I = (q & 1) ? I1 : I0, J = (q >> 1) ? J1 : J0;
-            const bool ok = ((q & 1) ? has1 : has0) && ((q >> 1) ? hj1 : hj0) && J <= I;
-            gq[q] = ok ? tile_ptr(fac, tr[I], J) : nullptr;
-          }
-          float4 x[4][R];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              const int e = tid + kThreads * j, r = e >> 4, c = 4 * (e & 15);
-              if (gq[q]) x[q][j] = *reinterpret_cast<const float4 *>(gq[q] + r * T + c);
-            }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (!gq[q]) continue;
-            const float *src = Dst + 64 * (q & 1) * kDstLd + 64 * (q >> 1);
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              const int e = tid + kThreads * j, r = e >> 4, c = 4 * (e & 15);
-              const float4 d = *reinterpret_cast<const float4 *>(src + r * kDstLd + c);
-              float4 v = x[q][j];
-              v.x -= d.x;
-              v.y -= d.y;
-              v.z -= d.z;
-              v.w -= d.w;
-              *reinterpret_cast<float4 *>(gq[q] + r * T + c) = v;
+        return false;
+      };
+      if (warp == 4) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+          for (int J = jlo; J < K; ++J) {
+            if (!pass_has(J)) continue;
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t sb = nb & 1;
+              if (nb >= 2 && !wait_phase(&ctl, &ctl.empty_b[sb], ((nb >> 1) - 1) & 1, err)) break;
+              if (ctl.abort) break;
+              unsigned char *dst = ringB + sb * kBStage;
+              const float *img = lc + 2 * tile_index(tr[K], J);
+              mbar_expect_tx(&ctl.full_b[sb], kBStage);
+              bulk_g2s(dst, img + h * (kHalf / 4), kHalf, &ctl.full_b[sb]);
+              bulk_g2s(dst + kHalf, img + (2 + h) * (kHalf / 4), kHalf, &ctl.full_b[sb]);
+              ++nb;
+              for (int p = 0; p < np; ++p) {
+                int I0, I1;
+                pair_rows(p, I0, I1);
+                if (!pair_has(I0, I1, J)) continue;
+                const uint32_t sa = na & 1;
+                if (na >= 2 && !wait_phase(&ctl, &ctl.empty_a[sa], ((na >> 1) - 1) & 1, err))
+                  break;
+                if (ctl.abort) break;
+                unsigned char *da = ringA + sa * kAStage;
+                const float *i0 = tr[I0].j0 <= J ? lc + 2 * tile_index(tr[I0], J) : nullptr;
+                const float *i1 =
+                    (I1 >= 0 && tr[I1].j0 <= J) ? lc + 2 * tile_index(tr[I1], J) : nullptr;
+                mbar_expect_tx(&ctl.full_a[sa], kAStage);
+                bulk_g2s(da, i0 ? i0 + h * (kHalf / 4) : zero_img, kHalf, &ctl.full_a[sa]);
+                bulk_g2s(da + kHalf, i1 ? i1 + h * (kHalf / 4) : zero_img, kHalf,
+                         &ctl.full_a[sa]);
+                bulk_g2s(da + 2 * kHalf, i0 ? i0 + (2 + h) * (kHalf / 4) : zero_img, kHalf,
+                         &ctl.full_a[sa]);
+                bulk_g2s(da + 3 * kHalf, i1 ? i1 + (2 + h) * (kHalf / 4) : zero_img, kHalf,
+                         &ctl.full_a[sa]);
+                ++na;
+              }
             }
           }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+      } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+          uint32_t started = 0;  // bit p: pair p has its first product in this pass
+          for (int J = jlo; J < K && !ctl.abort; ++J) {
+            if (!pass_has(J)) continue;
+            for (int h = 0; h < 2 && !ctl.abort; ++h) {
+              const uint32_t sb = nb & 1;
+              if (!wait_phase(&ctl, &ctl.full_b[sb], (nb >> 1) & 1, err)) break;
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t bh = smem_u32(ringB + sb * kBStage), bl = bh + kHalf;
+              for (int p = 0; p < np; ++p) {
+                int I0, I1;
+                pair_rows(p, I0, I1);
+                if (!pair_has(I0, I1, J)) continue;
+                const uint32_t sa = na & 1;
+                if (!wait_phase(&ctl, &ctl.full_a[sa], (na >> 1) & 1, err)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ah = smem_u32(ringA + sa * kAStage), al = ah + 2 * kHalf;
+                mma_3x(tmem + 64 * p, ah, al, bh, bl, 1024, 4, (started >> p) & 1u);
+                started |= 1u << p;
+                mma_commit(&ctl.empty_a[sa]);
+                ++na;
+              }
+              mma_commit(&ctl.empty_b[sb]);
+              ++nb;
+            }
+          }
+          mma_commit(&ctl.acc_ready);
+          // TRSM of every pair, once the epilogue has staged its operand
+          for (int p = 0; p < np; ++p) {
+            if (!wait_phase(&ctl, &ctl.trsm_ready, ph_ready & 1, err)) break;
+            ++ph_ready;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(Ax), al = ah + 32768;
+            const uint32_t bh = smem_u32(Binv), bl = bh + 16384;
+            mma_3x(tmem + 64 * p, ah, al, bh, bl, 2048, 8, false);
+            mma_commit(&ctl.trsm_done);
+          }
+        }
+      } else {
+        // ---------------------------------------------------------------- epilogue (0-3)
+        const int t = tid;  // accumulator row
+        // tcgen05.ld is warp-collective: every decision before one is made warp-uniform
+        bool ok = __all_sync(0xffffffffu, wait_phase(&ctl, &ctl.acc_ready, ph_acc & 1, err));
+        ++ph_acc;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        if (p0 == 0) {
+          // diagonal tile: S = G_KK - D_K (rows 0..63 of pair 0)
+          float d[64];
+          int I0, I1;
+          pair_rows(0, I0, I1);
+          const bool acc0 = jlo < K;
+          if (acc0 && ok) {
+            tmem_ld64(tmem + lane_base, d);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) d[c] = 0.f;
+          }
+          if (t < T) {
+            const float *g = fac + tile_index(tr[K], K) + t * T;
+#pragma unroll
+            for (int c = 0; c < T; c += 4) {
+              const float4 x = *reinterpret_cast<const float4 *>(g + c);
+              S[t * LDS + c] = c <= t ? x.x - d[c] : 0.f;
+              S[t * LDS + c + 1] = c + 1 <= t ? x.y - d[c + 1] : 0.f;
+              S[t * LDS + c + 2] = c + 2 <= t ? x.z - d[c + 2] : 0.f;
+              S[t * LDS + c + 3] = c + 3 <= t ? x.w - d[c + 3] : 0.f;
+            }
+          }
+          epi_sync();
+          // unblocked right-looking factorisation with deferred column scaling
+          const int tr8 = t >> 4, tc8 = t & 15;  // 8 x 16 threads
+          for (int j = 0; j < T; ++j) {
+            float dj = S[j * LDS + j];
+            if (t == 0 && K * T + j < B.m) ctl.pmin = fmin(ctl.pmin, (double)dj);
+            if (!(dj > 0.f) || !isfinite(dj)) {
+              if (t == 0) ctl.fail = 1;
+              dj = 1.f;
+            }
+            const float inv = 1.f / dj;
+            for (int i = j + 1 + tr8; i < T; i += 8) {
+              const float x = S[i * LDS + j] * inv;
+              for (int k = j + 1 + tc8; k <= i; k += 16)
+                S[i * LDS + k] = fmaf(-x, S[k * LDS + j], S[i * LDS + k]);
+            }
+            epi_sync();
+          }
+          for (int e = t; e < T * T; e += kEpi) {
+            const int i = e / T, j = e % T;
+            if (j > i) continue;
+            float dj = S[j * LDS + j];
+            if (!(dj > 0.f) || !isfinite(dj)) dj = 1.f;
+            Di[i * LDS + j] = i == j ? sqrtf(dj) : S[i * LDS + j] / sqrtf(dj);
+          }
+          epi_sync();
+          for (int e = t; e < T * T; e += kEpi) {
+            const int i = e / T, j = e % T;
+            S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.f;
+          }
+          epi_sync();
+          // inv(L_KK) by rows (2 threads per column, fixed-order sum)
+          {
+            const int c = t >> 1, q = t & 1;
+            for (int i = 0; i < T; ++i) {
+              float acc = 0.f;
+              if (c < i)
+                for (int k = c + q; k < i; k += 2) acc = fmaf(S[i * LDS + k], Di[k * LDS + c], acc);
+              acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+              if (q == 0) {
+                const float lii = S[i * LDS + i];
+                Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.f / lii : 0.f);
+              }
+              epi_sync();
+            }
+          }
+          float *gKK = fac + tile_index(tr[K], K);
+          float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+          for (int e = t; e < T * T; e += kEpi) {
+            const int r = e / T, c = e % T;
+            gKK[e] = c <= r ? S[r * LDS + c] : 0.f;
+            dK[e] = c <= r ? Di[r * LDS + c] : 0.f;
+          }
+          epi_sync();  // S / Di are read; the TRSM operands may overwrite them
+        }
+        // B operand of the TRSM: rows of inv(L_KK) (B[n][k] = inv(L_KK)[n][k]), full K
+        {
+          const float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+          for (int e = t; e < T * T; e += kEpi) {
+            const int n = e / T, k = e % T;
+            const float x = dK[e];
+            const float hi = tf32_hi(x);
+            *reinterpret_cast<float *>(Binv + full_off(n, k)) = hi;
+            *reinterpret_cast<float *>(Binv + 16384 + full_off(n, k)) = x - hi;
+          }
+        }
+        for (int p = 0; p < np; ++p) {
+          int I0, I1;
+          pair_rows(p, I0, I1);
+          const int I = t < T ? I0 : I1;
+          const bool real = I >= 0 && I != K;  // rows of this thread's tile to solve
+          // X = G_IK - D_I, split into the A operand (rows of the pair, full K)
+          const bool accp = ok && pair_has(I0, I1, jlo < K ? K - 1 : -1) && jlo < K;
+          float d[64];
+          if (accp) {
+            tmem_ld64(tmem + lane_base + 64 * p, d);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) d[c] = 0.f;
+          }
+          const float *g = real ? fac + tile_index(tr[I], K) + (t & 63) * T : nullptr;
+#pragma unroll
+          for (int c = 0; c < 64; c += 4) {
+            float4 x = real ? *reinterpret_cast<const float4 *>(g + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x.x -= d[c];
+            x.y -= d[c + 1];
+            x.z -= d[c + 2];
+            x.w -= d[c + 3];
+            if (!real) x = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            *reinterpret_cast<float4 *>(Ax + full_off(t, c)) = h;
+            *reinterpret_cast<float4 *>(Ax + 32768 + full_off(t, c)) =
+                make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(&ctl.trsm_ready);
+          ok = __all_sync(0xffffffffu, ok && wait_phase(&ctl, &ctl.trsm_done, ph_done & 1, err));
+          ++ph_done;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          float l[64];
+          if (ok) {
+            tmem_ld64(tmem + lane_base + 64 * p, l);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) l[c] = 0.f;
+          }
+          if (real && ok) {
+            const int r = t & 63;
+            float *o = fac + tile_index(tr[I], K) + r * T;
+            float *img = lc + 2 * tile_index(tr[I], K);
+#pragma unroll
+            for (int c = 0; c < 64; c += 4) {
+              const float4 v = make_float4(l[c], l[c + 1], l[c + 2], l[c + 3]);
+              *reinterpret_cast<float4 *>(o + c) = v;
+              const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+              // hi at K-half images 0 / 1, lo at 2 / 3
+              *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(img) + half_off(r, c)) = h;
+              *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(img) + 2 * kHalf +
+                                          half_off(r, c)) =
+                  make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            }
+          }
+        }
+        // the finished tiles are read by the next passes' bulk copies (async proxy)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
+      // end of the pass: the next one reads what this one wrote, and reuses tensor memory
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    __syncthreads();
   }
+  // Without an abort every copy the producer issued was waited for by the MMA thread.  After
+  // an abort the producer waits (bounded) for the last copy into each of its slots.
+  if (warp == 4 && lane == 0 && ctl.abort) {
+    auto drain = [&](uint64_t *full, uint32_t n) {
+      for (uint32_t s = 0; s < 2 && s < n; ++s) {
+        const uint32_t last = n - 1 - ((n - 1 - s) & 1);  // last use of slot s
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(&full[s], (last >> 1) & 1) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    };
+    drain(ctl.full_a, na);
+    drain(ctl.full_b, nb);
+  }
+  __syncthreads();
   if (tid == 0) {
-    pivmin[b] = s_pmin;
-    pivfail[b] = s_fail | s_err;
+    pivmin[b] = ctl.pmin;
+    pivfail[b] = ctl.fail | ctl.abort;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -500,22 +554,79 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
 }
 
-constexpr int kTcSmem = 4 * 32768 + (int)sizeof(float) * (2 * T * LD + 2 * T * LDS);
-// the epilogue staging area (128 x kDstLd floats from Bhi) fits in Bhi, Blo and At; the
-// TRSM staging area (128 x kStLd floats from At) in At, Bt and S, short of Di
-static_assert(128 * kDstLd * 4 <= 2 * 32768 + (int)sizeof(float) * T * LD, "staging area");
-static_assert(128 * kStLd <= 2 * T * LD + T * LDS, "TRSM staging area");
-static_assert(64 * kDstLd <= 2 * T * LD + T * LDS, "N-transform staging area");
+// N_KJ = inv(L_KK) L_KJ in place for every off-diagonal tile of row K (CUDA cores, FP32):
+// one CTA per tile row, 16 x 16 threads with 4 x 4 register tiles; inv(L_KK) is lower
+// triangular, so row block R of the output needs k < 16 (R + 1).
+__global__ void __launch_bounds__(256)
+    k_ntransform(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ rowblk_t,
+                 const TileRow *__restrict__ trow, float *__restrict__ fac,
+                 const float *__restrict__ dinv) {
+  __shared__ __align__(16) float Di[T][T + 4];  // Di[r][k]
+  __shared__ __align__(16) float L[T][T + 4];   // L[k][c]
+  const int row = blockIdx.x;                   // global tile row
+  const int b = rowblk_t[row];
+  const BlockDesc B = blk[b];
+  const int K = row - B.trow0;
+  const TileRow TK = trow[row];
+  if (TK.j0 >= K) return;
+  const int tid = threadIdx.x, tr4 = tid >> 4, tc4 = tid & 15;
+  const float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+  for (int e = tid; e < T * T; e += 256) Di[e / T][e % T] = dK[e];
+  for (int J = TK.j0; J < K; ++J) {
+    float *g = fac + TK.off + (int64_t)(J - TK.j0) * T * T;
+    __syncthreads();
+    for (int e = tid; e < T * T / 4; e += 256) {
+      const int k = e / (T / 4), c = 4 * (e % (T / 4));
+      *reinterpret_cast<float4 *>(&L[k][c]) = *reinterpret_cast<const float4 *>(g + k * T + c);
+    }
+    __syncthreads();
+    float acc[4][4] = {};
+    const int kend = 4 * tr4 + 4;  // k <= the thread's last row
+    for (int k = 0; k < kend; ++k) {
+      const float4 lv = *reinterpret_cast<const float4 *>(&L[k][4 * tc4]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float a = Di[4 * tr4 + i][k];
+        acc[i][0] = fmaf(a, lv.x, acc[i][0]);
+        acc[i][1] = fmaf(a, lv.y, acc[i][1]);
+        acc[i][2] = fmaf(a, lv.z, acc[i][2]);
+        acc[i][3] = fmaf(a, lv.w, acc[i][3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float4 *>(g + (4 * tr4 + i) * T + 4 * tc4) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+__global__ void k_tile_row_blocks(const BlockDesc *__restrict__ blk, int32_t nblk,
+                                  int32_t *__restrict__ rowblk_t) {
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const BlockDesc B = blk[b];
+  for (int I = threadIdx.x; I < B.nt; I += blockDim.x) rowblk_t[B.trow0 + I] = b;
+}
+
+constexpr int kTcSmem = (int)kRing;
+static_assert(2 * T * LDS * 4 <= 2 * kAStage, "diagonal scratch inside the A stages");
 
 }  // namespace
 
-void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                        const TileRow *trow, float *fac, float *dinv, double *pivmin,
+int64_t cholesky_tc_scratch_floats(int64_t factor_elems) { return 2 * factor_elems + kHalf / 4; }
+
+void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist, int32_t nblk,
+                        int32_t ntrow, const TileRow *trow, float *fac, float *dinv,
+                        float *scratch, int64_t factor_elems, int32_t *rowblk_t, double *pivmin,
                         int32_t *pivfail, int32_t *err, cudaStream_t s) {
   if (nlist <= 0) return;
+  float *zero_img = scratch + 2 * factor_elems;
+  cudaMemsetAsync(zero_img, 0, kHalf, s);
   cudaFuncSetAttribute(k_cholesky_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  k_cholesky_tc<<<(unsigned)nlist, kThreads, kTcSmem, s>>>(blk, blist, trow, fac, dinv, pivmin,
-                                                           pivfail, err);
+  k_cholesky_tc<<<(unsigned)nlist, kThreads, kTcSmem, s>>>(blk, blist, trow, fac, dinv, scratch,
+                                                           zero_img, pivmin, pivfail, err);
+  k_tile_row_blocks<<<(unsigned)nblk, 64, 0, s>>>(blk, nblk, rowblk_t);
+  k_ntransform<<<(unsigned)ntrow, 256, 0, s>>>(blk, rowblk_t, trow, fac, dinv);
 }
 
 }  // namespace cimmino

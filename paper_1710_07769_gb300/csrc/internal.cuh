@@ -210,9 +210,13 @@ struct FactorPtrs {
   float *dinvTP32;
 };
 
-// chol_tc.cu: FP32 blocks, trailing update on the tensor cores (tcgen05, 3xTF32)
-void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                        const TileRow *trow, float *fac, float *dinv, double *pivmin,
+// chol_tc.cu: FP32 blocks, left-looking on the tensor cores (tcgen05, 3xTF32), then the N
+// transform of every off-diagonal tile.  scratch: cholesky_tc_scratch_floats(factor elements)
+// floats (the split operand copy of L and a zero image); rowblk_t: one int per tile row.
+int64_t cholesky_tc_scratch_floats(int64_t factor_elems);
+void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlist, int32_t nblk,
+                        int32_t ntrow, const TileRow *trow, float *fac, float *dinv,
+                        float *scratch, int64_t factor_elems, int32_t *rowblk_t, double *pivmin,
                         int32_t *pivfail, int32_t *err, cudaStream_t s);
 
 // chol_kernels.cu
