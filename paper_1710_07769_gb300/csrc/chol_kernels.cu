@@ -18,7 +18,10 @@
 // the work that is zero by structure: the symmetric update of a diagonal tile computes
 // its 10 lower units only, and products with the triangular inv(L_KK) stop the k loop
 // where the triangle ends (k <= column for G inv^T, k <= row for inv L).  Work is then
-// close to the algorithmic count (plus the N transform).
+// close to the algorithmic count.  The N transform of row K runs afterwards in a kernel of
+// its own (every tile independent), and the diagonal scratch shares shared memory with the
+// operand tiles, so that three blocks run on an SM: while one block is in its latency-bound
+// diagonal factorisation, the others keep the FP64 pipe busy.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -102,7 +105,7 @@ __device__ __forceinline__ void unit_store(double *out, int R, int C, const doub
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_cholesky(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
                const TileRow *__restrict__ trow, double *__restrict__ fac,
                double *__restrict__ dinv, double *__restrict__ pivmin,
@@ -110,15 +113,17 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *At = reinterpret_cast<double *>(smem_raw);  // [T][LD]
   double *Bt = At + T * LD;                            // [T][LD]
-  double *S = Bt + T * LD;                             // [T][LDS]
-  double *Di = S + T * LDS;                            // [T][LDS]
+  double *S = At;                                      // [T][LDS], diagonal phase only
+  double *Di = Bt;                                     // [T][LDS], diagonal phase only
   __shared__ double s_pmin;
   __shared__ int s_fail;
+  __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
-  const TileRow *tr = trow + B.trow0;
   const int tid = threadIdx.x, warp = tid >> 5;
+  for (int I = tid; I < B.nt; I += kThreads) s_tr[I] = trow[B.trow0 + I];
+  const TileRow *tr = s_tr;
   const int tr4 = tid / 16, tc4 = tid % 16;
   if (tid == 0) {
     s_pmin = 1e300;
@@ -186,32 +191,10 @@ __global__ void __launch_bounds__(kThreads)
       gKK[e] = c <= r ? S[r * LDS + c] : 0.0;
       dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
     }
-    // Row K is final now: store N_KJ = inv(L_KK) L_KJ in place of L_KJ (J < K), so that
-    // the solves see L = diag(L_II) (I + N) and their sequential chains need no diagonal
-    // solve.  At[k][r] = Di(r, k) (lower: unit row block R needs k < 16 (R + 1)).
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int k = e / T, r = e % T;
-      At[k * LD + r] = Di[r * LDS + k];
-    }
-    for (int J = TK.j0; J < K; ++J) {
-      double *gKJ = tile_ptr(fac, TK, J);
-      __syncthreads();  // At ready / previous use of Bt finished
-      load_rowmajor(gKJ, Bt);
-      __syncthreads();
-      for (int u = warp; u < 16; u += kWarps) {
-        const int R = u >> 2, C = u & 3;
-        double acc[2][4];
-        unit_product(At, Bt, R, C, 16 * (R + 1), acc);
-        unit_store(gKJ, R, C, acc, false);
-      }
-    }
-    __syncthreads();
-    // Bt[k][c] = Di(c, k) for the TRSM below (upper triangle: unit column block C needs
-    // k < 16 (C + 1))
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int k = e / T, c = e % T;
-      Bt[k * LD + c] = Di[c * LDS + k];
-    }
+    __syncthreads();  // L_KK and inv(L_KK) are in global memory; S / Di are free
+    // Bt[k][c] = inv(L_KK)(c, k) for the TRSM below (upper triangle: unit column block C
+    // needs k < 16 (C + 1)); read back from dinv (L1-resident)
+    load_kmajor(dK, Bt);
     __syncthreads();
     // ---- 3. L_IK = G_IK * Di^T for every stored tile below the diagonal
     for (int I = K + 1; I < B.nt; ++I) {
@@ -376,7 +359,39 @@ __global__ void __launch_bounds__(kThreads)
                            f.dinvT32, reinterpret_cast<float *>(sm));
 }
 
-constexpr int kCholSmem = (int)sizeof(double) * (2 * T * LD + 2 * T * LDS);
+// N_KJ = inv(L_KK) L_KJ in place for every off-diagonal tile of tile row K of the listed
+// blocks (one CTA per block and tile row); inv(L_KK) is lower triangular, so unit row block R
+// needs k < 16 (R + 1).
+__global__ void __launch_bounds__(kThreads)
+    k_ntransform64(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
+                   const TileRow *__restrict__ trow, double *__restrict__ fac,
+                   const double *__restrict__ dinv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *At = reinterpret_cast<double *>(smem_raw);  // At[k][r] = inv(L_KK)(r, k)
+  double *Bt = At + T * LD;                            // Bt[k][c] = L_KJ(k, c)
+  const BlockDesc B = blk[blist[blockIdx.x]];
+  const int K = blockIdx.y;
+  if (K >= B.nt) return;
+  const TileRow TK = trow[B.trow0 + K];
+  if (TK.j0 >= K) return;
+  const int warp = threadIdx.x >> 5;
+  load_kmajor(dinv + B.dinv_off + (int64_t)K * T * T, At);
+  for (int J = TK.j0; J < K; ++J) {
+    double *g = tile_ptr(fac, TK, J);
+    __syncthreads();
+    load_rowmajor(g, Bt);
+    __syncthreads();
+    for (int u = warp; u < 16; u += kWarps) {
+      const int R = u >> 2, C = u & 3;
+      double acc[2][4];
+      unit_product(At, Bt, R, C, 16 * (R + 1), acc);
+      unit_store(g, R, C, acc, false);
+    }
+  }
+}
+
+constexpr int kCholSmem = (int)sizeof(double) * 2 * T * LD;
+static_assert(T * LDS <= T * LD, "diagonal scratch inside an operand tile");
 
 }  // namespace
 
@@ -387,6 +402,9 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
   cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
   k_cholesky<<<(unsigned)nlist, kThreads, kCholSmem, s>>>(blk, blist, trow, fac, dinv, pivmin,
                                                          pivfail);
+  cudaFuncSetAttribute(k_ntransform64, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
+  k_ntransform64<<<dim3((unsigned)nlist, kMaxBlockRows / T), kThreads, kCholSmem, s>>>(
+      blk, blist, trow, fac, dinv);
 }
 
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,

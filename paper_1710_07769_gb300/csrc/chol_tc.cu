@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ Ctl ctl;
   __shared__ int s_rows[T];  // panel rows (a block has at most 64 tile rows)
   __shared__ int s_nrows;
+  __shared__ TileRow s_tr[T];  // the block's tile-row table, read on every dependent step
   unsigned char *ringA = smem;                  // 2 x 32 KB
   unsigned char *ringB = smem + 2 * kAStage;    // 2 x 16 KB
   // outside the accumulation (ring idle): diagonal factor scratch, then TRSM operands
@@ -220,8 +221,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
-  const TileRow *tr = trow + B.trow0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int I = tid; I < B.nt; I += kThreads) s_tr[I] = trow[B.trow0 + I];
+  const TileRow *tr = s_tr;
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&ctl.full_a[s], 1);
