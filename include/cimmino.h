@@ -123,6 +123,14 @@ typedef struct cimmino_opts {
                           /* once the pool is warm); set both alloc and free to use */
                           /* the caller's allocator (e.g. a framework's caching     */
                           /* allocator), else EINVAL                                 */
+  int32_t tune;           /* 1: time the projection kernel's candidate configurations */
+                          /* (factor-tile ring depth; registers for one or two CTAs */
+                          /* per SM) on this context's blocks at setup and keep the */
+                          /* fastest; 0 (default): deepest ring, one CTA per SM.     */
+                          /* Results do not depend on the choice (same arithmetic).  */
+  const char *tune_cache; /* NULL, or a text file of tuned configurations keyed by   */
+                          /* GPU name, precision and block shape: read before tuning */
+                          /* (a hit skips the timing), appended after it             */
 } cimmino_opts;
 
 /* Statistics of one right-hand side of one system. */
@@ -148,6 +156,9 @@ typedef struct cimmino_stats {
                               /* per solved tile, 2 r_I r_J r_K per trailing product) */
   double t_chol_ms;           /* device time of the batched Cholesky launch alone    */
   int64_t nnz_gram;           /* entries of the exact Gram blocks G_i (sum over i)    */
+  int32_t proj_slots;         /* factor-tile ring depth of the projection kernel      */
+  int32_t proj_ctas_per_sm;   /* CTAs per SM its registers are budgeted for (1 or 2)  */
+  int32_t proj_tuned;         /* 0 default, 1 measured at setup, 2 from the cache     */
 } cimmino_stats;
 
 typedef struct cimmino_ctx cimmino_ctx;

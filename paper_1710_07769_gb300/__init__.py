@@ -56,7 +56,8 @@ class OptsStruct(C.Structure):
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("keep_aat", C.c_int32),
                 ("refine_relax", C.c_int32), ("multi_rhs", C.c_int32),
                 ("ruiz_sweeps", C.c_int32), ("time_proj", C.c_int32), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("tune", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 def torch_allocator():
@@ -90,7 +91,8 @@ class StatsStruct(C.Structure):
                 ("t_solve_ms", C.c_double), ("nnz_aat", C.c_int64), ("factor_bytes", C.c_int64),
                 ("pass_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("factor_flops", C.c_double), ("t_chol_ms", C.c_double),
-                ("nnz_gram", C.c_int64)]
+                ("nnz_gram", C.c_int64), ("proj_slots", C.c_int32),
+                ("proj_ctas_per_sm", C.c_int32), ("proj_tuned", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -184,7 +186,8 @@ def _check(L, code: int, ctx=None):
 def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
           pivot_ratio_min=None, max_iter=None, use_graph=None, check_every=None,
           keep_aat=False, refine_relax=None, multi_rhs=None, ruiz_sweeps=None,
-          time_proj=None, stream=None, allocator=None) -> OptsStruct:
+          time_proj=None, stream=None, allocator=None, tune=None,
+          tune_cache=None) -> OptsStruct:
     o = OptsStruct()
     L.cimmino_opts_default(C.byref(o))
     o.precision = {"fp64": FP64, "fp32_refine": FP32_REFINE}.get(precision, precision)
@@ -213,6 +216,10 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
     o.stream = stream
     if allocator is not None:
         o.alloc, o.free = allocator
+    if tune is not None:
+        o.tune = int(bool(tune))
+    if tune_cache is not None:
+        o.tune_cache = os.fsencode(tune_cache)
     return o
 
 

@@ -201,6 +201,8 @@ struct cimmino_ctx {
   std::vector<CtaDesc> hcta;
   int32_t max_mp = 0;
   int32_t proj_slots = 0, proj_slot_bytes = 0, proj_smem = 0, proj_wbytes = 8;
+  int32_t proj_minb = 1;  // CTAs per SM of the projection kernel (autotuned with opts.tune)
+  int32_t tuned = 0;      // 1: configuration measured here, 2: read from the tuning cache
   // matrices
   DBuf<int64_t> rp, cp, brp, crp;
   DBuf<int32_t> ci, ri, bci, cci, perm;
@@ -270,6 +272,8 @@ void opts_default(cimmino_opts *o) {
   o->alloc = nullptr;
   o->free = nullptr;
   o->alloc_user = nullptr;
+  o->tune = 0;
+  o->tune_cache = nullptr;
 }
 
 void check_opts(const cimmino_opts &o) {
@@ -288,6 +292,7 @@ void check_opts(const cimmino_opts &o) {
   if (o.time_proj != 0 && o.time_proj != 1) fail(CIMMINO_EINVAL, "opts.time_proj must be 0 or 1");
   if ((o.alloc == nullptr) != (o.free == nullptr))
     fail(CIMMINO_EINVAL, "opts.alloc and opts.free must be set together");
+  if (o.tune != 0 && o.tune != 1) fail(CIMMINO_EINVAL, "opts.tune must be 0 or 1");
 }
 
 // One NVTX range per stage (header-only NVTX 3: a no-op unless a profiler attaches), so
@@ -855,11 +860,122 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                   c->proj_slot_bytes);
   if (c->proj_slots < 2) fail(CIMMINO_EUNSUPPORTED, "block too large for the projection kernel");
   c->proj_smem = proj_smem_bytes(c->max_mp, c->proj_slots, c->proj_slot_bytes, c->proj_wbytes);
+  c->proj_minb = 1;
   CUDA_TRY(set_proj_smem_attr(c->proj_smem));
   if (!c->err_flag.p) c->err_flag.alloc(1);
   CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ projection autotuner
+// The projection kernel's free parameters: the depth of its factor-tile ring and whether
+// its registers are budgeted for one or two CTAs per SM (a second block then fills the
+// first one's chain barriers, at the price of a shallower ring).  Candidates are timed on
+// the context's own blocks (a few launches on a fixed vector) and the fastest is kept; with
+// opts.tune_cache the choice is stored per (GPU, precision, block shape) and reused.
+struct ProjConfig {
+  int32_t minb, slots;
+};
+
+std::string tune_key(const cimmino_ctx *c) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, c->device);
+  int64_t tiles = 0;
+  for (const auto &B : c->hblk)
+    for (int32_t I = 0; I < B.nt; ++I)
+      tiles += (I - c->htrow[B.trow0 + I].j0) + (c->htrowT[B.trow0 + I].j0 - I) + 2;
+  std::string name(prop.name);
+  for (char &ch : name)
+    if (ch == ' ' || ch == '|') ch = '_';
+  return name + "|" + (c->proj_wbytes == 8 ? "fp64" : "fp32") + "|mp" +
+         std::to_string(c->max_mp) + "|blocks" + std::to_string(c->hblk.size()) + "|tiles" +
+         std::to_string(tiles);
+}
+
+bool tune_cache_read(const char *path, const std::string &key, ProjConfig &cfg) {
+  if (!path) return false;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[400];
+    int minb = 0, slots = 0;
+    if (std::sscanf(line, "%399s %d %d", k, &minb, &slots) == 3 && key == k &&
+        (minb == 1 || minb == 2) && slots >= 2 && slots <= kMaxProjSlots) {
+      cfg = {minb, slots};
+      found = true;  // the last entry for a key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_cache_write(const char *path, const std::string &key, const ProjConfig &cfg) {
+  if (!path) return;
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;  // an unwritable cache only costs a re-tune next time
+  std::fprintf(f, "%s %d %d\n", key.c_str(), cfg.minb, cfg.slots);
+  std::fclose(f);
+}
+
+__global__ void k_fill(double *v, int64_t n, double x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = x;
+}
+
+void apply_proj_config(cimmino_ctx *c, const ProjConfig &cfg) {
+  c->proj_minb = cfg.minb;
+  c->proj_slots = cfg.slots;
+  c->proj_smem = proj_smem_bytes(c->max_mp, c->proj_slots, c->proj_slot_bytes, c->proj_wbytes);
+  CUDA_TRY(set_proj_smem_attr(c->proj_smem));
+  c->args.proj_minb = c->proj_minb;
+  c->args.proj_slots = c->proj_slots;
+  c->args.proj_smem = c->proj_smem;
+}
+
+void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs);
+
+void tune_projection(cimmino_ctx *c) {
+  const std::string key = tune_key(c);
+  ProjConfig best{c->proj_minb, c->proj_slots};
+  if (tune_cache_read(c->opts.tune_cache, key, best)) {
+    ensure_solve_buffers(c, 1);
+    apply_proj_config(c, best);
+    c->tuned = 2;
+    return;
+  }
+  ensure_solve_buffers(c, 1);
+  cudaStream_t s = c->stream;
+  const int64_t N = c->N;
+  k_fill<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(c->u.p, N, 1.0);
+  std::vector<ProjConfig> cand;
+  const int base = proj_smem_bytes(c->max_mp, 0, 0, c->proj_wbytes);
+  const int max1 = std::min(kMaxProjSlots, (kProjSmemMax - base) / c->proj_slot_bytes);
+  cand.push_back({1, max1});
+  if (max1 > 8) cand.push_back({1, 8});
+  // two CTAs per SM: half of the SM's shared memory each (less the static part)
+  const int max2 = std::min(kMaxProjSlots, (kProjSmemMax / 2 - 2048 - base) / c->proj_slot_bytes);
+  if (max2 >= 2) cand.push_back({2, max2});
+  Timer tm;
+  double best_ms = 1e300;
+  for (const ProjConfig &cfg : cand) {
+    apply_proj_config(c, cfg);
+    launch_proj(c->args, c->u.p, c->y.p, 0, s);  // warm-up
+    tm.start(s);
+    constexpr int kReps = 3;
+    for (int r = 0; r < kReps; ++r) launch_proj(c->args, c->u.p, c->y.p, 0, s);
+    CUDA_TRY(cudaGetLastError());
+    const double ms = tm.stop_ms(s) / kReps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cfg;
+    }
+  }
+  apply_proj_config(c, best);
+  c->tuned = 1;
+  tune_cache_write(c->opts.tune_cache, key, best);
 }
 
 // ------------------------------------------------------------------ solve
@@ -946,6 +1062,7 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.max_mp = c->max_mp;
   a.proj_smem = c->proj_smem;
   a.proj_slots = c->proj_slots;
+  a.proj_minb = c->proj_minb;
   a.proj_slot_bytes = c->proj_slot_bytes;
   a.proj_wbytes = c->proj_wbytes;
   // several right-hand sides: groups of 16 (FP32 factors) or 8 share each factor tile,
@@ -1110,6 +1227,9 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.factor_flops = c->factor_flops;
         o.t_chol_ms = c->t_chol_ms;
         o.nnz_gram = c->nnz_bd;
+        o.proj_slots = c->proj_slots;
+        o.proj_ctas_per_sm = c->proj_minb;
+        o.proj_tuned = c->tuned;
         o.pass_bytes = c->pass_bytes;
         // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
         o.kernel_launches =
@@ -1187,6 +1307,7 @@ int cimmino_setup_batch(int32_t nsys, const cimmino_csr *A, const int32_t *K,
     c->mem.stream = c->stream;
     AllocScope scope(&c->mem);
     setup_impl(c, nsys, A, K, perm, block_ptr);
+    if (c->opts.tune) tune_projection(c);
   } catch (const Error &e) {
     int code = set_error(nullptr, e);
     if (c->stream) cudaStreamSynchronize(c->stream);

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   __shared__ double s_pmin;
   __shared__ int s_fail;
   __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
+  __shared__ double s_rcp[T], s_d[T];            // pivots and their reciprocals
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
@@ -137,28 +138,42 @@ __global__ void __launch_bounds__(kThreads, 3)
     // ---- 1. diagonal tile, right-looking with the column scaling deferred: step j
     // subtracts S_ij S_kj / d_j from the trailing triangle (one barrier per column);
     // afterwards L_jj = sqrt(d_j) and L_ij = S_ij / sqrt(d_j)
+    // Divisions and square roots run as long FP64 sequences on GB300's narrow FP64 pipe,
+    // whose cost is per warp instruction: each reciprocal is computed by one warp only
+    // (warp 0, lane 0) and shared, never by every warp.
     for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
     __syncthreads();
     for (int j = 0; j < T; ++j) {
-      double dj = S[j * LDS + j];
-      if (tid == 0 && K * T + j < B.m) s_pmin = fmin(s_pmin, dj);
-      if (!(dj > 0.0) || !isfinite(dj)) {
-        if (tid == 0) s_fail = 1;
-        dj = 1.0;
+      if (tid == 0) {
+        double dj = S[j * LDS + j];
+        if (K * T + j < B.m) s_pmin = fmin(s_pmin, dj);
+        if (!(dj > 0.0) || !isfinite(dj)) {
+          s_fail = 1;
+          dj = 1.0;
+        }
+        s_rcp[j] = 1.0 / dj;
+        s_d[j] = dj;
       }
-      const double inv = 1.0 / dj;
+      __syncthreads();
+      const double inv = s_rcp[j];
       for (int i = j + 1 + tr4; i < T; i += 16) {
         const double t = S[i * LDS + j] * inv;
         for (int k = j + 1 + tc4; k <= i; k += 16) S[i * LDS + k] = fma(-t, S[k * LDS + j], S[i * LDS + k]);
       }
       __syncthreads();
     }
+    // L_jj = sqrt(d_j), L_ij = S_ij / sqrt(d_j): one square root and one reciprocal per
+    // column (warps 0 and 1), then products
+    if (tid < T) {
+      const double r = sqrt(s_d[tid]);
+      s_d[tid] = r;
+      s_rcp[tid] = 1.0 / r;
+    }
+    __syncthreads();
     for (int e = tid; e < T * T; e += kThreads) {
       const int i = e / T, j = e % T;
       if (j > i) continue;
-      double dj = S[j * LDS + j];
-      if (!(dj > 0.0) || !isfinite(dj)) dj = 1.0;
-      Di[i * LDS + j] = i == j ? sqrt(dj) : S[i * LDS + j] / sqrt(dj);  // L_KK, staged in Di
+      Di[i * LDS + j] = i == j ? s_d[j] : S[i * LDS + j] * s_rcp[j];  // L_KK, staged in Di
     }
     __syncthreads();
     for (int e = tid; e < T * T; e += kThreads) {
@@ -170,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     // depends on rows < i only, so all columns c of a row run in parallel (4 threads per
     // column split the sum, fixed-order shuffle reduction)
     {
+      // 1 / L_ii of every row is s_rcp (computed above from the same sqrt(d_i))
       const int c = tid >> 2, q = tid & 3;
       for (int i = 0; i < T; ++i) {
         double acc = 0.0;
@@ -178,8 +194,8 @@ __global__ void __launch_bounds__(kThreads, 3)
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (q == 0) {
-          const double lii = S[i * LDS + i];
-          Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.0 / lii : 0.0);
+          const double ri = s_rcp[i];
+          Di[i * LDS + c] = c < i ? -acc * ri : (c == i ? ri : 0.0);
         }
         __syncthreads();
       }

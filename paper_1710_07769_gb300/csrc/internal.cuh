@@ -289,6 +289,7 @@ struct IterArgs {
   int32_t max_mp;        // largest padded block (rows), sizes the projection smem
   int32_t proj_smem;     // dynamic shared memory bytes of the projection kernel
   int32_t proj_slots;    // factor-tile slots in the projection kernel's ring
+  int32_t proj_minb;     // CTAs per SM the projection kernel is compiled for (1 or 2)
   int32_t proj_slot_bytes;
   int32_t proj_wbytes;   // bytes per entry of the projection's working vectors (4 or 8)
   int32_t proj_rg;       // right-hand sides per group of the multi-RHS projection (0: off)

@@ -434,9 +434,11 @@ __device__ void producer_block(const IterArgs &a, const BlockDesc &B, const Ring
 }
 
 // ANY64: the context holds FP64 blocks (FP64 precision or fallbacks).  An all-FP32 context
-// runs the instance without the FP64 path.  RELAX: CG iterations with refine_relax.
-template <bool ANY64, bool RELAX>
-__global__ void __launch_bounds__(kProjThreads, 1)
+// runs the instance without the FP64 path.  RELAX: CG iterations with refine_relax.  MINB:
+// CTAs per SM the registers are budgeted for (1: a deep ring per block; 2: a shallower ring,
+// but a second block's chain steps fill the first one's barrier waits); the autotuner picks.
+template <bool ANY64, bool RELAX, int MINB>
+__global__ void __launch_bounds__(kProjThreads, MINB)
     k_proj(IterArgs a, const double *__restrict__ u, double *__restrict__ y, int check_lane) {
   __shared__ uint64_t full[kMaxProjSlots], empty[kMaxProjSlots];
   __shared__ double red[8];
@@ -511,8 +513,10 @@ int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes) {
 }
 
 cudaError_t set_proj_smem_attr(int bytes) {
-  const void *fs[4] = {(const void *)k_proj<false, false>, (const void *)k_proj<false, true>,
-                       (const void *)k_proj<true, false>, (const void *)k_proj<true, true>};
+  const void *fs[8] = {(const void *)k_proj<false, false, 1>, (const void *)k_proj<false, true, 1>,
+                       (const void *)k_proj<true, false, 1>,  (const void *)k_proj<true, true, 1>,
+                       (const void *)k_proj<false, false, 2>, (const void *)k_proj<false, true, 2>,
+                       (const void *)k_proj<true, false, 2>,  (const void *)k_proj<true, true, 2>};
   for (const void *f : fs) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -522,14 +526,17 @@ cudaError_t set_proj_smem_attr(int bytes) {
 }
 
 void launch_proj(const IterArgs &a, const double *u, double *y, int check_lane, cudaStream_t s) {
-  if (a.nrhs > 1 && a.proj_rg > 0)
+  if (a.nrhs > 1 && a.proj_rg > 0) {
     launch_proj_mr(a, u, y, check_lane, s);
-  else {
-    const bool any64 = a.proj_wbytes == 8, relax = a.refine_relax && check_lane;
-    auto k = any64 ? (relax ? k_proj<true, true> : k_proj<true, false>)
-                   : (relax ? k_proj<false, true> : k_proj<false, false>);
-    k<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
+    return;
   }
+  const bool any64 = a.proj_wbytes == 8, relax = a.refine_relax && check_lane;
+  auto k = a.proj_minb == 2
+               ? (any64 ? (relax ? k_proj<true, true, 2> : k_proj<true, false, 2>)
+                        : (relax ? k_proj<false, true, 2> : k_proj<false, false, 2>))
+               : (any64 ? (relax ? k_proj<true, true, 1> : k_proj<true, false, 1>)
+                        : (relax ? k_proj<false, true, 1> : k_proj<false, false, 1>));
+  k<<<a.nblk, kProjThreads, a.proj_smem, s>>>(a, u, y, check_lane);
 }
 
 }  // namespace cimmino

@@ -119,3 +119,32 @@ def test_torch_caching_allocator_callbacks():
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == before
     assert st1[0]["iters"] == st0[0]["iters"] and np.array_equal(x1, x0)
+
+
+def test_projection_autotuner_and_cache(tmp_path):
+    """opts.tune: candidate configurations of the projection kernel are timed on the
+    context's blocks and the fastest kept; the choice goes to the tuning cache and a second
+    context with the same block shape reads it instead of timing.  The arithmetic does not
+    depend on the choice, so the solves agree bit for bit with the untuned default."""
+    w = inputs.workload(1)
+    cache = tmp_path / "tune.txt"
+    x0, st0, _ = g.Solver(w.A, w.block_ptr, precision="fp32_refine").solve(w.F[0])
+    assert st0[0]["proj_tuned"] == 0 and st0[0]["proj_ctas_per_sm"] == 1
+    s1 = g.Solver(w.A, w.block_ptr, precision="fp32_refine", tune=True, tune_cache=str(cache))
+    x1, st1, c1 = s1.solve(w.F[0])
+    assert c1 == 0 and st1[0]["proj_tuned"] == 1
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and "|fp32|" in lines[0]
+    key, minb, slots = lines[0].split()
+    assert (int(minb), int(slots)) == (st1[0]["proj_ctas_per_sm"], st1[0]["proj_slots"])
+    s2 = g.Solver(w.A, w.block_ptr, precision="fp32_refine", tune=True, tune_cache=str(cache))
+    x2, st2, c2 = s2.solve(w.F[0])
+    assert st2[0]["proj_tuned"] == 2
+    assert (st2[0]["proj_ctas_per_sm"], st2[0]["proj_slots"]) == (int(minb), int(slots))
+    assert np.array_equal(x1, x0) and np.array_equal(x2, x0)
+    # the two-CTA variant is forced through a cache entry and still agrees bit for bit
+    cache.write_text(f"{key} 2 4\n")
+    s3 = g.Solver(w.A, w.block_ptr, precision="fp32_refine", tune=True, tune_cache=str(cache))
+    x3, st3, _ = s3.solve(w.F[0])
+    assert st3[0]["proj_ctas_per_sm"] == 2 and st3[0]["proj_slots"] == 4
+    assert np.array_equal(x3, x0)
