@@ -20,8 +20,10 @@
 // where the triangle ends (k <= column for G inv^T, k <= row for inv L).  Work is then
 // close to the algorithmic count.  The N transform of row K runs afterwards in a kernel of
 // its own (every tile independent), and the diagonal scratch shares shared memory with the
-// operand tiles, so that three blocks run on an SM: while one block is in its latency-bound
-// diagonal factorisation, the others keep the FP64 pipe busy.
+// operand tiles.  One block per SM: on the 512-block random workload (n = 2^20) the
+// factorisation took 79.9 ms with one, 87.3 ms with two and 99.7 ms with three blocks per
+// SM, so the launch reserves enough shared memory to keep the others off the SM (the rest
+// of the SM's 256 KB stays L1 for the tiles every product re-reads).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,7 +107,7 @@ __device__ __forceinline__ void unit_store(double *out, int R, int C, const doub
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 1)
     k_cholesky(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
                const TileRow *__restrict__ trow, double *__restrict__ fac,
                double *__restrict__ dinv, double *__restrict__ pivmin,
@@ -407,7 +409,11 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 constexpr int kCholSmem = (int)sizeof(double) * 2 * T * LD;
+// dynamic shared memory requested by k_cholesky: more than half of an SM's 228 KB, so that
+// one block runs per SM (measured fastest, see the header)
+constexpr int kCholSmemLaunch = 120 * 1024;
 static_assert(T * LDS <= T * LD, "diagonal scratch inside an operand tile");
+static_assert(kCholSmemLaunch >= kCholSmem, "launch reservation covers the tiles");
 
 }  // namespace
 
@@ -415,9 +421,9 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                      const TileRow *trow, double *fac, double *dinv, double *pivmin,
                      int32_t *pivfail, cudaStream_t s) {
   if (nlist <= 0) return;
-  cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
-  k_cholesky<<<(unsigned)nlist, kThreads, kCholSmem, s>>>(blk, blist, trow, fac, dinv, pivmin,
-                                                         pivfail);
+  cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemLaunch);
+  k_cholesky<<<(unsigned)nlist, kThreads, kCholSmemLaunch, s>>>(blk, blist, trow, fac, dinv,
+                                                               pivmin, pivfail);
   cudaFuncSetAttribute(k_ntransform64, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
   k_ntransform64<<<dim3((unsigned)nlist, kMaxBlockRows / T), kThreads, kCholSmem, s>>>(
       blk, blist, trow, fac, dinv);

@@ -102,6 +102,31 @@ def test_config3_full():
     assert abs(its["fp32_refine"] - its["fp64"]) <= 1, its
 
 
+def test_config3_graph_partition_full(tmp_path):
+    """The benchmark's workload and launch configuration: random n = 2^20, K = 512 blocks of
+    exactly 2048 rows from the graph partition of the row inner-product graph (Section 2),
+    projection autotuned.  Sampled factors against the oracle's dense Cholesky of the same
+    Gram blocks; solves by properties (true residual recomputed on the host, error against
+    x_true, FP32+refine within one iteration of FP64)."""
+    w = inputs.workload(3)
+    perm, bp, cut = g.partition_rip(w.A.n, g.aat(w.A), 512, cap=2048, seed=0)
+    assert np.all(np.diff(bp) == 2048)
+    o = oracle.Oracle(w.A, bp, perm=perm, factor=False, nthreads=os.cpu_count())
+    its, xs = {}, {}
+    for precision in ("fp32_refine", "fp64"):
+        s = g.Solver(w.A, bp, perm=perm, precision=precision, tune=True,
+                     tune_cache=str(tmp_path / "tune.txt"))
+        x, st, code = s.solve(w.F[0], tol=1e-10)
+        assert code == 0 and st[0]["rel_res"] <= 1e-10
+        assert true_relres(w.A, x, w.F[0]) <= 1.01e-10
+        assert rel(x, w.x_true[0]) <= 1e-8
+        its[precision], xs[precision] = st[0]["iters"], x
+        check_sampled_factors(s, o, [0, 255, 511])
+        s.close()
+    assert abs(its["fp32_refine"] - its["fp64"]) <= 1, its
+    assert_close(xs["fp32_refine"], xs["fp64"], 1e-8, "FP32+refine vs FP64")
+
+
 def test_config5_full_16rhs():
     """3D 128^3 (n = 2,097,152), K = 1024 blocks of 2048, 16 right-hand sides sharing
     the FP32 factors (FP64 refinement); every lane to 1e-10."""
