@@ -642,8 +642,12 @@ def run_profile(args):
         return 0
     multi = args.profile == "fp32_refine_16rhs"
     w = inputs.workload(args.config, nrhs=16 if multi else None)
-    s = g.Solver(w.A, w.block_ptr, perm=w.perm, precision="fp32_refine" if multi else args.profile,
-                 layout=args.layout, max_iter=4, check_every=1)
+    partition = args.partition or DEFAULT_PARTITION.get(args.config, "contiguous")
+    perm, bp, _ = partition_of(w, partition, args.config)
+    # the benchmark's launch configuration: the projection autotuned (candidate launches
+    # first, then the right-hand side's projection and the CG iterations)
+    s = g.Solver(w.A, bp, perm=perm, precision="fp32_refine" if multi else args.profile,
+                 layout=args.layout, max_iter=4, check_every=1, tune=True)
     x, st, code = s.solve(w.F if multi else w.F[0], tol=TOL)
     print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
                       "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
@@ -670,8 +674,9 @@ def main():
                     choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "cholesky_tc",
                              "cholesky_fp64", "spgemm"],
                     help="profiling target, nothing timed: fp64 / fp32_refine / "
-                         "fp32_refine_16rhs = one setup + 4 CG iterations of --config (16 "
-                         "right-hand sides for the last); cholesky_tc / cholesky_fp64 = setup "
+                         "fp32_refine_16rhs = one autotuned setup + 4 CG iterations of --config "
+                         "and its default blocks (16 right-hand sides for the last); "
+                         "cholesky_tc / cholesky_fp64 = setup "
                          "of 128 Gram blocks of 2048 rows of a random n = 2^18 system "
                          "(graph-partitioned unless --partition contiguous); spgemm = "
                          "standalone C = A A^T of --config")
