@@ -371,6 +371,12 @@ int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches);
  * it did not, EINVAL (limit_us outside [1, 1e6], NULL err_word), ECUDA, ENOMEM. */
 int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word);
 
+/* Benchmark hook: the FP64 FMA rate of the current device in TFLOP/s (2 flops per FMA),
+ * measured by a kernel of independent FMA chains on every SM (CUDA events, after a warm-up
+ * launch).  It is the ALU roofline of the FP64 kernels, which GB300's FP64 pipe bounds.
+ * Errors: EINVAL (NULL), ECUDA, ENOMEM. */
+int cimmino_fp64_peak(double *tflops);
+
 /* Library build information (compile-time architecture, version). */
 const char *cimmino_version(void);
 

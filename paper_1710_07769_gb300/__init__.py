@@ -20,7 +20,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["FP64", "FP32_REFINE", "DENSE", "SKYLINE", "CimminoError", "Solver", "BatchSolver",
-           "aat", "partition_rip", "sparsify_dense_columns", "selftest_wait", "load", "lib_path", "EXPORTS"]
+           "aat", "partition_rip", "sparsify_dense_columns", "selftest_wait", "fp64_peak", "load",
+           "lib_path", "EXPORTS"]
 
 FP64, FP32_REFINE = 0, 1
 DENSE, SKYLINE = 0, 1
@@ -36,7 +37,8 @@ EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimm
            "cimmino_project", "cimmino_project_rhs", "cimmino_sweeps", "cimmino_aat",
            "cimmino_aat_noalloc",
            "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_proj_timing",
-           "cimmino_selftest_wait", "cimmino_time_kernels", "cimmino_version"]
+           "cimmino_selftest_wait", "cimmino_time_kernels", "cimmino_fp64_peak",
+           "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -151,6 +153,7 @@ def load(build_if_missing: bool = False):
         L.cimmino_time_kernels.argtypes = [vp, i32, vp]
         L.cimmino_proj_timing.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
         L.cimmino_selftest_wait.argtypes = [i32, C.POINTER(i32)]
+        L.cimmino_fp64_peak.argtypes = [C.POINTER(dbl)]
         L.cimmino_partition_rip.argtypes = [i64, vp, vp, vp, i32, i32, C.c_uint64, vp, vp,
                                             C.POINTER(dbl)]
         L.cimmino_sparsify_dense_columns.argtypes = [i64, vp, vp, vp, vp, vp, vp,
@@ -496,6 +499,14 @@ def selftest_wait(limit_us: int = 2000):
     word = C.c_int32(0)
     code = L.cimmino_selftest_wait(int(limit_us), C.byref(word))
     return code, word.value
+
+
+def fp64_peak() -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s (the FP64 ALU roofline)."""
+    L = load()
+    t = C.c_double(0.0)
+    _check(L, L.cimmino_fp64_peak(C.byref(t)))
+    return t.value
 
 
 def sparsify_dense_columns(A):

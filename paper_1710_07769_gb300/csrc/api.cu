@@ -1428,6 +1428,32 @@ int cimmino_get_aat(cimmino_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, double
   }
 }
 
+int cimmino_fp64_peak(double *tflops) {
+  if (!tflops) {
+    g_last_error = "invalid argument (NULL tflops)";
+    return CIMMINO_EINVAL;
+  }
+  try {
+    OwnedStream os;
+    CUDA_TRY(cudaStreamCreateWithFlags(&os.s, cudaStreamNonBlocking));
+    Allocator mem;
+    mem.stream = os.s;
+    AllocScope scope(&mem);
+    DBuf<double> sink;
+    sink.alloc(1);
+    Timer tm;
+    int64_t fmas = 0;
+    const double ms = launch_dfma_probe(1 << 14, sink.p, os.s, tm.a, tm.b, &fmas);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(os.s));
+    if (!(ms > 0.0)) fail(CIMMINO_ECUDA, "the probe's timing failed");
+    *tflops = 2.0 * (double)fmas / (ms * 1e-3) / 1e12;
+    return CIMMINO_OK;
+  } catch (const Error &e) {
+    return set_error(nullptr, e);
+  }
+}
+
 int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word) {
   if (limit_us < 1 || limit_us > 1000000 || !err_word) {
     g_last_error = "limit_us must be in [1, 1e6] and err_word non-NULL";

@@ -318,6 +318,10 @@ int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_smem_attr(int bytes);
 // watchdog self-test: a bounded wait on an mbarrier nothing completes; sets bit 8 of *err
 void launch_wait_selftest(uint64_t limit_ns, int32_t *err, cudaStream_t s);
+// FP64 FMA throughput probe on every SM: returns the device milliseconds of `iters` rounds of
+// 8 FMA chains per thread and writes the number of FMAs to *fmas
+double launch_dfma_probe(int iters, double *sink, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                         int64_t *fmas);
 // proj_mr.cu: groups of rg right-hand sides share every factor tile read
 int proj_mr_smem_bytes(int max_mp, int rg, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_mr_smem_attr(int rg, int bytes);

@@ -777,4 +777,40 @@ void launch_unscale_cols(double *x, const double *cs, int64_t N, int32_t nrhs, c
   k_unscale_cols<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, cs, N, nrhs);
 }
 
+
+// ----------------------------------------------------------------------------
+// FP64 FMA throughput probe: every thread runs 8 independent FMA chains; the result is
+// written only if it is NaN (never, for the given inputs), so the work cannot be dropped.
+namespace {
+__global__ void __launch_bounds__(256) k_dfma_probe(int iters, double a, double b, double *sink) {
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s != s) sink[0] = s;
+}
+}  // namespace
+
+double launch_dfma_probe(int iters, double *sink, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                         int64_t *fmas) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8;  // 8 CTAs x 256 threads per SM
+  k_dfma_probe<<<blocks, 256, 0, s>>>(iters / 8, 0.999999, 1e-9, sink);  // warm-up
+  cudaEventRecord(e0, s);
+  k_dfma_probe<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-9, sink);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *fmas = (int64_t)blocks * 256 * 8 * iters;
+  return ms;
+}
 }  // namespace cimmino
