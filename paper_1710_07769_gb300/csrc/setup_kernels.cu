@@ -291,6 +291,62 @@ __device__ int gather_candidates(const int64_t *__restrict__ rp, const int32_t *
   return U;
 }
 
+// Warp gather of the candidates of row i when the row has at most 32 entries: lane q looks
+// up column j_q's range in the transpose (all lanes at once), a warp scan gives each
+// column's offset in the candidate list, and then every lane fetches its candidates (and,
+// with val, the products a_ij a_rj) independently, so the row costs a few dependent loads
+// instead of a chain per column.  Candidates are in column order, rows increasing within a
+// column, the order of the serial gather.  Returns the total (entries beyond cap are not
+// written); key/val (optional): 64-bit (row << 32 | position of j in row i) and products.
+struct WarpCols {
+  int32_t off[32];
+  int64_t start[32];
+  double a[32];
+};
+
+__device__ int gather_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ va, const int64_t *__restrict__ cp,
+                           const int32_t *__restrict__ ri, const double *__restrict__ cv,
+                           int64_t i, WarpCols &wc, int32_t *rows, uint64_t *key, double *val,
+                           int cap, int lane) {
+  const int64_t q0 = rp[i];
+  const int nq = (int)(rp[i + 1] - q0);
+  int len = 0;
+  if (lane < nq) {
+    const int32_t j = ci[q0 + lane];
+    const int64_t s0 = cp[j];
+    len = (int)(cp[j + 1] - s0);
+    wc.start[lane] = s0;
+    if (val) wc.a[lane] = va[q0 + lane];
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane < nq) wc.off[lane] = incl - len;
+  const int U = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  const int lim = U < cap ? U : cap;
+  for (int t = lane; t < lim; t += 32) {
+    int lo = 0, hi = nq - 1;  // last column whose offset is <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (wc.off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int64_t e = wc.start[lo] + (t - wc.off[lo]);
+    const int32_t r = ri[e];
+    if (rows) rows[t] = r;
+    if (key) {
+      key[t] = ((uint64_t)(uint32_t)r << 32) | (uint32_t)lo;
+      val[t] = __dmul_rn(wc.a[lo], cv[e]);
+    }
+  }
+  __syncwarp();
+  return U;
+}
+
 template <int G>
 __device__ void bitonic_sort(int32_t *buf, int U, int gt) {
   int P = 1;
@@ -380,11 +436,15 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
                         int64_t N, int64_t *__restrict__ cnt, int32_t *__restrict__ ovf_list,
                         int32_t *__restrict__ ovf_n) {
   __shared__ int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
+  __shared__ WarpCols scols[kSpgemmWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
   int32_t *buf = sbuf[warp];
-  int U = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+  const int U = rp[i + 1] - rp[i] <= 32
+                    ? gather_warp(rp, ci, nullptr, cp, ri, nullptr, i, scols[warp], buf, nullptr,
+                                  nullptr, kSpgemmWarpCap, lane)
+                    : gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
   if (U > kSpgemmWarpCap) {
     if (lane == 0) {
       int slot = atomicAdd(ovf_n, 1);
@@ -438,36 +498,19 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
                        const int64_t *__restrict__ crp, int32_t *__restrict__ cci,
                        double *__restrict__ ccv) {
   __shared__ __align__(16) int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
+  __shared__ WarpCols scols[kSpgemmWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
   int32_t *buf = sbuf[warp];
-  const int64_t q0 = rp[i];
-  const int nq = (int)(rp[i + 1] - q0);
-  int64_t U64 = 0;
-  for (int qq = lane; qq < nq; qq += 32) {
-    const int32_t j = ci[q0 + qq];
-    U64 += cp[j + 1] - cp[j];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) U64 += __shfl_xor_sync(0xffffffffu, U64, o);
-  if (U64 <= kFillFast) {
-    const int U = (int)U64;
-    uint64_t *key = reinterpret_cast<uint64_t *>(buf);
-    double *val = reinterpret_cast<double *>(buf) + kFillFast;
-    int base = 0;
-    for (int qq = 0; qq < nq; ++qq) {
-      const int32_t j = ci[q0 + qq];
-      const double a = va[q0 + qq];
-      const int64_t s0 = cp[j];
-      const int len = (int)(cp[j + 1] - s0);
-      for (int t = lane; t < len; t += 32) {
-        key[base + t] = ((uint64_t)(uint32_t)ri[s0 + t] << 32) | (uint32_t)qq;
-        val[base + t] = __dmul_rn(a, cv[s0 + t]);
-      }
-      base += len;
-    }
-    __syncwarp();
+  const int nq = (int)(rp[i + 1] - rp[i]);
+  uint64_t *key = reinterpret_cast<uint64_t *>(buf);
+  double *val = reinterpret_cast<double *>(buf) + kFillFast;
+  // rows of at most 32 entries whose candidates fit the sort buffer: Gustavson's scheme
+  const int U = nq <= 32 ? gather_warp(rp, ci, va, cp, ri, cv, i, scols[warp], nullptr, key,
+                                       val, kFillFast, lane)
+                         : kFillFast + 1;
+  if (U <= kFillFast) {
     bitonic_sort_kv(key, val, U, lane);
     const int64_t w = crp[i];
     int total = 0;
@@ -487,10 +530,10 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
     }
     return;
   }
-  int U = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
-  if (U > kSpgemmWarpCap) return;  // CTA variant fills this row
-  bitonic_sort<32>(buf, U, lane);
-  int u = unique_compact<32>(buf, U, lane);
+  const int Ul = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+  if (Ul > kSpgemmWarpCap) return;  // CTA variant fills this row
+  bitonic_sort<32>(buf, Ul, lane);
+  int u = unique_compact<32>(buf, Ul, lane);
   int64_t w = crp[i];
   for (int t = lane; t < u; t += 32) {
     int32_t j = buf[t];
