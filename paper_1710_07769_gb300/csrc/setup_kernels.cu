@@ -347,6 +347,61 @@ __device__ int gather_warp(const int64_t *__restrict__ rp, const int32_t *__rest
   return U;
 }
 
+// Number of distinct candidate rows of row i (at most 32 entries) when there are at most
+// kHashCands candidates: a shared-memory hash set of kHashSlots slots (linear probing,
+// atomicCAS), no sort.  Returns -1 when the row has more candidates.
+constexpr int kHashSlots = kSpgemmWarpCap;  // the warp's 4 KB buffer
+constexpr int kHashCands = kHashSlots / 2;
+
+__device__ int count_unique_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
+                                 int64_t i, WarpCols &wc, int32_t *table, int lane) {
+  const int64_t q0 = rp[i];
+  const int nq = (int)(rp[i + 1] - q0);
+  int len = 0;
+  if (lane < nq) {
+    const int32_t j = ci[q0 + lane];
+    const int64_t s0 = cp[j];
+    len = (int)(cp[j + 1] - s0);
+    wc.start[lane] = s0;
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane < nq) wc.off[lane] = incl - len;
+  const int U = __shfl_sync(0xffffffffu, incl, 31);
+  if (U > kHashCands) return -1;
+  for (int t = lane; t < kHashSlots; t += 32) table[t] = -1;
+  __syncwarp();
+  int mine = 0;
+  for (int t = lane; t < U; t += 32) {
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (wc.off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int32_t r = ri[wc.start[lo] + (t - wc.off[lo])];
+    uint32_t h = ((uint32_t)r * 2654435761u) >> 22;  // 10 bits: kHashSlots = 1024
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+      const int32_t prev = atomicCAS(&table[h], -1, r);
+      if (prev == -1) {
+        ++mine;
+        break;
+      }
+      if (prev == r) break;
+      h = (h + 1) & (kHashSlots - 1);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  __syncwarp();
+  return mine;
+}
+static_assert(kHashSlots == 1024, "the hash takes 10 bits");
+
 template <int G>
 __device__ void bitonic_sort(int32_t *buf, int U, int gt) {
   int P = 1;
@@ -441,6 +496,13 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
   int32_t *buf = sbuf[warp];
+  if (rp[i + 1] - rp[i] <= 32) {
+    const int u = count_unique_warp(rp, ci, cp, ri, i, scols[warp], buf, lane);
+    if (u >= 0) {
+      if (lane == 0) cnt[i] = u;
+      return;
+    }
+  }
   const int U = rp[i + 1] - rp[i] <= 32
                     ? gather_warp(rp, ci, nullptr, cp, ri, nullptr, i, scols[warp], buf, nullptr,
                                   nullptr, kSpgemmWarpCap, lane)
