@@ -190,6 +190,126 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// Cholesky L L^T of the 64 x 64 SPD tile in S (lower part read; L written in place, upper part
+// zeroed) and inv(L) into Di, by the 128 epilogue threads (t = 0..127), blocked in 16 x 16
+// sub-blocks so that the 64 pivots need 12 CTA-wide barriers instead of one each:
+//   for each block column k: one warp factors the diagonal sub-block (warp-synchronous), the
+//   rows below solve against it (one thread per row), the trailing lower triangle is updated;
+// then the inverse: each warp inverts one diagonal sub-block (a lane per column), and the
+// off-diagonal sub-blocks follow by distance d = i - k: Di_ik = -Di_ii sum_{k<=m<i} L_im Di_mk.
+// pmin receives the smallest pivot of the first `rows` rows; a pivot that is not positive
+// and finite sets *fail and is replaced by 1.  Tmp: 3 x 256 floats of scratch.
+__device__ void diag_factor_blocked(float *S, float *Di, float *Tmp, int t, int rows,
+                                    double *pmin, int *fail) {
+  const int warp = t >> 5, lane = t & 31;
+  for (int k = 0; k < 4; ++k) {
+    const int b0 = 16 * k;
+    if (warp == 0) {
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = b0 + jj;
+        float d = S[j * LDS + j];
+        if (lane == 0 && j < rows) *pmin = fmin(*pmin, (double)d);
+        if (!(d > 0.f) || !isfinite(d)) {
+          if (lane == 0) *fail = 1;
+          d = 1.f;
+        }
+        const float l = sqrtf(d), r = 1.f / l;
+        __syncwarp();
+        if (lane == 0) S[j * LDS + j] = l;
+        if (lane > jj && lane < 16) S[(b0 + lane) * LDS + j] *= r;
+        __syncwarp();
+        // rank-1 update of the block's remaining lower triangle
+        const int w = 15 - jj;
+        for (int e = lane; e < w * w; e += 32) {
+          const int i = jj + 1 + e / w, c = jj + 1 + e % w;
+          if (c <= i)
+            S[(b0 + i) * LDS + b0 + c] =
+                fmaf(-S[(b0 + i) * LDS + j], S[(b0 + c) * LDS + j], S[(b0 + i) * LDS + b0 + c]);
+        }
+        __syncwarp();
+      }
+    }
+    epi_sync();
+    // rows below: L_ik = S_ik L_kk^-T, forward substitution along the row, one thread per row
+    const int i = b0 + 16 + t;
+    if (i < T) {
+      float x[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float v = S[i * LDS + b0 + c];
+#pragma unroll
+        for (int m = 0; m < c; ++m) v = fmaf(-x[m], S[(b0 + c) * LDS + b0 + m], v);
+        x[c] = v / S[(b0 + c) * LDS + b0 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) S[i * LDS + b0 + c] = x[c];
+    }
+    epi_sync();
+    // trailing lower triangle: S_ic -= sum_m L_im L_cm over the block column
+    const int n = T - b0 - 16;
+    for (int e = t; e < n * n; e += kEpi) {
+      const int ii = b0 + 16 + e / n, c = b0 + 16 + e % n;
+      if (c > ii) continue;
+      float v = S[ii * LDS + c];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v = fmaf(-S[ii * LDS + b0 + m], S[c * LDS + b0 + m], v);
+      S[ii * LDS + c] = v;
+    }
+    epi_sync();
+  }
+  // zero the upper triangle of L
+  for (int e = t; e < T * T; e += kEpi) {
+    const int i = e / T, j = e % T;
+    if (j > i) S[i * LDS + j] = 0.f;
+  }
+  // inverse of every diagonal sub-block: warp k, lane c < 16 owns column c
+  {
+    const int b0 = 16 * warp;
+    if (lane < 16) {
+      const int c = lane;
+      for (int i = 0; i < 16; ++i) {
+        float v = 0.f;
+        if (i > c) {
+          for (int m = c; m < i; ++m) v = fmaf(-S[(b0 + i) * LDS + b0 + m], Di[(b0 + m) * LDS + b0 + c], v);
+          v = v / S[(b0 + i) * LDS + b0 + i];
+        } else if (i == c) {
+          v = 1.f / S[(b0 + i) * LDS + b0 + i];
+        }
+        Di[(b0 + i) * LDS + b0 + c] = v;
+      }
+    }
+  }
+  // the upper triangle of Di
+  for (int e = t; e < T * T; e += kEpi) {
+    const int i = e / T, j = e % T;
+    if (j > i) Di[i * LDS + j] = 0.f;
+  }
+  epi_sync();
+  for (int d = 1; d < 4; ++d) {
+    const int np = 4 - d;  // pairs (i, k = i - d), i = d..3
+    // Tmp_p = sum_{k <= m < i} L_im Di_mk
+    for (int e = t; e < np * 256; e += kEpi) {
+      const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
+      const int bi = d + p, bk = p;
+      float v = 0.f;
+      for (int m = 16 * bk; m < 16 * bi; ++m)
+        v = fmaf(S[(16 * bi + r) * LDS + m], Di[m * LDS + 16 * bk + c], v);
+      Tmp[e] = v;
+    }
+    epi_sync();
+    // Di_ik = -Di_ii Tmp
+    for (int e = t; e < np * 256; e += kEpi) {
+      const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
+      const int bi = d + p, bk = p;
+      float v = 0.f;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v = fmaf(Di[(16 * bi + r) * LDS + 16 * bi + m], Tmp[(p << 8) + m * 16 + c], v);
+      Di[(16 * bi + r) * LDS + 16 * bk + c] = -v;
+    }
+    epi_sync();
+  }
+}
+
 // The panel of column K: rows I >= K whose envelope reaches column K, in pairs.
 struct Panel {
   int rows[2 * 64];
@@ -397,51 +517,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
           }
           epi_sync();
-          // unblocked right-looking factorisation with deferred column scaling
-          const int tr8 = t >> 4, tc8 = t & 15;  // 8 x 16 threads
-          for (int j = 0; j < T; ++j) {
-            float dj = S[j * LDS + j];
-            if (t == 0 && K * T + j < B.m) ctl.pmin = fmin(ctl.pmin, (double)dj);
-            if (!(dj > 0.f) || !isfinite(dj)) {
-              if (t == 0) ctl.fail = 1;
-              dj = 1.f;
-            }
-            const float inv = 1.f / dj;
-            for (int i = j + 1 + tr8; i < T; i += 8) {
-              const float x = S[i * LDS + j] * inv;
-              for (int k = j + 1 + tc8; k <= i; k += 16)
-                S[i * LDS + k] = fmaf(-x, S[k * LDS + j], S[i * LDS + k]);
-            }
-            epi_sync();
-          }
-          for (int e = t; e < T * T; e += kEpi) {
-            const int i = e / T, j = e % T;
-            if (j > i) continue;
-            float dj = S[j * LDS + j];
-            if (!(dj > 0.f) || !isfinite(dj)) dj = 1.f;
-            Di[i * LDS + j] = i == j ? sqrtf(dj) : S[i * LDS + j] / sqrtf(dj);
-          }
-          epi_sync();
-          for (int e = t; e < T * T; e += kEpi) {
-            const int i = e / T, j = e % T;
-            S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.f;
-          }
-          epi_sync();
-          // inv(L_KK) by rows (2 threads per column, fixed-order sum)
-          {
-            const int c = t >> 1, q = t & 1;
-            for (int i = 0; i < T; ++i) {
-              float acc = 0.f;
-              if (c < i)
-                for (int k = c + q; k < i; k += 2) acc = fmaf(S[i * LDS + k], Di[k * LDS + c], acc);
-              acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-              if (q == 0) {
-                const float lii = S[i * LDS + i];
-                Di[i * LDS + c] = c < i ? -acc / lii : (c == i ? 1.f / lii : 0.f);
-              }
-              epi_sync();
-            }
-          }
+          diag_factor_blocked(S, Di, Di + T * LDS, t, B.m - K * T, &ctl.pmin, &ctl.fail);
           float *gKK = fac + tile_index(tr[K], K);
           float *dK = dinv + B.dinv_off + (int64_t)K * T * T;
           for (int e = t; e < T * T; e += kEpi) {
@@ -611,7 +687,7 @@ __global__ void k_tile_row_blocks(const BlockDesc *__restrict__ blk, int32_t nbl
 }
 
 constexpr int kTcSmem = (int)kRing;
-static_assert(2 * T * LDS * 4 <= 2 * kAStage, "diagonal scratch inside the A stages");
+static_assert((2 * T * LDS + 3 * 256) * 4 <= 2 * kAStage, "diagonal scratch inside the A stages");
 
 }  // namespace
 
