@@ -338,10 +338,8 @@ __device__ int gather_warp(const int64_t *__restrict__ rp, const int32_t *__rest
     const int64_t e = wc.start[lo] + (t - wc.off[lo]);
     const int32_t r = ri[e];
     if (rows) rows[t] = r;
-    if (key) {
-      key[t] = ((uint64_t)(uint32_t)r << 32) | (uint32_t)lo;
-      val[t] = __dmul_rn(wc.a[lo], cv[e]);
-    }
+    if (key) key[t] = ((uint64_t)(uint32_t)r << 32) | (uint32_t)lo;
+    if (val) val[t] = __dmul_rn(wc.a[lo], cv[e]);
   }
   __syncwarp();
   return U;
@@ -526,6 +524,11 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
 // the order of the row-wise definition (explicitly rounded products and sums, so the values
 // are those of a sequential loop).  Longer rows take the dot-product path below.
 constexpr int kFillFast = kSpgemmWarpCap / 4;  // 16-byte pairs in the warp's 4 KB buffer
+// rows with at most kHashFill candidates use a hash table (rows, products, table keys and
+// values: 24 bytes per candidate in the same 4 KB buffer)
+constexpr int kHashFillBits = 7;
+constexpr int kHashFill = 1 << kHashFillBits;
+static_assert(24 * kHashFill <= 4 * kSpgemmWarpCap, "hash fill inside the warp buffer");
 
 __device__ void bitonic_sort_kv(uint64_t *key, double *val, int U, int lane) {
   int P = 1;
@@ -569,6 +572,65 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
   uint64_t *key = reinterpret_cast<uint64_t *>(buf);
   double *val = reinterpret_cast<double *>(buf) + kFillFast;
   // rows of at most 32 entries whose candidates fit the sort buffer: Gustavson's scheme
+  if (nq <= 32) {
+    // up to kHashFill candidates: accumulate a_ij a_rj per candidate row r in a shared hash
+    // table, one column j after the other (so every r sums in increasing j), then place
+    // each distinct r at its rank among the row's distinct candidates (no sort)
+    int32_t *crow = buf;                                               // [kHashFill]
+    double *cval = reinterpret_cast<double *>(buf + kHashFill);        // [kHashFill]
+    int32_t *hk = buf + 3 * kHashFill;                                 // [kHashFill]
+    double *hv = reinterpret_cast<double *>(buf + 4 * kHashFill);      // [kHashFill]
+    const int Uh = gather_warp(rp, ci, va, cp, ri, cv, i, scols[warp], crow, nullptr, cval,
+                               kHashFill, lane);
+    if (Uh <= kHashFill) {
+      for (int t = lane; t < kHashFill; t += 32) hk[t] = -1;
+      __syncwarp();
+      const WarpCols &wc = scols[warp];
+      for (int q = 0; q < nq; ++q) {
+        const int t1 = q + 1 < nq ? wc.off[q + 1] : Uh;
+        for (int t = wc.off[q] + lane; t < t1; t += 32) {
+          const int32_t r = crow[t];
+          const double pr = cval[t];
+          uint32_t h = ((uint32_t)r * 2654435761u) >> (32 - kHashFillBits);
+          for (int probe = 0; probe < kHashFill; ++probe) {
+            const int32_t prev = atomicCAS(&hk[h], -1, r);
+            if (prev == -1) {
+              hv[h] = pr;
+              break;
+            }
+            if (prev == r) {
+              hv[h] = __dadd_rn(hv[h], pr);
+              break;
+            }
+            h = (h + 1) & (kHashFill - 1);
+          }
+        }
+        __syncwarp();
+      }
+      int total = 0;
+      for (int b0 = 0; b0 < kHashFill; b0 += 32) {
+        const int sl = b0 + lane;
+        const bool occ = hk[sl] >= 0;
+        const unsigned m = __ballot_sync(0xffffffffu, occ);
+        if (occ) {
+          const int pos = total + __popc(m & ((1u << lane) - 1u));
+          crow[pos] = hk[sl];
+          cval[pos] = hv[sl];
+        }
+        total += __popc(m);
+      }
+      __syncwarp();
+      const int64_t w = crp[i];
+      for (int e = lane; e < total; e += 32) {
+        const int32_t r = crow[e];
+        int rank = 0;
+        for (int m = 0; m < total; ++m) rank += crow[m] < r;
+        cci[w + rank] = r;
+        ccv[w + rank] = cval[e];
+      }
+      return;
+    }
+  }
   const int U = nq <= 32 ? gather_warp(rp, ci, va, cp, ri, cv, i, scols[warp], nullptr, key,
                                        val, kFillFast, lane)
                          : kFillFast + 1;
