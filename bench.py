@@ -370,6 +370,18 @@ def leg_config5(dev, stream, flush, layout, local, window=64):
                               "setup_ms": round(st[0]["t_setup_ms"], 3),
                               "factor_ms": round(st[0]["t_factor_ms"], 3),
                               "per_iter_ms": round(st[0]["t_solve_ms"] / (window + 1), 4)}
+        # the same FP32+refine iterations with the 16 lanes' triangular solves on the tensor
+        # cores (opts.multi_rhs = 2), over the FP64 leg's window
+        with torch.cuda.stream(stream):
+            s = g.Solver(dA, w.block_ptr, perm=w.perm, precision="fp32_refine", layout=layout,
+                         max_iter=window, multi_rhs=2)
+            X, st, code = s.solve(dF, tol=TOL, X=dX)
+        s.close()
+        nproj = (window + 1) * (len(w.block_ptr) - 1) * int(w.F.shape[0])
+        out["fp32_refine_tensor_cores_window"] = {
+            "iters": window, "mr_tc_blocks": st[0]["mr_tc_blocks"],
+            "per_iter_ms": round(st[0]["t_solve_ms"] / (window + 1), 4),
+            "refine_steps_per_inner_solve": round(st[0]["refine_steps_total"] / nproj, 3)}
     out["clocks"] = ck.summary()
     del dA, dF, dX
     return out
@@ -645,14 +657,34 @@ def run_profile(args):
                           "factor_gflop": st[0]["factor_flops"] / 1e9}))
         s.close()
         return 0
-    multi = args.profile == "fp32_refine_16rhs"
+    if args.profile == "mr_passes":
+        # live projection time (CUDA events around every projection of a 16-iteration window)
+        # of the 16-RHS workload: one pass, two passes and one residual, and to refine_tol,
+        # with the triangular solves on the tensor cores (multi_rhs 2) and on CUDA cores (1)
+        w = inputs.workload(args.config, nrhs=16)
+        res = {"profile": "mr_passes", "workload": w.name}
+        for mode in (2, 1):
+            for rm in (0, 1, None):
+                s = g.Solver(w.A, w.block_ptr, perm=w.perm, precision="fp32_refine",
+                             multi_rhs=mode, max_iter=16, time_proj=True, refine_max=rm)
+                x, st, code = s.solve(w.F, tol=TOL)
+                ms, n = s.proj_timing()
+                res[f"multi_rhs{mode}_refine_max{'default' if rm is None else rm}"] = {
+                    "proj_ms": round(ms / max(n, 1), 3),
+                    "refine_steps_per_inner_solve": round(
+                        st[0]["refine_steps_total"] / (max(n, 1) * 16 * (len(w.block_ptr) - 1)), 3)}
+                s.close()
+        print(json.dumps(res))
+        return 0
+    multi = args.profile in ("fp32_refine_16rhs", "fp32_refine_16rhs_tc")
     w = inputs.workload(args.config, nrhs=16 if multi else None)
     partition = args.partition or DEFAULT_PARTITION.get(args.config, "contiguous")
     perm, bp, _ = partition_of(w, partition, args.config)
     # the benchmark's launch configuration: the projection autotuned (candidate launches
     # first, then the right-hand side's projection and the CG iterations)
     s = g.Solver(w.A, bp, perm=perm, precision="fp32_refine" if multi else args.profile,
-                 layout=args.layout, max_iter=4, check_every=1, tune=True)
+                 layout=args.layout, max_iter=4, check_every=1, tune=True,
+                 multi_rhs=2 if args.profile == "fp32_refine_16rhs_tc" else None)
     x, st, code = s.solve(w.F if multi else w.F[0], tol=TOL)
     print(json.dumps({"profile": args.profile, "workload": w.name, "iters": st[0]["iters"],
                       "status": st[0]["status_name"], "factor_bytes": st[0]["factor_bytes"]}))
@@ -676,11 +708,13 @@ def main():
     ap.add_argument("--no-cfg2", action="store_true", help="skip the 64^3 leg")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 128^3 16-RHS leg")
     ap.add_argument("--profile", default=None,
-                    choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "cholesky_tc",
-                             "cholesky_fp64", "spgemm"],
+                    choices=["fp64", "fp32_refine", "fp32_refine_16rhs", "fp32_refine_16rhs_tc",
+                             "mr_passes", "cholesky_tc", "cholesky_fp64", "spgemm"],
                     help="profiling target, nothing timed: fp64 / fp32_refine / "
                          "fp32_refine_16rhs = one autotuned setup + 4 CG iterations of --config "
-                         "and its default blocks (16 right-hand sides for the last); "
+                         "and its default blocks (16 right-hand sides for the last two, _tc: "
+                         "FP32 triangular solves on the tensor cores); mr_passes = live "
+                         "projection times of the 16-RHS --config on both multi-RHS kernels; "
                          "cholesky_tc / cholesky_fp64 = setup "
                          "of 128 Gram blocks of 2048 rows of a random n = 2^18 system "
                          "(graph-partitioned unless --partition contiguous); spgemm = "

@@ -102,8 +102,12 @@ typedef struct cimmino_opts {
                           /* relative residual of the current x (inexact Krylov    */
                           /* subspace methods); 0 (default): refine_tol throughout  */
   int32_t multi_rhs;      /* 1 (default): with several right-hand sides, groups of  */
-                          /* 8 or 16 share every factor tile read; 0: one factor    */
-                          /* pass per right-hand side                               */
+                          /* 8 or 16 share every factor tile read (CUDA cores);     */
+                          /* 2: the same, with the FP32 blocks of up to 32 tile     */
+                          /* rows solved on the tensor cores (groups of 16, 3xTF32 */
+                          /* products accumulated in tensor memory, about 3x less   */
+                          /* accurate than FP32 FMAs: FP64 refinement may take one */
+                          /* more step); 0: one factor pass per right-hand side    */
   int32_t ruiz_sweeps;    /* sweeps of row and column infinity-norm equilibration  */
                           /* before the row 2-norm step (Section 3.1), 0..100;     */
                           /* 0 (default): off.  Column scaling changes H (it acts  */
@@ -159,6 +163,8 @@ typedef struct cimmino_stats {
   int32_t proj_slots;         /* factor-tile ring depth of the projection kernel      */
   int32_t proj_ctas_per_sm;   /* CTAs per SM its registers are budgeted for (1 or 2)  */
   int32_t proj_tuned;         /* 0 default, 1 measured at setup, 2 from the cache     */
+  int32_t mr_tc_blocks;       /* blocks whose multi-RHS projection (nrhs > 1) runs on  */
+                              /* the tensor cores; the others run on CUDA cores      */
 } cimmino_stats;
 
 typedef struct cimmino_ctx cimmino_ctx;

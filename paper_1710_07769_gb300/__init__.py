@@ -94,7 +94,8 @@ class StatsStruct(C.Structure):
                 ("pass_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("factor_flops", C.c_double), ("t_chol_ms", C.c_double),
                 ("nnz_gram", C.c_int64), ("proj_slots", C.c_int32),
-                ("proj_ctas_per_sm", C.c_int32), ("proj_tuned", C.c_int32)]
+                ("proj_ctas_per_sm", C.c_int32), ("proj_tuned", C.c_int32),
+                ("mr_tc_blocks", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -209,7 +210,9 @@ def _opts(L, precision=FP64, layout=SKYLINE, refine_max=None, refine_tol=None,
         o.check_every = int(check_every)
     o.keep_aat = int(bool(keep_aat))
     if multi_rhs is not None:
-        o.multi_rhs = int(bool(multi_rhs))
+        # True/1: shared factor reads on CUDA cores; 2: FP32 blocks on the tensor cores
+        o.multi_rhs = multi_rhs if isinstance(multi_rhs, int) and not isinstance(
+            multi_rhs, bool) else int(bool(multi_rhs))
     if refine_relax is not None:
         o.refine_relax = int(bool(refine_relax))
     if ruiz_sweeps is not None:

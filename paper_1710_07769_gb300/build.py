@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcimmino.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "setup_kernels.cu", "chol_kernels.cu", "chol_tc.cu", "solve_kernels.cu",
-           "proj_kernel.cu", "proj_mr.cu", "noalloc.cu", "partition.cpp"]
+           "proj_kernel.cu", "proj_mr.cu", "proj_mr_tc.cu", "noalloc.cu", "partition.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -214,6 +214,10 @@ struct cimmino_ctx {
   DBuf<double> aval, tval;
   DBuf<BlockDesc> blk;
   DBuf<int32_t> border;  // projection launch order (longest first)
+  std::vector<int32_t> hborder;
+  DBuf<int32_t> mr_list;  // multi-RHS launch order: tensor-core blocks first
+  int32_t mr_ntc = 0;     // blocks the tensor-core multi-RHS kernel takes
+  std::vector<unsigned char> tmaps;  // its 4 tensor maps (host copies, passed by value)
   DBuf<TileRow> trow;
   DBuf<SysDesc> sys;
   DBuf<CtaDesc> cta;
@@ -293,6 +297,7 @@ void check_opts(const cimmino_opts &o) {
   if ((o.alloc == nullptr) != (o.free == nullptr))
     fail(CIMMINO_EINVAL, "opts.alloc and opts.free must be set together");
   if (o.tune != 0 && o.tune != 1) fail(CIMMINO_EINVAL, "opts.tune must be 0 or 1");
+  if (o.multi_rhs < 0 || o.multi_rhs > 2) fail(CIMMINO_EINVAL, "opts.multi_rhs not in [0,2]");
 }
 
 // One NVTX range per stage (header-only NVTX 3: a no-op unless a profiler attaches), so
@@ -767,6 +772,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                        [&](int32_t x, int32_t y) { return work[x] > work[y]; });
       c->border.alloc(nblk);
       h2d(c->border.p, order.data(), nblk, s);
+      c->hborder = order;
     }
     c->trowT.alloc(ntrow);
     h2d(c->trowT.p, c->htrowT.data(), ntrow, s);
@@ -1085,6 +1091,38 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
       }
     }
   }
+  // with opts.multi_rhs == 2, FP32 blocks of up to 32 tile rows take the tensor-core kernel
+  // and the others (FP64 fallbacks, larger blocks) the CUDA-core one, in one launch each
+  const int32_t nblk = (int32_t)c->hblk.size();
+  std::vector<int32_t> ml = c->hborder;
+  c->mr_ntc = 0;
+  if (a.proj_rg > 0 && c->opts.multi_rhs == 2 && c->fac32.p && c->dinv32.p) {
+    std::vector<int32_t> tc, rest;
+    for (int32_t b : c->hborder) {
+      const BlockDesc &B = c->hblk[b];
+      (B.prec64 == 0 && B.nt <= proj_mr_tc_max_tiles() ? tc : rest).push_back(b);
+    }
+    const size_t mb = tile_map_bytes();
+    c->tmaps.assign(4 * mb, 0);
+    // the transposed factor is empty when no block has an off-diagonal tile: its map is
+    // then never read, and any valid array stands in
+    const float *ft = c->facT32.p ? c->facT32.p : c->dinv32.p;
+    const int64_t nft = c->facT32.p ? (int64_t)c->facT32.n : (int64_t)c->dinv32.n;
+    if (!tc.empty() && make_tile_map(&c->tmaps[0], c->fac32.p, (int64_t)c->fac32.n) &&
+        make_tile_map(&c->tmaps[mb], ft, nft) &&
+        make_tile_map(&c->tmaps[2 * mb], c->dinv32.p, (int64_t)c->dinv32.n) &&
+        make_tile_map(&c->tmaps[3 * mb], c->dinvT32.p, (int64_t)c->dinvT32.n)) {
+      CUDA_TRY(set_proj_mr_tc_smem_attr());
+      ml = tc;
+      ml.insert(ml.end(), rest.begin(), rest.end());
+      c->mr_ntc = (int32_t)tc.size();
+    }
+  }
+  c->mr_list.alloc(nblk);
+  h2d(c->mr_list.p, ml.data(), nblk, c->stream);
+  a.mr_list = c->mr_list.p;
+  a.mr_ntc = c->mr_ntc;
+  a.mr_tmaps = c->tmaps.empty() ? nullptr : c->tmaps.data();
   a.err = c->err_flag.p;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -1230,10 +1268,13 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.proj_slots = c->proj_slots;
         o.proj_ctas_per_sm = c->proj_minb;
         o.proj_tuned = c->tuned;
+        o.mr_tc_blocks = nrhs > 1 ? c->mr_ntc : 0;
         o.pass_bytes = c->pass_bytes;
-        // rhs scale, xi projection, A^T y, CG init, 5 kernels per iteration, final stats
-        o.kernel_launches =
-            c->setup_launches + 5 + 5 * launched + (nrhs > 1 ? 1 : 0) + (a.cs ? 1 : 0);
+        // rhs scale, xi projection, A^T y, CG init, 4 kernels plus the projection per
+        // iteration, final stats; several right-hand sides may take two projection kernels
+        const int pk = (nrhs > 1 && c->mr_ntc > 0 && c->mr_ntc < (int32_t)c->hblk.size()) ? 2 : 1;
+        o.kernel_launches = c->setup_launches + 4 + pk + (4 + pk) * launched +
+                            (nrhs > 1 ? 1 : 0) + (a.cs ? 1 : 0);
       }
     }
   }

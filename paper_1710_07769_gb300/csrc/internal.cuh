@@ -295,6 +295,9 @@ struct IterArgs {
   int32_t proj_rg;       // right-hand sides per group of the multi-RHS projection (0: off)
   int32_t proj_mr_slots; // factor-tile slots of the multi-RHS projection's ring
   int32_t proj_mr_smem;  // dynamic shared memory bytes of the multi-RHS projection
+  const int32_t *mr_list;  // multi-RHS launch order: tensor-core blocks first, then the rest
+  int32_t mr_ntc;          // blocks at the front of mr_list taken by the tensor-core kernel
+  const void *mr_tmaps;    // host array of 4 tensor maps (fac32, facT32, dinv32, dinvT32)
   int32_t *err;          // device error word: bounded waits that ran out
   int32_t max_iter;
   int32_t refine_relax;  // 1: inner tolerance min(1e-6, refine_tol / relres_t) in iterations
@@ -314,6 +317,41 @@ __device__ __forceinline__ double inner_tol(const IterArgs &a, int check_lane, i
   return fmin(1e-6, a.refine_tol / fmax(rr, 1e-300));
 }
 
+// FP64 refinement residual of row r (block-local) for a group of RG right-hand sides:
+// acc[g] -= sum_c G_rc y[c][g] over the row's entries in the sliced-ELL Gram copy (in entry
+// order), for the active g (bit g of mask).  y rows are [ld] doubles, the group at column k0.
+// A full group with an even row length reads each y row as 16-byte pairs.
+template <int RG>
+__device__ __forceinline__ void gram_row_residual(const IterArgs &a, const BlockDesc &B, int r,
+                                                  const double *__restrict__ y, int64_t ld,
+                                                  int k0, uint32_t mask, double (&acc)[RG]) {
+  const int sl = B.slice0 + (r >> 5), l = r & 31;
+  const int64_t o = a.soff[sl];
+  const int wd = (int)((a.soff[sl + 1] - o) >> 5);
+  const double *sv = a.sval + o + l;
+  const int16_t *sc = a.scol + o + l;
+  if (mask == (RG == 32 ? 0xffffffffu : (1u << RG) - 1u) && (ld & 1) == 0) {
+    for (int kk = 0; kk < wd; ++kk) {
+      const double gv = sv[32 * kk];
+      const double2 *yc = reinterpret_cast<const double2 *>(y + (B.row0 + sc[32 * kk]) * ld + k0);
+#pragma unroll
+      for (int h = 0; h < RG / 2; ++h) {
+        const double2 t = yc[h];
+        acc[2 * h] = fma(-gv, t.x, acc[2 * h]);
+        acc[2 * h + 1] = fma(-gv, t.y, acc[2 * h + 1]);
+      }
+    }
+  } else {
+    for (int kk = 0; kk < wd; ++kk) {
+      const double gv = sv[32 * kk];
+      const double *yc = y + (B.row0 + sc[32 * kk]) * ld + k0;
+#pragma unroll
+      for (int g = 0; g < RG; ++g)
+        if ((mask >> g) & 1u) acc[g] = fma(-gv, yc[g], acc[g]);
+    }
+  }
+}
+
 int proj_smem_bytes(int max_mp, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_smem_attr(int bytes);
 // watchdog self-test: a bounded wait on an mbarrier nothing completes; sets bit 8 of *err
@@ -322,6 +360,13 @@ void launch_wait_selftest(uint64_t limit_ns, int32_t *err, cudaStream_t s);
 // 8 FMA chains per thread and writes the number of FMAs to *fmas
 double launch_dfma_probe(int iters, double *sink, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
                          int64_t *fmas);
+// proj_mr_tc.cu: groups of 16 right-hand sides of FP32 blocks on the tensor cores
+int proj_mr_tc_max_tiles();
+size_t tile_map_bytes();
+bool make_tile_map(void *map, const float *base, int64_t elems);
+cudaError_t set_proj_mr_tc_smem_attr();
+void launch_proj_mr_tc(const IterArgs &a, const double *u, double *y, int check_lane,
+                       cudaStream_t s);
 // proj_mr.cu: groups of rg right-hand sides share every factor tile read
 int proj_mr_smem_bytes(int max_mp, int rg, int slots, int slot_bytes, int wbytes);
 cudaError_t set_proj_mr_smem_attr(int rg, int bytes);

@@ -347,18 +347,7 @@ __device__ void mr_block(const IterArgs &a, const BlockDesc &B, const Ring &R, W
         const double *ur = u + (B.row0 + r) * ld + k0;
 #pragma unroll
         for (int g = 0; g < RG; ++g) acc[g] = ((mask >> g) & 1u) ? ur[g] : 0.0;
-        const int sl = B.slice0 + (r >> 5), l = r & 31;
-        const int64_t o = a.soff[sl];
-        const int wd = (int)((a.soff[sl + 1] - o) >> 5);
-        const double *sv = a.sval + o + l;
-        const int16_t *sc = a.scol + o + l;
-        for (int kk = 0; kk < wd; ++kk) {
-          const double v = sv[32 * kk];
-          const double *yc = y + (B.row0 + sc[32 * kk]) * ld + k0;
-#pragma unroll
-          for (int g = 0; g < RG; ++g)
-            if ((mask >> g) & 1u) acc[g] = fma(-v, yc[g], acc[g]);
-        }
+        gram_row_residual<RG>(a, B, r, y, ld, k0, mask, acc);
 #pragma unroll
         for (int g = 0; g < RG; ++g) {
           wr[g] = W(acc[g]);
@@ -430,7 +419,8 @@ __global__ void __launch_bounds__(kProjThreads, 1)
   __shared__ double tmp[8 * RG], un2[RG], e2[RG];
   __shared__ int s_again, s_abort;
   extern __shared__ __align__(128) unsigned char dsm[];
-  const BlockDesc B = a.blk[a.border[blockIdx.x]];  // longest blocks first
+  // longest blocks first, after the ones the tensor-core kernel takes
+  const BlockDesc B = a.blk[a.mr_list[a.mr_ntc + blockIdx.x]];
   Ring R;
   R.base = dsm;
   R.full = full;
@@ -488,10 +478,13 @@ cudaError_t set_proj_mr_smem_attr(int rg, int bytes) {
 
 void launch_proj_mr(const IterArgs &a, const double *u, double *y, int check_lane,
                     cudaStream_t s) {
+  if (a.mr_ntc > 0) launch_proj_mr_tc(a, u, y, check_lane, s);
+  const int rest = a.nblk - a.mr_ntc;
+  if (rest <= 0) return;
   if (a.proj_rg == 16)
-    k_proj_mr<16><<<a.nblk, kProjThreads, a.proj_mr_smem, s>>>(a, u, y, check_lane);
+    k_proj_mr<16><<<rest, kProjThreads, a.proj_mr_smem, s>>>(a, u, y, check_lane);
   else
-    k_proj_mr<8><<<a.nblk, kProjThreads, a.proj_mr_smem, s>>>(a, u, y, check_lane);
+    k_proj_mr<8><<<rest, kProjThreads, a.proj_mr_smem, s>>>(a, u, y, check_lane);
 }
 
 }  // namespace cimmino

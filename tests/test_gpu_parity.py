@@ -284,11 +284,51 @@ def test_projection_multi_rhs_nonmonotone_envelope(precision, tol):
     A, bp = envelope_matrix()
     o = oracle.Oracle(A, bp)
     V = np.random.default_rng(3).standard_normal((16, A.n))
-    for multi in (True, False):
+    for multi in (2, True, False):  # tensor cores (FP32 blocks), CUDA cores, one per RHS
         s = g.Solver(A, bp, precision=precision, multi_rhs=multi)
         P = s.project(V)
         for k in range(16):
             assert_close(P[k], o.project(V[k]), tol, (multi, k))
+
+
+@pytest.mark.parametrize("nrhs", [3, 16, 21])
+def test_multi_rhs_tensor_cores_and_cuda_cores_match_oracle(sys_small, nrhs):
+    """Algorithm 2 step 5 for several right-hand sides sharing the FP32 factors: on the
+    tensor cores (multi_rhs = 2: 3xTF32 MMAs, W in tensor memory) and on CUDA cores
+    (multi_rhs = 1), each column element by element against the oracle's H v (Eq. 1.5);
+    the solve reports every block on the tensor-core kernel in the first case only."""
+    A, perm, f = sys_small
+    o = oracle.Oracle(A, RAGGED, perm=perm)
+    V = np.random.default_rng(100 + nrhs).standard_normal((nrhs, A.n))
+    F = np.stack([inputs.matvec(A, V[k]) for k in range(nrhs)])
+    ref = [o.project(V[k]) for k in range(nrhs)]
+    for mode, ntc in ((2, len(RAGGED) - 1), (1, 0)):
+        s = g.Solver(A, RAGGED, perm=perm, precision="fp32_refine", multi_rhs=mode)
+        P = s.project(V)
+        for k in range(nrhs):
+            assert_close(P[k], ref[k], 1e-10, (mode, k))
+        X, st, code = s.solve(F)
+        assert code == 0 and all(q["mr_tc_blocks"] == ntc for q in st), (mode, st[0])
+        for k in (0, nrhs - 1):
+            assert_close(X[k], V[k], 1e-8, (mode, k))
+        s.close()
+
+
+def test_multi_rhs_large_block_takes_cuda_cores():
+    """A block of 33 tile rows (2060 rows) is beyond the tensor-core kernel's 32; it runs
+    on the CUDA-core kernel in the same projection as the tensor-core blocks."""
+    A = inputs.random_dd(2600, 4, 17)
+    bp = np.array([0, 2060, 2071, 2600], np.int64)
+    o = oracle.Oracle(A, bp)
+    V = np.random.default_rng(31).standard_normal((16, A.n))
+    s = g.Solver(A, bp, precision="fp32_refine", multi_rhs=2)
+    P = s.project(V)
+    for k in (0, 7, 15):
+        assert_close(P[k], o.project(V[k]), 1e-10, k)
+    F = np.stack([inputs.matvec(A, V[k]) for k in range(16)])
+    X, st, code = s.solve(F)
+    assert code == 0 and st[0]["mr_tc_blocks"] == 2
+    assert_close(X[5], V[5], 1e-8)
 
 
 def test_solve_16_rhs_matches_oracle():
@@ -306,11 +346,14 @@ def test_solve_16_rhs_matches_oracle():
         assert st[k]["status"] == 0 and abs(st[k]["iters"] - ito) <= 1, (k, st[k]["iters"], ito)
         assert st[k]["rel_res"] <= 1e-10
         assert_close(X[k], xo, 1e-8)
-    # the same lanes through one factor pass per right-hand side
-    X2, st2, _ = g.Solver(w.A, w.block_ptr, precision="fp32_refine", multi_rhs=False).solve(F)
-    for k in range(16):
-        assert abs(st2[k]["iters"] - st[k]["iters"]) <= 1
-        assert_close(X2[k], X[k], 1e-8)
+    # the same lanes through one factor pass per right-hand side, and with the triangular
+    # solves of the 16 lanes on the tensor cores
+    for multi in (False, 2):
+        X2, st2, _ = g.Solver(w.A, w.block_ptr, precision="fp32_refine",
+                              multi_rhs=multi).solve(F)
+        for k in range(16):
+            assert abs(st2[k]["iters"] - st[k]["iters"]) <= 1, (multi, k)
+            assert_close(X2[k], X[k], 1e-8, (multi, k))
 
 
 # ------------------------------------------------------------------ relaxed inner tolerance
@@ -363,6 +406,13 @@ def test_fp64_fallback_mixed_context(sys_small):
     P = s.project(V)
     for k in range(11):
         assert_close(P[k], o.project(V[k]), 1e-10, k)
+    # FP32 blocks on the tensor-core kernel, the FP64 ones on the CUDA-core kernel
+    s2 = g.Solver(A, RAGGED, perm=perm, precision="fp32_refine", pivot_ratio_min=0.8,
+                  multi_rhs=2)
+    P2 = s2.project(V)
+    for k in range(11):
+        assert_close(P2[k], o.project(V[k]), 1e-10, ("tc", k))
+    s2.close()
     xo, ito, *_ = o.solve(f)
     x, st, code = s.solve(f)
     assert code == 0 and st[0]["fallbacks"] == len(FALLBACK_BLOCKS)
