@@ -193,40 +193,58 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" :::
 // Cholesky L L^T of the 64 x 64 SPD tile in S (lower part read; L written in place, upper part
 // zeroed) and inv(L) into Di, by the 128 epilogue threads (t = 0..127), blocked in 16 x 16
 // sub-blocks so that the 64 pivots need 12 CTA-wide barriers instead of one each:
-//   for each block column k: one warp factors the diagonal sub-block (warp-synchronous), the
-//   rows below solve against it (one thread per row), the trailing lower triangle is updated;
-// then the inverse: each warp inverts one diagonal sub-block (a lane per column), and the
+//   for each block column k: one warp factors the diagonal sub-block (rows in registers,
+//   columns of L passed by shuffles), the rows below solve against it (one thread per row),
+//   the trailing lower triangle is updated;
+// then the inverse: each warp inverts one diagonal sub-block (a lane per column, in
+// registers), and the
 // off-diagonal sub-blocks follow by distance d = i - k: Di_ik = -Di_ii sum_{k<=m<i} L_im Di_mk.
 // pmin receives the smallest pivot of the first `rows` rows; a pivot that is not positive
 // and finite sets *fail and is replaced by 1.  Tmp: 3 x 256 floats of scratch.
-__device__ void diag_factor_blocked(float *S, float *Di, float *Tmp, int t, int rows,
+__device__ __noinline__ void diag_factor_blocked(float *S, float *Di, float *Tmp, int t, int rows,
                                     double *pmin, int *fail) {
   const int warp = t >> 5, lane = t & 31;
+  float *rcp = Tmp;  // 1 / L_jj of the 64 pivots (Tmp is free until the off-diagonal inverse)
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int b0 = 16 * k;
     if (warp == 0) {
+      // the 16 x 16 diagonal sub-block in registers: lane r (and its mirror r + 16) holds
+      // row r; column jj of L reaches the other rows by shuffles instead of shared memory
+      const int r = lane & 15;
+      float a[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a[c] = S[(b0 + r) * LDS + b0 + c];
+      // smallest pivot and failure of this sub-block, in registers (one shared update after)
+      float pm = INFINITY;
+      bool bad = false;
+#pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         const int j = b0 + jj;
-        float d = S[j * LDS + j];
-        if (lane == 0 && j < rows) *pmin = fmin(*pmin, (double)d);
+        float d = __shfl_sync(0xffffffffu, a[jj], jj);
+        if (j < rows) pm = fminf(pm, d);
         if (!(d > 0.f) || !isfinite(d)) {
-          if (lane == 0) *fail = 1;
+          bad = true;
           d = 1.f;
         }
-        const float l = sqrtf(d), r = 1.f / l;
-        __syncwarp();
-        if (lane == 0) S[j * LDS + j] = l;
-        if (lane > jj && lane < 16) S[(b0 + lane) * LDS + j] *= r;
-        __syncwarp();
+        const float rc = rsqrtf(d), l = d * rc;
+        if (lane == jj) rcp[j] = rc;
+        // selects, not branches: the lanes stay converged through the step
+        a[jj] = r == jj ? l : (r > jj ? a[jj] * rc : a[jj]);
         // rank-1 update of the block's remaining lower triangle
-        const int w = 15 - jj;
-        for (int e = lane; e < w * w; e += 32) {
-          const int i = jj + 1 + e / w, c = jj + 1 + e % w;
-          if (c <= i)
-            S[(b0 + i) * LDS + b0 + c] =
-                fmaf(-S[(b0 + i) * LDS + j], S[(b0 + c) * LDS + j], S[(b0 + i) * LDS + b0 + c]);
-        }
-        __syncwarp();
+        float lc[16];
+#pragma unroll
+        for (int c = jj + 1; c < 16; ++c) lc[c] = __shfl_sync(0xffffffffu, a[jj], c);
+#pragma unroll
+        for (int c = jj + 1; c < 16; ++c) a[c] = r >= c ? fmaf(-a[jj], lc[c], a[c]) : a[c];
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S[(b0 + r) * LDS + b0 + c] = a[c];
+      }
+      if (lane == 0) {
+        if (pm < INFINITY) *pmin = fmin(*pmin, (double)pm);
+        if (bad) *fail = 1;
       }
     }
     epi_sync();
@@ -239,7 +257,7 @@ __device__ void diag_factor_blocked(float *S, float *Di, float *Tmp, int t, int 
         float v = S[i * LDS + b0 + c];
 #pragma unroll
         for (int m = 0; m < c; ++m) v = fmaf(-x[m], S[(b0 + c) * LDS + b0 + m], v);
-        x[c] = v / S[(b0 + c) * LDS + b0 + c];
+        x[c] = v * rcp[b0 + c];
       }
 #pragma unroll
       for (int c = 0; c < 16; ++c) S[i * LDS + b0 + c] = x[c];
@@ -262,21 +280,23 @@ __device__ void diag_factor_blocked(float *S, float *Di, float *Tmp, int t, int 
     const int i = e / T, j = e % T;
     if (j > i) S[i * LDS + j] = 0.f;
   }
-  // inverse of every diagonal sub-block: warp k, lane c < 16 owns column c
+  // inverse of every diagonal sub-block: warp k, lane c < 16 owns column c, kept in registers
+  // (entries above the diagonal are zero, so the sums may start at m = 0)
   {
     const int b0 = 16 * warp;
+    const int c = lane & 15;
+    float col[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float ri = rcp[b0 + i];
+      float v = 0.f;
+#pragma unroll
+      for (int m = 0; m < i; ++m) v = fmaf(-S[(b0 + i) * LDS + b0 + m], col[m], v);
+      col[i] = i < c ? 0.f : (i == c ? ri : v * ri);
+    }
     if (lane < 16) {
-      const int c = lane;
-      for (int i = 0; i < 16; ++i) {
-        float v = 0.f;
-        if (i > c) {
-          for (int m = c; m < i; ++m) v = fmaf(-S[(b0 + i) * LDS + b0 + m], Di[(b0 + m) * LDS + b0 + c], v);
-          v = v / S[(b0 + i) * LDS + b0 + i];
-        } else if (i == c) {
-          v = 1.f / S[(b0 + i) * LDS + b0 + i];
-        }
-        Di[(b0 + i) * LDS + b0 + c] = v;
-      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) Di[(b0 + i) * LDS + b0 + c] = col[i];
     }
   }
   // the upper triangle of Di
