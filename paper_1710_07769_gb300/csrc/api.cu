@@ -658,7 +658,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   h2d(blist.p, hlist.data(), nblk, s);
   void *fac = fp64 ? (void *)c->fac64.p : (void *)c->fac32.p;
   launch_gram_scatter(c->blk.p, blist.p, nblk, c->trow.p, c->brp.p, c->bci.p, c->bcv.p, fac,
-                      fp64, s);
+                      fp64 ? (int64_t)c->fac64.n : (int64_t)c->fac32.n, fp64, s);
   if (!fp64) {
     c->err_flag.alloc(1);
     CUDA_TRY(cudaMemsetAsync(c->err_flag.p, 0, sizeof(int32_t), s));
@@ -717,7 +717,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
       h2d(c->blk.p, c->hblk.data(), nblk, s);
       h2d(blist.p, fb.data(), fb.size(), s);
       launch_gram_scatter(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->brp.p, c->bci.p,
-                          c->bcv.p, c->fac64.p, 1, s);
+                          c->bcv.p, c->fac64.p, (int64_t)c->fac64.n, 1, s);
       launch_cholesky(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
                       c->dinv64.p, pmin.p, pfail.p, s);
       c->setup_launches += 2;

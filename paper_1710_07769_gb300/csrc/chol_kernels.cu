@@ -284,17 +284,18 @@ __device__ void transpose_block(const BlockDesc &B, const TileRow *__restrict__ 
     __syncthreads();
     for (int e = threadIdx.x; e < T * T; e += kThreads) dst[e] = sm[(e % T) * LDS + (e / T)];
   };
-  for (int I = 0; I < B.nt; ++I) {
-    tile_t(dinv + B.dinv_off + (int64_t)I * T * T, dinvT + B.dinv_off + (int64_t)I * T * T);
-    const TileRow U = trT[I];
-    for (int J = I + 1; J <= U.j0; ++J) {
-      W *dst = facT + U.off + (int64_t)(J - I - 1) * T * T;
-      const TileRow R = tr[J];
-      if (R.j0 <= I) {
-        tile_t(fac + R.off + (int64_t)(I - R.j0) * T * T, dst);
-      } else {
-        for (int e = threadIdx.x; e < T * T; e += kThreads) dst[e] = W(0);
-      }
+  // tile row I of the transposed copy: one CTA per (block, tile row)
+  const int I = blockIdx.y;
+  if (I >= B.nt) return;
+  tile_t(dinv + B.dinv_off + (int64_t)I * T * T, dinvT + B.dinv_off + (int64_t)I * T * T);
+  const TileRow U = trT[I];
+  for (int J = I + 1; J <= U.j0; ++J) {
+    W *dst = facT + U.off + (int64_t)(J - I - 1) * T * T;
+    const TileRow R = tr[J];
+    if (R.j0 <= I) {
+      tile_t(fac + R.off + (int64_t)(I - R.j0) * T * T, dst);
+    } else {
+      for (int e = threadIdx.x; e < T * T; e += kThreads) dst[e] = W(0);
     }
   }
 }
@@ -431,7 +432,9 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
 
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
                              const TileRow *trowT, const FactorPtrs &f, cudaStream_t s) {
-  if (nblk > 0) k_transpose_factor<<<(unsigned)nblk, kThreads, 0, s>>>(blk, trow, trowT, f);
+  if (nblk > 0)
+    k_transpose_factor<<<dim3((unsigned)nblk, kMaxBlockRows / T), kThreads, 0, s>>>(blk, trow,
+                                                                                    trowT, f);
   if (nblk > 0) k_pack_diag<<<(unsigned)nblk, kThreads, 0, s>>>(blk, f);
 }
 

@@ -191,7 +191,8 @@ void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
                     const int64_t *off, int32_t *ocol, double *oval, cudaStream_t s);
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, const int64_t *brp, const int32_t *bci,
-                         const double *bcv, void *fac, int prec64, cudaStream_t s);
+                         const double *bcv, void *fac, int64_t fac_elems, int prec64,
+                         cudaStream_t s);
 
 // factor arrays of both precisions (a context may hold FP64 fallback blocks beside
 // FP32 blocks): forward tiles (L_II, N_IJ), inv(L_II), and their transposed copies

@@ -849,13 +849,11 @@ __global__ void k_gram_scatter(const BlockDesc *__restrict__ blk, const int32_t 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
   const int mp = B.nt * kTile;
+  // the tiles were zeroed by one memset of the whole factor array before the launch
   for (int r = threadIdx.x; r < mp; r += blockDim.x) {
     const int I = r / kTile, rr = r % kTile;
     const TileRow T = trow[B.trow0 + I];
     W *rowbase = fac + T.off + (int64_t)rr * kTile;
-    const int ntiles = I - T.j0 + 1;
-    for (int t = 0; t < ntiles; ++t)
-      for (int c = 0; c < kTile; ++c) rowbase[(int64_t)t * kTile * kTile + c] = W(0);
     if (r >= B.m) {
       rowbase[(int64_t)(I - T.j0) * kTile * kTile + rr] = W(1);
       continue;
@@ -1005,8 +1003,11 @@ void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
 
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, const int64_t *brp, const int32_t *bci,
-                         const double *bcv, void *fac, int prec64, cudaStream_t s) {
+                         const double *bcv, void *fac, int64_t fac_elems, int prec64,
+                         cudaStream_t s) {
   if (nlist <= 0) return;
+  // every tile of the listed blocks starts at zero (fac holds exactly their tiles)
+  cudaMemsetAsync(fac, 0, (size_t)fac_elems * (prec64 ? sizeof(double) : sizeof(float)), s);
   if (prec64)
     k_gram_scatter<double><<<(unsigned)nlist, kThreads, 0, s>>>(
         blk, blist, trow, brp, bci, bcv, static_cast<double *>(fac));
