@@ -151,7 +151,8 @@ typedef struct cimmino_stats {
   double t_setup_ms;          /* scaling, permutation, A^T, C = A A^T, G_i extraction */
   double t_factor_ms;         /* Cholesky of all G_i (including FP64 fallbacks)     */
   double t_solve_ms;          /* this solve: xi plus all CG iterations              */
-  int64_t nnz_aat;            /* nnz(C)                                              */
+  int64_t nnz_aat;            /* nnz(C) with opts.keep_aat; 0 otherwise (the setup   */
+                              /* then forms only the Gram blocks, nnz_gram entries)  */
   int64_t factor_bytes;       /* bytes of the stored factor tiles (L_II and N_IJ)    */
   int64_t pass_bytes;         /* factor bytes one forward + backward solve streams    */
   int64_t kernel_launches;    /* kernels launched by the setup plus by this solve     */

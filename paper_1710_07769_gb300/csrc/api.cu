@@ -517,55 +517,72 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   rs.release();
 
   stage.next("cimmino.setup.aat");
-  // ---- C = A A^T (Section 2.3)
+  // ---- C = A A^T (Section 2.3).  The solve needs only its block-diagonal part, the Gram
+  // blocks G_i: unless the caller keeps C (opts.keep_aat), every row gathers only the
+  // candidates of its own block (a window of each sorted column of the transpose), and the
+  // SpGEMM writes G_i directly.  Its values are those entries of C, bit for bit.
   DBuf<int64_t> cntc;
   DBuf<int32_t> ovf;
+  DBuf<int32_t> rowblk, rowmin;
   cntc.alloc(N);
   ovf.alloc(N + 1);
-  spgemm_count(c->rp.p, c->ci.p, c->cp.p, c->ri.p, N, cntc.p, ovf.p + 1, ovf.p, s);
-  c->setup_launches += 1;
+  rowblk.alloc(N);
+  rowmin.alloc(N);
+  launch_row_block_ids(c->blk.p, nblk, rowblk.p, s);
+  const bool full_c = c->opts.keep_aat != 0;
+  const BlockDesc *wblk = full_c ? nullptr : c->blk.p;
+  const int32_t *wrow = full_c ? nullptr : rowblk.p;
+  spgemm_count(c->rp.p, c->ci.p, c->cp.p, c->ri.p, N, cntc.p, ovf.p + 1, ovf.p, s, wblk, wrow);
+  c->setup_launches += 2;
   int32_t novf = 0;
   d2h(&novf, ovf.p, 1, s);
   CUDA_TRY(cudaStreamSynchronize(s));
   if (novf > 0) {
     spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p, nullptr,
-                    nullptr, nullptr, flag.p + 2, s);
+                    nullptr, nullptr, flag.p + 2, s, wblk, wrow);
     d2h(hflag + 2, flag.p + 2, 1, s);
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hflag[2])
       fail(CIMMINO_EUNSUPPORTED, "a row of A A^T has more than 8192 structural candidates");
   }
-  c->crp.alloc(N + 1);
-  launch_scan_counts(cntc.p, c->crp.p, N, tmp.p, tl, s);
+  DBuf<int64_t> &orp = full_c ? c->crp : c->brp;
+  orp.alloc(N + 1);
+  launch_scan_counts(cntc.p, orp.p, N, tmp.p, tl, s);
   c->setup_launches += 3 + (novf > 0 ? 2 : 0);
-  d2h(&c->nnzc, c->crp.p + N, 1, s);
+  int64_t nout = 0;
+  d2h(&nout, orp.p + N, 1, s);
   CUDA_TRY(cudaStreamSynchronize(s));
-  c->cci.alloc(c->nnzc);
-  c->ccv.alloc(c->nnzc);
-  spgemm_fill(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, c->cv.p, N, c->crp.p, c->cci.p,
-              c->ccv.p, s);
+  DBuf<int32_t> &oci = full_c ? c->cci : c->bci;
+  DBuf<double> &ocv = full_c ? c->ccv : c->bcv;
+  oci.alloc(nout);
+  ocv.alloc(nout);
+  spgemm_fill(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, c->cv.p, N, orp.p, oci.p, ocv.p, s,
+              wblk, wrow);
   c->setup_launches += 1;
   if (novf > 0)
-    spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p,
-                    c->crp.p, c->cci.p, c->ccv.p, flag.p + 2, s);
-  c->have_aat = true;
+    spgemm_overflow(c->rp.p, c->ci.p, c->va.p, c->cp.p, c->ri.p, ovf.p + 1, novf, cntc.p, orp.p,
+                    oci.p, ocv.p, flag.p + 2, s, wblk, wrow);
 
-  // ---- block-diagonal part of C: the Gram blocks G_i (exact, FP64)
-  DBuf<int32_t> rowblk, rowmin;
-  rowblk.alloc(N);
-  rowmin.alloc(N);
-  launch_row_block_ids(c->blk.p, nblk, rowblk.p, s);
-  bd_count(c->crp.p, c->cci.p, c->blk.p, rowblk.p, N, cntc.p, s);
-  c->brp.alloc(N + 1);
-  launch_scan_counts(cntc.p, c->brp.p, N, tmp.p, tl, s);
-  c->setup_launches += 5;  // block ids, count, 3-pass scan
-  d2h(&c->nnz_bd, c->brp.p + N, 1, s);
-  CUDA_TRY(cudaStreamSynchronize(s));
-  c->bci.alloc(c->nnz_bd);
-  c->bcv.alloc(c->nnz_bd);
-  bd_fill(c->crp.p, c->cci.p, c->ccv.p, c->blk.p, rowblk.p, N, c->brp.p, c->bci.p, c->bcv.p,
-          rowmin.p, s);
-  c->setup_launches += 2;  // fill, tile envelope
+  // ---- block-diagonal part of C: the Gram blocks G_i (exact, FP64, local columns)
+  if (full_c) {
+    c->nnzc = nout;
+    c->have_aat = true;
+    bd_count(c->crp.p, c->cci.p, c->blk.p, rowblk.p, N, cntc.p, s);
+    c->brp.alloc(N + 1);
+    launch_scan_counts(cntc.p, c->brp.p, N, tmp.p, tl, s);
+    c->setup_launches += 4;  // count, 3-pass scan
+    d2h(&c->nnz_bd, c->brp.p + N, 1, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    c->bci.alloc(c->nnz_bd);
+    c->bcv.alloc(c->nnz_bd);
+    bd_fill(c->crp.p, c->cci.p, c->ccv.p, c->blk.p, rowblk.p, N, c->brp.p, c->bci.p, c->bcv.p,
+            rowmin.p, s);
+  } else {
+    c->nnzc = 0;
+    c->nnz_bd = nout;
+    bd_localize(c->brp.p, c->bci.p, c->blk.p, rowblk.p, N, rowmin.p, s);
+  }
+  c->setup_launches += 2;  // fill or local columns, tile envelope
   // sliced-ELL copy of the Gram blocks for the refinement residual
   {
     DBuf<int64_t> scnt;

@@ -161,16 +161,24 @@ void launch_scale_permute(const int64_t *rp0, const int32_t *ci0, const double *
 void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, int64_t N,
                       int64_t nnz, int64_t *cp, int32_t *ri, double *cv, int64_t *work,
                       int64_t *tmp, int64_t tmp_len, cudaStream_t s);
+// C = A A^T by rows.  With blk and rowblk (row -> block), row i keeps only the columns of its
+// own block (the Gram block G_i, global column indices); without them, every column.
 void spgemm_count(const int64_t *rp, const int32_t *ci, const int64_t *cp, const int32_t *ri,
-                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s);
+                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s,
+                  const BlockDesc *blk = nullptr, const int32_t *rowblk = nullptr);
 void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
                      const int32_t *ri, const int32_t *ovf, int32_t novf, int64_t *cnt,
                      const int64_t *crp, int32_t *cci, double *ccv, int32_t *flag,
-                     cudaStream_t s);
+                     cudaStream_t s, const BlockDesc *blk = nullptr,
+                     const int32_t *rowblk = nullptr);
 // cv: values of the transpose (CSC of A), aligned with ri
 void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
                  const int32_t *ri, const double *cv, int64_t N, const int64_t *crp,
-                 int32_t *cci, double *ccv, cudaStream_t s);
+                 int32_t *cci, double *ccv, cudaStream_t s, const BlockDesc *blk = nullptr,
+                 const int32_t *rowblk = nullptr);
+// block-restricted rows of C: global columns -> block-local ones, and each row's first one
+void bd_localize(const int64_t *brp, int32_t *bci, const BlockDesc *blk, const int32_t *rowblk,
+                 int64_t N, int32_t *rowmin, cudaStream_t s);
 void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s);
 void bd_count(const int64_t *crp, const int32_t *cci, const BlockDesc *blk, const int32_t *rowblk,
               int64_t N, int64_t *cnt, cudaStream_t s);

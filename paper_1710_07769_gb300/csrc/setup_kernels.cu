@@ -266,6 +266,38 @@ __global__ void k_col_sort(const int64_t *__restrict__ cp, int64_t N, int32_t *_
 // Values follow the definition c_ij = sum_k a_ik a_jk, evaluated by merging the two
 // sorted rows in increasing k -- the same order as Gustavson's accumulation.
 
+// Rows of column k of A (sorted ascending in the transpose) that fall in [lo, hi): the
+// candidates of a row whose output is restricted to its own block's rows.
+__device__ __forceinline__ void col_window(const int32_t *__restrict__ ri, int64_t &s0,
+                                           int64_t &e0, int32_t lo, int32_t hi) {
+  if (lo <= 0 && hi == INT32_MAX) return;
+  int64_t a = s0, b = e0;
+  while (a < b) {  // first row >= lo
+    const int64_t m = (a + b) >> 1;
+    if (ri[m] < lo) a = m + 1; else b = m;
+  }
+  int64_t c = a, d = e0;
+  while (c < d) {  // first row >= hi
+    const int64_t m = (c + d) >> 1;
+    if (ri[m] < hi) c = m + 1; else d = m;
+  }
+  s0 = a;
+  e0 = c;
+}
+
+// The output window of row i: its block's rows when blk is given, else every row.
+__device__ __forceinline__ void row_window(const BlockDesc *__restrict__ blk,
+                                           const int32_t *__restrict__ rowblk, int64_t i,
+                                           int32_t &lo, int32_t &hi) {
+  lo = 0;
+  hi = INT32_MAX;
+  if (blk) {
+    const BlockDesc B = blk[rowblk[i]];
+    lo = (int32_t)B.row0;
+    hi = (int32_t)(B.row0 + B.m);
+  }
+}
+
 template <int G>
 __device__ __forceinline__ void group_sync() {
   if (G == 32)
@@ -277,12 +309,14 @@ __device__ __forceinline__ void group_sync() {
 template <int G>
 __device__ int gather_candidates(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
-                                 int64_t i, int32_t *buf, int cap, int gt) {
+                                 int64_t i, int32_t *buf, int cap, int gt, int32_t wlo,
+                                 int32_t whi) {
   int U = 0;
   for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
     int32_t k = ci[q];
-    int64_t s0 = cp[k];
-    int len = (int)(cp[k + 1] - s0);
+    int64_t s0 = cp[k], e0 = cp[k + 1];
+    col_window(ri, s0, e0, wlo, whi);
+    int len = (int)(e0 - s0);
     for (int t = gt; t < len; t += G)
       if (U + t < cap) buf[U + t] = ri[s0 + t];
     U += len;
@@ -308,14 +342,15 @@ __device__ int gather_warp(const int64_t *__restrict__ rp, const int32_t *__rest
                            const double *__restrict__ va, const int64_t *__restrict__ cp,
                            const int32_t *__restrict__ ri, const double *__restrict__ cv,
                            int64_t i, WarpCols &wc, int32_t *rows, uint64_t *key, double *val,
-                           int cap, int lane) {
+                           int cap, int lane, int32_t wlo, int32_t whi) {
   const int64_t q0 = rp[i];
   const int nq = (int)(rp[i + 1] - q0);
   int len = 0;
   if (lane < nq) {
     const int32_t j = ci[q0 + lane];
-    const int64_t s0 = cp[j];
-    len = (int)(cp[j + 1] - s0);
+    int64_t s0 = cp[j], e0 = cp[j + 1];
+    col_window(ri, s0, e0, wlo, whi);
+    len = (int)(e0 - s0);
     wc.start[lane] = s0;
     if (val) wc.a[lane] = va[q0 + lane];
   }
@@ -353,14 +388,16 @@ constexpr int kHashCands = kHashSlots / 2;
 
 __device__ int count_unique_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
-                                 int64_t i, WarpCols &wc, int32_t *table, int lane) {
+                                 int64_t i, WarpCols &wc, int32_t *table, int lane,
+                                 int32_t wlo, int32_t whi) {
   const int64_t q0 = rp[i];
   const int nq = (int)(rp[i + 1] - q0);
   int len = 0;
   if (lane < nq) {
     const int32_t j = ci[q0 + lane];
-    const int64_t s0 = cp[j];
-    len = (int)(cp[j + 1] - s0);
+    int64_t s0 = cp[j], e0 = cp[j + 1];
+    col_window(ri, s0, e0, wlo, whi);
+    len = (int)(e0 - s0);
     wc.start[lane] = s0;
   }
   int incl = len;
@@ -487,15 +524,18 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
     k_spgemm_count_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                         const int64_t *__restrict__ cp, const int32_t *__restrict__ ri,
                         int64_t N, int64_t *__restrict__ cnt, int32_t *__restrict__ ovf_list,
-                        int32_t *__restrict__ ovf_n) {
+                        int32_t *__restrict__ ovf_n, const BlockDesc *__restrict__ blk,
+                        const int32_t *__restrict__ rowblk) {
   __shared__ int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
   __shared__ WarpCols scols[kSpgemmWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
+  int32_t wlo, whi;
+  row_window(blk, rowblk, i, wlo, whi);
   int32_t *buf = sbuf[warp];
   if (rp[i + 1] - rp[i] <= 32) {
-    const int u = count_unique_warp(rp, ci, cp, ri, i, scols[warp], buf, lane);
+    const int u = count_unique_warp(rp, ci, cp, ri, i, scols[warp], buf, lane, wlo, whi);
     if (u >= 0) {
       if (lane == 0) cnt[i] = u;
       return;
@@ -503,8 +543,9 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
   }
   const int U = rp[i + 1] - rp[i] <= 32
                     ? gather_warp(rp, ci, nullptr, cp, ri, nullptr, i, scols[warp], buf, nullptr,
-                                  nullptr, kSpgemmWarpCap, lane)
-                    : gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+                                  nullptr, kSpgemmWarpCap, lane, wlo, whi)
+                    : gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane, wlo,
+                                            whi);
   if (U > kSpgemmWarpCap) {
     if (lane == 0) {
       int slot = atomicAdd(ovf_n, 1);
@@ -561,12 +602,15 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
                        const double *__restrict__ va, const int64_t *__restrict__ cp,
                        const int32_t *__restrict__ ri, const double *__restrict__ cv, int64_t N,
                        const int64_t *__restrict__ crp, int32_t *__restrict__ cci,
-                       double *__restrict__ ccv) {
+                       double *__restrict__ ccv, const BlockDesc *__restrict__ blk,
+                       const int32_t *__restrict__ rowblk) {
   __shared__ __align__(16) int32_t sbuf[kSpgemmWarps][kSpgemmWarpCap];
   __shared__ WarpCols scols[kSpgemmWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * kSpgemmWarps + warp;
   if (i >= N) return;
+  int32_t wlo, whi;
+  row_window(blk, rowblk, i, wlo, whi);
   int32_t *buf = sbuf[warp];
   const int nq = (int)(rp[i + 1] - rp[i]);
   uint64_t *key = reinterpret_cast<uint64_t *>(buf);
@@ -581,7 +625,7 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
     int32_t *hk = buf + 3 * kHashFill;                                 // [kHashFill]
     double *hv = reinterpret_cast<double *>(buf + 4 * kHashFill);      // [kHashFill]
     const int Uh = gather_warp(rp, ci, va, cp, ri, cv, i, scols[warp], crow, nullptr, cval,
-                               kHashFill, lane);
+                               kHashFill, lane, wlo, whi);
     if (Uh <= kHashFill) {
       for (int t = lane; t < kHashFill; t += 32) hk[t] = -1;
       __syncwarp();
@@ -632,7 +676,7 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
     }
   }
   const int U = nq <= 32 ? gather_warp(rp, ci, va, cp, ri, cv, i, scols[warp], nullptr, key,
-                                       val, kFillFast, lane)
+                                       val, kFillFast, lane, wlo, whi)
                          : kFillFast + 1;
   if (U <= kFillFast) {
     bitonic_sort_kv(key, val, U, lane);
@@ -654,7 +698,7 @@ __global__ void __launch_bounds__(kSpgemmWarps * 32)
     }
     return;
   }
-  const int Ul = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane);
+  const int Ul = gather_candidates<32>(rp, ci, cp, ri, i, buf, kSpgemmWarpCap, lane, wlo, whi);
   if (Ul > kSpgemmWarpCap) return;  // CTA variant fills this row
   bitonic_sort<32>(buf, Ul, lane);
   int u = unique_compact<32>(buf, Ul, lane);
@@ -671,10 +715,14 @@ __global__ void k_spgemm_cta(const int64_t *__restrict__ rp, const int32_t *__re
                              const int32_t *__restrict__ ri, const int32_t *__restrict__ ovf_list,
                              int64_t *__restrict__ cnt, const int64_t *__restrict__ crp,
                              int32_t *__restrict__ cci, double *__restrict__ ccv,
-                             int32_t *flag) {
+                             int32_t *flag, const BlockDesc *__restrict__ blk,
+                             const int32_t *__restrict__ rowblk) {
   extern __shared__ int32_t dbuf[];
   const int64_t i = ovf_list[blockIdx.x];
-  int U = gather_candidates<kThreads>(rp, ci, cp, ri, i, dbuf, kSpgemmCtaCap, threadIdx.x);
+  int32_t wlo, whi;
+  row_window(blk, rowblk, i, wlo, whi);
+  int U = gather_candidates<kThreads>(rp, ci, cp, ri, i, dbuf, kSpgemmCtaCap, threadIdx.x, wlo,
+                                      whi);
   if (U > kSpgemmCtaCap) {
     if (threadIdx.x == 0) atomicOr(flag, 8);
     return;
@@ -739,6 +787,23 @@ __global__ void k_bd_fill(const int64_t *__restrict__ crp, const int32_t *__rest
       ++w;
       if (lj < mn) mn = lj;
     }
+  }
+  rowmin[i] = mn;
+}
+
+// Rows of C restricted to their own block (the Gram blocks, computed directly): global
+// columns become block-local ones and rowmin[i] gets the row's first local column.
+__global__ void k_bd_local(const int64_t *__restrict__ brp, int32_t *__restrict__ bci,
+                           const BlockDesc *__restrict__ blk, const int32_t *__restrict__ rowblk,
+                           int64_t N, int32_t *__restrict__ rowmin) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t lo = blk[rowblk[i]].row0;
+  int32_t mn = (int32_t)(i - lo);
+  for (int64_t q = brp[i]; q < brp[i + 1]; ++q) {
+    const int32_t lj = (int32_t)(bci[q] - lo);
+    bci[q] = lj;
+    if (lj < mn) mn = lj;
   }
   rowmin[i] = mn;
 }
@@ -930,27 +995,29 @@ void launch_transpose(const int64_t *rp, const int32_t *ci, const double *va, in
 }
 
 void spgemm_count(const int64_t *rp, const int32_t *ci, const int64_t *cp, const int32_t *ri,
-                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s) {
+                  int64_t N, int64_t *cnt, int32_t *ovf, int32_t *ovf_n, cudaStream_t s,
+                  const BlockDesc *blk, const int32_t *rowblk) {
   cudaMemsetAsync(ovf_n, 0, sizeof(int32_t), s);
-  k_spgemm_count_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(rp, ci, cp, ri, N,
-                                                                             cnt, ovf, ovf_n);
+  k_spgemm_count_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(
+      rp, ci, cp, ri, N, cnt, ovf, ovf_n, blk, rowblk);
 }
 
 void spgemm_overflow(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
                      const int32_t *ri, const int32_t *ovf, int32_t novf, int64_t *cnt,
                      const int64_t *crp, int32_t *cci, double *ccv, int32_t *flag,
-                     cudaStream_t s) {
+                     cudaStream_t s, const BlockDesc *blk, const int32_t *rowblk) {
   if (novf <= 0) return;
   size_t smem = sizeof(int32_t) * kSpgemmCtaCap;
   k_spgemm_cta<<<(unsigned)novf, kThreads, smem, s>>>(rp, ci, va, cp, ri, ovf, cnt, crp, cci,
-                                                      ccv, flag);
+                                                      ccv, flag, blk, rowblk);
 }
 
 void spgemm_fill(const int64_t *rp, const int32_t *ci, const double *va, const int64_t *cp,
                  const int32_t *ri, const double *cv, int64_t N, const int64_t *crp,
-                 int32_t *cci, double *ccv, cudaStream_t s) {
+                 int32_t *cci, double *ccv, cudaStream_t s, const BlockDesc *blk,
+                 const int32_t *rowblk) {
   k_spgemm_fill_warp<<<grid_for(N, kSpgemmWarps), kSpgemmWarps * 32, 0, s>>>(
-      rp, ci, va, cp, ri, cv, N, crp, cci, ccv);
+      rp, ci, va, cp, ri, cv, N, crp, cci, ccv, blk, rowblk);
 }
 
 void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, cudaStream_t s) {
@@ -960,6 +1027,11 @@ void launch_row_block_ids(const BlockDesc *blk, int32_t nblk, int32_t *rowblk, c
 void bd_count(const int64_t *crp, const int32_t *cci, const BlockDesc *blk, const int32_t *rowblk,
               int64_t N, int64_t *cnt, cudaStream_t s) {
   k_bd_count<<<grid_for(N, kThreads), kThreads, 0, s>>>(crp, cci, blk, rowblk, N, cnt);
+}
+
+void bd_localize(const int64_t *brp, int32_t *bci, const BlockDesc *blk, const int32_t *rowblk,
+                 int64_t N, int32_t *rowmin, cudaStream_t s) {
+  k_bd_local<<<grid_for(N, kThreads), kThreads, 0, s>>>(brp, bci, blk, rowblk, N, rowmin);
 }
 
 void bd_fill(const int64_t *crp, const int32_t *cci, const double *ccv, const BlockDesc *blk,

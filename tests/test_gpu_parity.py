@@ -90,6 +90,43 @@ def test_setup_scaled_and_aat_match_oracle(sys_small):
     np.testing.assert_allclose(cv, ocv, rtol=1e-12, atol=1e-15)
 
 
+def _dense_column_system():
+    """2000 rows, a column with 1500 entries: rows with more than 1024 candidates."""
+    n = 2000
+    D = np.zeros((n, n))
+    D[np.arange(n), np.arange(n)] = 3.0
+    D[:1500, 7] += np.linspace(0.5, 1.5, 1500)
+    D[np.arange(1, n), np.arange(n - 1)] -= 0.4
+    return csr_from_dense(D), np.array([0, 700, 1400, 2000], np.int64)
+
+
+@pytest.mark.parametrize("case", ["ragged", "dense_column"])
+def test_gram_blocks_direct_equal_cut_from_full_c(sys_small, case):
+    """Without opts.keep_aat the setup forms the Gram blocks G_i directly: each row of
+    C = A A^T gathers only the candidates of its own block (Section 2.3 restricted to the
+    block diagonal).  The blocks, hence the factors and H v, are bit for bit those cut from
+    the full C; the dense column sends rows through the CTA path of the SpGEMM."""
+    if case == "ragged":
+        A, perm, f = sys_small
+        bp = RAGGED
+    else:
+        A, bp = _dense_column_system()
+        perm = None
+    s_full = g.Solver(A, bp, perm=perm, keep_aat=True, precision="fp64")
+    s_direct = g.Solver(A, bp, perm=perm, precision="fp64")
+    for b in range(len(bp) - 1):
+        assert np.array_equal(s_full.factor(b)[0], s_direct.factor(b)[0]), b
+    v = np.random.default_rng(41).standard_normal(A.n)
+    assert np.array_equal(s_full.project(v), s_direct.project(v))
+    x1, st1, c1 = s_full.solve(inputs.matvec(A, v))
+    x2, st2, c2 = s_direct.solve(inputs.matvec(A, v))
+    assert c1 == c2 == 0 and st2[0]["nnz_aat"] == 0 and st1[0]["nnz_aat"] > st2[0]["nnz_gram"]
+    assert st1[0]["nnz_gram"] == st2[0]["nnz_gram"]
+    assert np.array_equal(x1, x2)
+    s_full.close()
+    s_direct.close()
+
+
 # ------------------------------------------------------------------ Cholesky of G_i
 
 @pytest.mark.parametrize("layout", ["dense", "skyline"])
