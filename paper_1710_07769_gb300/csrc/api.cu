@@ -337,7 +337,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
         fail(CIMMINO_EUNSUPPORTED, "a block has more than 4096 rows");
     }
     const int32_t *pm = perms ? perms[q] : nullptr;
-    if (pm) {
+    if (pm && nsys > 1) {  // one system: checked on the device below
       std::vector<char> seen(M.n, 0);
       for (int64_t r = 0; r < M.n; ++r) {
         if (pm[r] < 0 || pm[r] >= M.n || seen[pm[r]])
@@ -427,8 +427,27 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4 * sizeof(int32_t), s));
   launch_validate_csr(drp0, dci0, N, NNZ, flag.p, s);
   c->setup_launches += 1;
+  // the row permutation (concatenated systems: each system's rows map into its own range);
+  // a single system's is copied as given and checked on the device (flag[3])
+  c->perm.alloc(N);
+  if (nsys == 1 && perms && perms[0]) {
+    h2d(c->perm.p, perms[0], N, s);
+    DBuf<int32_t> seen;
+    seen.alloc(N);
+    CUDA_TRY(cudaMemsetAsync(seen.p, 0, sizeof(int32_t) * N, s));
+    launch_check_perm(c->perm.p, N, seen.p, flag.p + 3, s);
+    c->setup_launches += 1;
+  } else {
+    std::vector<int32_t> hperm(N);
+    for (int32_t q = 0; q < nsys; ++q) {
+      const int64_t r0 = c->hsys[q].row0;
+      const int32_t *pm = perms ? perms[q] : nullptr;
+      for (int64_t r = 0; r < c->hsys[q].n; ++r) hperm[r0 + r] = (int32_t)(r0 + (pm ? pm[r] : r));
+    }
+    h2d(c->perm.p, hperm.data(), N, s);
+  }
   int32_t hflag[4] = {0, 0, 0, 0};
-  d2h(hflag, flag.p, 1, s);
+  d2h(hflag, flag.p, 4, s);
   CUDA_TRY(cudaStreamSynchronize(s));
   if (hflag[0]) {
     std::string why = (hflag[0] & 1) ? "row_ptr not monotone or inconsistent with nnz"
@@ -436,6 +455,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                                        : "column indices not strictly increasing within a row";
     fail(CIMMINO_EINVAL, "malformed CSR: " + why);
   }
+  if (hflag[3]) fail(CIMMINO_EINVAL, "perm is not a permutation of 0..n-1");
   stage.next("cimmino.setup.scale");
   // ---- row and column equilibration (Section 3.1), in place on our own copy of A's values
   DBuf<double> rs;
@@ -453,15 +473,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     c->setup_launches += 1 + 3 * c->opts.ruiz_sweeps;
     CUDA_TRY(cudaStreamSynchronize(s));
   }
-  // ---- permutation and blocks
-  std::vector<int32_t> hperm(N);
-  for (int32_t q = 0; q < nsys; ++q) {
-    const int64_t r0 = c->hsys[q].row0;
-    const int32_t *pm = perms ? perms[q] : nullptr;
-    for (int64_t r = 0; r < c->hsys[q].n; ++r) hperm[r0 + r] = (int32_t)(r0 + (pm ? pm[r] : r));
-  }
-  c->perm.alloc(N);
-  h2d(c->perm.p, hperm.data(), N, s);
+  // ---- blocks
   int32_t ntrow = 0, nslice = 0;
   c->max_mp = 0;
   for (int32_t q = 0; q < nsys; ++q) {

@@ -143,6 +143,8 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 // launchers (defined in the .cu files)
 
 // setup_kernels.cu
+void launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int32_t *flag,
+                       cudaStream_t s);
 void launch_validate_csr(const int64_t *rp, const int32_t *ci, int64_t n, int64_t nnz,
                          int32_t *flag, cudaStream_t s);
 int64_t scan_tmp_len(int64_t n);

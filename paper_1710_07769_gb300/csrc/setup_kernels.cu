@@ -935,10 +935,24 @@ __global__ void k_gram_scatter(const BlockDesc *__restrict__ blk, const int32_t 
 
 }  // namespace
 
+// perm is a permutation of 0..n-1: every value in range and taken once (seen: n zeros)
+__global__ void k_check_perm(const int32_t *__restrict__ perm, int64_t n, int32_t *seen,
+                             int32_t *flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = perm[i];
+  if (v < 0 || v >= n || atomicAdd(&seen[v], 1) != 0) atomicOr(flag, 1);
+}
+
 // ================================================================ launchers
 void launch_validate_csr(const int64_t *rp, const int32_t *ci, int64_t n, int64_t nnz,
                          int32_t *flag, cudaStream_t s) {
   k_validate_csr<<<grid_for(n + 1, kThreads), kThreads, 0, s>>>(rp, ci, n, nnz, flag);
+}
+
+void launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int32_t *flag,
+                       cudaStream_t s) {
+  k_check_perm<<<grid_for(n, kThreads), kThreads, 0, s>>>(perm, n, seen, flag);
 }
 
 int64_t scan_tmp_len(int64_t n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
