@@ -49,10 +49,23 @@ __device__ __forceinline__ bool arrive_last(int32_t *counter, int ncta) {
 // thread of the CTA must call it and gets the result.
 __device__ __forceinline__ double reduce_partials(const double *part, const SysDesc &S, int nrhs,
                                                   int k, double *red) {
-  double v = 0.0;
-  for (int c = threadIdx.x; c < S.ncta; c += blockDim.x)
-    v += __ldcg(part + (int64_t)(S.cta0 + c) * nrhs + k);
-  return block_sum(v, red);
+  // four independent accumulators keep four L2 loads in flight per thread; they are
+  // combined in a fixed tree, so the result depends only on ncta and the CTA size
+  const double *p = part + (int64_t)S.cta0 * nrhs + k;
+  const int step = blockDim.x;
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+  int c = threadIdx.x;
+#pragma unroll 1
+  for (; c + 3 * step < S.ncta; c += 4 * step) {
+    v0 += __ldcg(p + (int64_t)c * nrhs);
+    v1 += __ldcg(p + (int64_t)(c + step) * nrhs);
+    v2 += __ldcg(p + (int64_t)(c + 2 * step) * nrhs);
+    v3 += __ldcg(p + (int64_t)(c + 3 * step) * nrhs);
+  }
+#pragma unroll 1
+  for (; c < S.ncta; c += step) v0 += __ldcg(p + (int64_t)c * nrhs);
+  const double t = (v0 + v1) + (v2 + v3);
+  return block_sum(t, red);
 }
 
 __device__ __forceinline__ bool lane_running(const IterArgs &a, int sys, int k) {
