@@ -708,7 +708,13 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                        tc_scratch.p, off, tc_rowblk.p, pmin.p, pfail.p, c->err_flag.p, s);
   }
   c->t_chol_ms = tchol.stop_ms(s);
-  c->setup_launches += 2;  // scatter, Cholesky
+  // N_KJ = inv(L_KK) L_KJ: a kernel of its own, outside the Cholesky's time
+  if (fp64)
+    launch_ntransform64(c->blk.p, blist.p, nblk, c->trow.p, c->fac64.p, c->dinv64.p, s);
+  else
+    launch_ntransform_tc(c->blk.p, nblk, ntrow, c->trow.p, c->fac32.p, c->dinv32.p, tc_rowblk.p,
+                         s);
+  c->setup_launches += fp64 ? 3 : 4;  // scatter, Cholesky, (block ids,) N transform
   CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> hfail(nblk);
   std::vector<double> hpmin(nblk);
@@ -749,7 +755,9 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                           c->bcv.p, c->fac64.p, (int64_t)c->fac64.n, 1, s);
       launch_cholesky(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
                       c->dinv64.p, pmin.p, pfail.p, s);
-      c->setup_launches += 2;
+      launch_ntransform64(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
+                          c->dinv64.p, s);
+      c->setup_launches += 3;
       d2h(hfail.data(), pfail.p, nblk, s);
       CUDA_TRY(cudaStreamSynchronize(s));
       for (int32_t b : fb)

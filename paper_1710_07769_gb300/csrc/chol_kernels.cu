@@ -425,6 +425,11 @@ void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
   cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemLaunch);
   k_cholesky<<<(unsigned)nlist, kThreads, kCholSmemLaunch, s>>>(blk, blist, trow, fac, dinv,
                                                                pivmin, pivfail);
+}
+
+void launch_ntransform64(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                         const TileRow *trow, double *fac, const double *dinv, cudaStream_t s) {
+  if (nlist <= 0) return;
   cudaFuncSetAttribute(k_ntransform64, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
   k_ntransform64<<<dim3((unsigned)nlist, kMaxBlockRows / T), kThreads, kCholSmem, s>>>(
       blk, blist, trow, fac, dinv);

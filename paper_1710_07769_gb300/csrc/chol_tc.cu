@@ -723,6 +723,11 @@ void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlis
   cudaFuncSetAttribute(k_cholesky_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   k_cholesky_tc<<<(unsigned)nlist, kThreads, kTcSmem, s>>>(blk, blist, trow, fac, dinv, scratch,
                                                            zero_img, pivmin, pivfail, err);
+}
+
+void launch_ntransform_tc(const BlockDesc *blk, int32_t nblk, int32_t ntrow, const TileRow *trow,
+                          float *fac, const float *dinv, int32_t *rowblk_t, cudaStream_t s) {
+  if (nblk <= 0) return;
   k_tile_row_blocks<<<(unsigned)nblk, 64, 0, s>>>(blk, nblk, rowblk_t);
   k_ntransform<<<(unsigned)ntrow, 256, 0, s>>>(blk, rowblk_t, trow, fac, dinv);
 }

@@ -229,6 +229,9 @@ void launch_cholesky_tc(const BlockDesc *blk, const int32_t *blist, int32_t nlis
                         int32_t ntrow, const TileRow *trow, float *fac, float *dinv,
                         float *scratch, int64_t factor_elems, int32_t *rowblk_t, double *pivmin,
                         int32_t *pivfail, int32_t *err, cudaStream_t s);
+// the same for the FP32 blocks (all tile rows of the context; rowblk_t: ntrow scratch)
+void launch_ntransform_tc(const BlockDesc *blk, int32_t nblk, int32_t ntrow, const TileRow *trow,
+                          float *fac, const float *dinv, int32_t *rowblk_t, cudaStream_t s);
 
 // chol_kernels.cu
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
@@ -237,6 +240,9 @@ void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *
 void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                      const TileRow *trow, double *fac, double *dinv, double *pivmin,
                      int32_t *pivfail, cudaStream_t s);
+// N_KJ = inv(L_KK) L_KJ for the off-diagonal tiles of the listed FP64 blocks (after the Cholesky)
+void launch_ntransform64(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
+                         const TileRow *trow, double *fac, const double *dinv, cudaStream_t s);
 
 // solve_kernels.cu
 struct IterArgs {
