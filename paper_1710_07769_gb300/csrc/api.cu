@@ -211,6 +211,7 @@ struct cimmino_ctx {
   DBuf<int64_t> soff, aoff, toff;
   DBuf<int16_t> scol;
   DBuf<int32_t> acol, tcol;
+  DBuf<int32_t> tord;  // A^T's rows in sliced-ELL position order (sorted inside CTA chunks)
   DBuf<double> aval, tval;
   DBuf<BlockDesc> blk;
   DBuf<int32_t> border;  // projection launch order (longest first)
@@ -870,26 +871,32 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     h2d(srow0.p, hsrow0.data(), ns, s);
     h2d(srows.p, hsrows.data(), ns, s);
     auto build = [&](const int64_t *ptr, const int32_t *idx, const double *val,
-                     DBuf<int64_t> &off, DBuf<int32_t> &col, DBuf<double> &vv) {
+                     const int32_t *rmap, DBuf<int64_t> &off, DBuf<int32_t> &col,
+                     DBuf<double> &vv) {
       off.alloc(ns + 1);
-      sell_rows_width(ptr, srow0.p, srows.p, ns, scnt.p, s);
+      sell_rows_width(ptr, srow0.p, srows.p, ns, rmap, scnt.p, s);
       launch_scan_counts(scnt.p, off.p, ns, tmp.p, tl, s);
       int64_t tot = 0;
       d2h(&tot, off.p + ns, 1, s);
       CUDA_TRY(cudaStreamSynchronize(s));
       col.alloc(tot);
       vv.alloc(tot);
-      sell_rows_fill(ptr, idx, val, srow0.p, srows.p, ns, off.p, col.p, vv.p, s);
+      sell_rows_fill(ptr, idx, val, srow0.p, srows.p, ns, rmap, off.p, col.p, vv.p, s);
       c->setup_launches += 5;  // widths, 3-pass scan, fill
     };
-    build(c->rp.p, c->ci.p, c->va.p, c->aoff, c->acol, c->aval);
-    build(c->cp.p, c->ri.p, c->cv.p, c->toff, c->tcol, c->tval);
+    c->cta.alloc(c->hcta.size());
+    h2d(c->cta.p, c->hcta.data(), c->hcta.size(), s);
+    build(c->rp.p, c->ci.p, c->va.p, nullptr, c->aoff, c->acol, c->aval);
+    // A^T's rows (the columns of A) vary in length: inside every CTA's chunk they are
+    // ordered by decreasing length, so its 32-row slices pad little
+    c->tord.alloc(N);
+    chunk_order(c->cp.p, c->cta.p, (int32_t)c->hcta.size(), c->tord.p, s);
+    c->setup_launches += 1;
+    build(c->cp.p, c->ri.p, c->cv.p, c->tord.p, c->toff, c->tcol, c->tval);
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   c->sys.alloc(nsys);
   h2d(c->sys.p, c->hsys.data(), nsys, s);
-  c->cta.alloc(c->hcta.size());
-  h2d(c->cta.p, c->hcta.data(), c->hcta.size(), s);
   c->rowabs.alloc(N);
   launch_row_abs(c->rp.p, c->ci.p, c->va.p, c->d.p, c->cs.p, N, c->rowabs.p, s);
   c->setup_launches += 1;
@@ -1058,6 +1065,7 @@ void ensure_solve_buffers(cimmino_ctx *c, int32_t nrhs) {
   a.acol = c->acol.p;
   a.aval = c->aval.p;
   a.toff = c->toff.p;
+  a.tord = c->tord.p;
   a.tcol = c->tcol.p;
   a.tval = c->tval.p;
   a.soff = c->soff.p;

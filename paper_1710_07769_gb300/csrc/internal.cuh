@@ -194,11 +194,16 @@ void sell_width(const BlockDesc *blk, int32_t nblk, const int64_t *brp, int64_t 
 void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int32_t *bci,
                const double *bcv, const int64_t *soff, int16_t *scol, double *sval,
                cudaStream_t s);
+// rows of every CTA-table chunk by decreasing length (ord[position] = row)
+void chunk_order(const int64_t *ptr, const CtaDesc *cta, int32_t ncta, int32_t *ord,
+                 cudaStream_t s);
+// sliced-ELL copy of a CSR matrix; rmap (optional) gives the row at each position
 void sell_rows_width(const int64_t *ptr, const int64_t *srow0, const int32_t *srows,
-                     int32_t nslice, int64_t *cnt, cudaStream_t s);
+                     int32_t nslice, const int32_t *rmap, int64_t *cnt, cudaStream_t s);
 void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
                     const int64_t *srow0, const int32_t *srows, int32_t nslice,
-                    const int64_t *off, int32_t *ocol, double *oval, cudaStream_t s);
+                    const int32_t *rmap, const int64_t *off, int32_t *ocol, double *oval,
+                    cudaStream_t s);
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, const int64_t *brp, const int32_t *bci,
                          const double *bcv, void *fac, int64_t fac_elems, int prec64,
@@ -261,6 +266,7 @@ struct IterArgs {
   const int32_t *acol;   //   columns
   const double *aval;    //   values
   const int64_t *toff;   // sliced-ELL copy of A^T (32-column slices)
+  const int32_t *tord;   //   the column of A^T at each position (sorted inside CTA chunks)
   const int32_t *tcol;   //   rows
   const double *tval;    //   values
   const int64_t *soff;   // sliced-ELL Gram blocks: slice offsets (entries)

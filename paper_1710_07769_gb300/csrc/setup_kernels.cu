@@ -873,19 +873,43 @@ __global__ void k_sell_fill(const BlockDesc *__restrict__ blk, int32_t nblk,
 // srow0[k] .. srow0[k] + srows[k] - 1 (at most 32, never straddling systems); entry k
 // of lane l sits at off + 32 k + l.  Padding entries point at the slice's first row
 // with value 0, so they read a valid element and add nothing.
+// Rows of one CTA-table chunk in order of decreasing length (ties: increasing row), so that
+// the 32-row slices of a sliced-ELL copy hold rows of similar length and pad little:
+// ord[row0 + rank] = row.  One CTA (kVecRows threads) per chunk.
+__global__ void __launch_bounds__(kVecRows)
+    k_chunk_order(const int64_t *__restrict__ ptr, const CtaDesc *__restrict__ cta,
+                  int32_t *__restrict__ ord) {
+  __shared__ int64_t len[kVecRows];
+  const CtaDesc C = cta[blockIdx.x];
+  const int t = threadIdx.x;
+  const int64_t r = C.row0 + t;
+  len[t] = t < C.rows ? ptr[r + 1] - ptr[r] : -1;
+  __syncthreads();
+  if (t >= C.rows) return;
+  const int64_t mine = len[t];
+  int rank = 0;
+  for (int u = 0; u < C.rows; ++u) rank += len[u] > mine || (len[u] == mine && u < t);
+  ord[C.row0 + rank] = (int32_t)r;
+}
+
+// rmap (optional): the row in position srow0 + l of the copy
 __global__ void k_sell_rows_width(const int64_t *__restrict__ ptr, const int64_t *__restrict__ srow0,
                                   const int32_t *__restrict__ srows, int32_t nslice,
-                                  int64_t *__restrict__ cnt) {
+                                  const int32_t *__restrict__ rmap, int64_t *__restrict__ cnt) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nslice) return;
   int64_t w = 0;
-  for (int l = 0; l < srows[k]; ++l) w = max(w, ptr[srow0[k] + l + 1] - ptr[srow0[k] + l]);
+  for (int l = 0; l < srows[k]; ++l) {
+    const int64_t r = rmap ? rmap[srow0[k] + l] : srow0[k] + l;
+    w = max(w, ptr[r + 1] - ptr[r]);
+  }
   cnt[k] = 32 * w;
 }
 
 __global__ void k_sell_rows_fill(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                                  const double *__restrict__ val, const int64_t *__restrict__ srow0,
                                  const int32_t *__restrict__ srows, int32_t nslice,
+                                 const int32_t *__restrict__ rmap,
                                  const int64_t *__restrict__ off, int32_t *__restrict__ ocol,
                                  double *__restrict__ oval) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -893,8 +917,8 @@ __global__ void k_sell_rows_fill(const int64_t *__restrict__ ptr, const int32_t 
   if (k >= nslice) return;
   const int64_t o = off[k];
   const int w = (int)((off[k + 1] - o) >> 5);
-  const int64_t r = srow0[k] + l;
   const bool real = l < srows[k];
+  const int64_t r = real && rmap ? rmap[srow0[k] + l] : srow0[k] + l;
   const int64_t p0 = real ? ptr[r] : 0;
   const int len = real ? (int)(ptr[r + 1] - p0) : 0;
   for (int e = 0; e < w; ++e) {
@@ -1072,19 +1096,25 @@ void sell_fill(const BlockDesc *blk, int32_t nblk, const int64_t *brp, const int
     k_sell_fill<<<(unsigned)nblk, kThreads, 0, s>>>(blk, nblk, brp, bci, bcv, soff, scol, sval);
 }
 
+void chunk_order(const int64_t *ptr, const CtaDesc *cta, int32_t ncta, int32_t *ord,
+                 cudaStream_t s) {
+  if (ncta > 0) k_chunk_order<<<(unsigned)ncta, kVecRows, 0, s>>>(ptr, cta, ord);
+}
+
 void sell_rows_width(const int64_t *ptr, const int64_t *srow0, const int32_t *srows,
-                     int32_t nslice, int64_t *cnt, cudaStream_t s) {
+                     int32_t nslice, const int32_t *rmap, int64_t *cnt, cudaStream_t s) {
   if (nslice > 0)
     k_sell_rows_width<<<grid_for(nslice, kThreads), kThreads, 0, s>>>(ptr, srow0, srows, nslice,
-                                                                      cnt);
+                                                                      rmap, cnt);
 }
 
 void sell_rows_fill(const int64_t *ptr, const int32_t *idx, const double *val,
                     const int64_t *srow0, const int32_t *srows, int32_t nslice,
-                    const int64_t *off, int32_t *ocol, double *oval, cudaStream_t s) {
+                    const int32_t *rmap, const int64_t *off, int32_t *ocol, double *oval,
+                    cudaStream_t s) {
   if (nslice > 0)
     k_sell_rows_fill<<<grid_for((int64_t)nslice * 32, kThreads), kThreads, 0, s>>>(
-        ptr, idx, val, srow0, srows, nslice, off, ocol, oval);
+        ptr, idx, val, srow0, srows, nslice, rmap, off, ocol, oval);
 }
 
 void launch_gram_scatter(const BlockDesc *blk, const int32_t *blist, int32_t nlist,

@@ -188,8 +188,9 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double red[32];
   const CtaDesc C = a.cta[blockIdx.x];
   const SysDesc S = a.sys[C.sys];
-  const int64_t j = C.row0 + threadIdx.x;  // column index (square systems)
   const bool act = threadIdx.x < C.rows;
+  // column of A (row of the transpose) at this thread's sliced-ELL position
+  const int64_t j = act ? (int64_t)a.tord[C.row0 + threadIdx.x] : C.row0 + threadIdx.x;
   for (int k = 0; k < a.nrhs; ++k) {
     if (MODE == 1 && !lane_running(a, C.sys, k)) continue;
     double pq = 0.0;
@@ -407,8 +408,9 @@ __global__ void __launch_bounds__(kThreads) k_spmv_t_mr(IterArgs a) {
   __shared__ double red[KC * kWarps];
   const CtaDesc C = a.cta[blockIdx.x];
   const SysDesc S = a.sys[C.sys];
-  const int64_t j = C.row0 + threadIdx.x;
   const bool act = threadIdx.x < C.rows;
+  // column of A (row of the transpose) at this thread's sliced-ELL position
+  const int64_t j = act ? (int64_t)a.tord[C.row0 + threadIdx.x] : C.row0 + threadIdx.x;
   const int sl = C.slice0 + (threadIdx.x >> 5), l = threadIdx.x & 31;
   const int64_t o = a.toff[sl];
   const int wd = (int)((a.toff[sl + 1] - o) >> 5);
