@@ -1,7 +1,7 @@
 // Batched Cholesky G_i = L_i L_i^T of the Gram blocks in FP64, in place on the tiled
 // factor layout (tile rows J0(I)..I, T x T row-major tiles).  One CTA per block,
 // right-looking over tile columns K:
-//   1. factor the diagonal tile (unblocked, in shared memory), record the pivots;
+//   1. factor the diagonal tile (in shared memory, 16 x 16 sub-blocks), record the pivots;
 //   2. invert L_KK (kept in dinv for the triangular solves);
 //   3. L_IK = G_IK * inv(L_KK)^T for the stored tiles below the diagonal;
 //   4. G_IJ -= L_IK * L_JK^T for K < J <= I (only tiles inside the envelope exist,
@@ -107,6 +107,136 @@ __device__ __forceinline__ void unit_store(double *out, int R, int C, const doub
   }
 }
 
+// Cholesky L L^T of the 64 x 64 SPD tile in S (lower part read, L written over it) and inv(L)
+// into the lower part of Di, by the CTA's threads, in 16 x 16 sub-blocks so that the 64 pivots
+// take 12 barriers instead of two each:
+//   block column k: warp 0 factors the diagonal sub-block (lane r holds row r in registers; the
+//   columns of L reach the other rows by shuffles), the rows below solve against it (a thread
+//   per row), and the trailing lower triangle, folded into a rectangle (rows p and n-1-p share
+//   a line of n+1 entries), takes the rank-16 update;
+//   inverse: warp k inverts diagonal sub-block k (a lane per column, in registers), and the
+//   off-diagonal sub-blocks follow by distance d = i - k: Di_ik = -Di_ii sum_{k<=m<i} L_im Di_mk.
+// Each FP64 operation on the pivot chain waits tens of cycles on GB300's narrow FP64 pipe, so a
+// pivot costs one reciprocal square root (L_jj = d rsqrt(d), 1 / L_jj = rsqrt(d)), its chain
+// stays in registers, and the lanes stay converged (selects instead of branches).  Entries
+// above the diagonal of S are never read; Di's are zero inside the diagonal sub-blocks and
+// unset elsewhere.  *pmin receives the smallest pivot of the first `rows` rows; a pivot that is
+// not positive and finite sets *fail and is replaced by 1.  Tmp: 3 x 256 doubles.
+__device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, int rows,
+                                           double *pmin, int *fail) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  double *rcp = Tmp;  // 1 / L_jj (Tmp is free until the off-diagonal inverse)
+  for (int k = 0; k < 4; ++k) {
+    const int b0 = 16 * k;
+    if (warp == 0) {
+      const int r = lane & 15;
+      double a[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a[c] = S[(b0 + r) * LDS + b0 + c];
+      double pm = INFINITY;
+      bool bad = false;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = b0 + jj;
+        double d = __shfl_sync(0xffffffffu, a[jj], jj);
+        if (j < rows) pm = fmin(pm, d);
+        if (!(d > 0.0) || !isfinite(d)) {
+          bad = true;
+          d = 1.0;
+        }
+        const double rc = rsqrt(d), l = d * rc;
+        if (lane == jj) rcp[j] = rc;
+        a[jj] = r == jj ? l : (r > jj ? a[jj] * rc : a[jj]);
+        double lc[16];
+#pragma unroll
+        for (int c = jj + 1; c < 16; ++c) lc[c] = __shfl_sync(0xffffffffu, a[jj], c);
+#pragma unroll
+        for (int c = jj + 1; c < 16; ++c) a[c] = r >= c ? fma(-a[jj], lc[c], a[c]) : a[c];
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S[(b0 + r) * LDS + b0 + c] = a[c];
+      }
+      if (lane == 0) {
+        if (pm < INFINITY) *pmin = fmin(*pmin, pm);
+        if (bad) *fail = 1;
+      }
+    }
+    __syncthreads();
+    if (k == 3) break;
+    // rows below: L_ic = S_ic L_cc^-T, forward substitution along the row, a thread per row
+    const int i = b0 + 16 + t;
+    if (i < T) {
+      double x[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        double v = S[i * LDS + b0 + c];
+#pragma unroll
+        for (int m = 0; m < c; ++m) v = fma(-x[m], S[(b0 + c) * LDS + b0 + m], v);
+        x[c] = v * rcp[b0 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) S[i * LDS + b0 + c] = x[c];
+    }
+    __syncthreads();
+    // trailing lower triangle: S_ic -= sum_m L_im L_cm over the block column
+    const int n = T - b0 - 16, w = n + 1;
+    for (int e = t; e < (n / 2) * w; e += kThreads) {
+      const int p = e / w, q = e % w;
+      const int ii = b0 + 16 + (q <= p ? p : n - 1 - p);
+      const int c = b0 + 16 + (q <= p ? q : q - p - 1);
+      double v = S[ii * LDS + c];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v = fma(-S[ii * LDS + b0 + m], S[c * LDS + b0 + m], v);
+      S[ii * LDS + c] = v;
+    }
+    __syncthreads();
+  }
+  // inverse of every diagonal sub-block: warp k, lane c < 16 owns column c (entries above the
+  // diagonal are zero, so the sums may start at m = 0)
+  if (warp < 4) {
+    const int b0 = 16 * warp, c = lane & 15;
+    double col[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const double ri = rcp[b0 + i];
+      double v = 0.0;
+#pragma unroll
+      for (int m = 0; m < i; ++m) v = fma(-S[(b0 + i) * LDS + b0 + m], col[m], v);
+      col[i] = i < c ? 0.0 : (i == c ? ri : v * ri);
+    }
+    if (lane < 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) Di[(b0 + i) * LDS + b0 + c] = col[i];
+    }
+  }
+  __syncthreads();
+  for (int d = 1; d < 4; ++d) {
+    const int np = 4 - d;  // sub-block pairs (i, k = i - d), i = d..3
+    // Tmp_p = sum_{k <= m < i} L_im Di_mk
+    for (int e = t; e < np * 256; e += kThreads) {
+      const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
+      const int bi = d + p, bk = p;
+      double v = 0.0;
+      for (int m = 16 * bk; m < 16 * bi; ++m)
+        v = fma(S[(16 * bi + r) * LDS + m], Di[m * LDS + 16 * bk + c], v);
+      Tmp[e] = v;
+    }
+    __syncthreads();
+    // Di_ik = -Di_ii Tmp_p
+    for (int e = t; e < np * 256; e += kThreads) {
+      const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
+      const int bi = d + p, bk = p;
+      double v = 0.0;
+#pragma unroll
+      for (int m = 0; m < 16; ++m)
+        v = fma(Di[(16 * bi + r) * LDS + 16 * bi + m], Tmp[(p << 8) + m * 16 + c], v);
+      Di[(16 * bi + r) * LDS + 16 * bk + c] = -v;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_cholesky(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
                const TileRow *__restrict__ trow, double *__restrict__ fac,
@@ -117,17 +247,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   double *Bt = At + T * LD;                            // [T][LD]
   double *S = At;                                      // [T][LDS], diagonal phase only
   double *Di = Bt;                                     // [T][LDS], diagonal phase only
+  double *Tmp = Bt + T * LD;                           // [3 * 256], diagonal phase only
   __shared__ double s_pmin;
   __shared__ int s_fail;
   __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
-  __shared__ double s_rcp[T], s_d[T];            // pivots and their reciprocals
 
   const int b = blist[blockIdx.x];
   const BlockDesc B = blk[b];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int I = tid; I < B.nt; I += kThreads) s_tr[I] = trow[B.trow0 + I];
   const TileRow *tr = s_tr;
-  const int tr4 = tid / 16, tc4 = tid % 16;
   if (tid == 0) {
     s_pmin = 1e300;
     s_fail = 0;
@@ -137,71 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int K = 0; K < B.nt; ++K) {
     const TileRow TK = tr[K];
     double *gKK = tile_ptr(fac, TK, K);
-    // ---- 1. diagonal tile, right-looking with the column scaling deferred: step j
-    // subtracts S_ij S_kj / d_j from the trailing triangle (one barrier per column);
-    // afterwards L_jj = sqrt(d_j) and L_ij = S_ij / sqrt(d_j)
-    // Divisions and square roots run as long FP64 sequences on GB300's narrow FP64 pipe,
-    // whose cost is per warp instruction: each reciprocal is computed by one warp only
-    // (warp 0, lane 0) and shared, never by every warp.
+    // ---- 1-2. factor the diagonal tile and invert it, in shared memory
     for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
     __syncthreads();
-    for (int j = 0; j < T; ++j) {
-      if (tid == 0) {
-        double dj = S[j * LDS + j];
-        if (K * T + j < B.m) s_pmin = fmin(s_pmin, dj);
-        if (!(dj > 0.0) || !isfinite(dj)) {
-          s_fail = 1;
-          dj = 1.0;
-        }
-        s_rcp[j] = 1.0 / dj;
-        s_d[j] = dj;
-      }
-      __syncthreads();
-      const double inv = s_rcp[j];
-      for (int i = j + 1 + tr4; i < T; i += 16) {
-        const double t = S[i * LDS + j] * inv;
-        for (int k = j + 1 + tc4; k <= i; k += 16) S[i * LDS + k] = fma(-t, S[k * LDS + j], S[i * LDS + k]);
-      }
-      __syncthreads();
-    }
-    // L_jj = sqrt(d_j), L_ij = S_ij / sqrt(d_j): one square root and one reciprocal per
-    // column (warps 0 and 1), then products
-    if (tid < T) {
-      const double r = sqrt(s_d[tid]);
-      s_d[tid] = r;
-      s_rcp[tid] = 1.0 / r;
-    }
-    __syncthreads();
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int i = e / T, j = e % T;
-      if (j > i) continue;
-      Di[i * LDS + j] = i == j ? s_d[j] : S[i * LDS + j] * s_rcp[j];  // L_KK, staged in Di
-    }
-    __syncthreads();
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int i = e / T, j = e % T;
-      S[i * LDS + j] = j <= i ? Di[i * LDS + j] : 0.0;
-    }
-    __syncthreads();
-    // ---- 2. inv(L_KK) by rows: Di_ic = (delta_ic - sum_{c<=k<i} L_ik Di_kc) / L_ii; row i
-    // depends on rows < i only, so all columns c of a row run in parallel (4 threads per
-    // column split the sum, fixed-order shuffle reduction)
-    {
-      // 1 / L_ii of every row is s_rcp (computed above from the same sqrt(d_i))
-      const int c = tid >> 2, q = tid & 3;
-      for (int i = 0; i < T; ++i) {
-        double acc = 0.0;
-        if (c < i)
-          for (int k = c + q; k < i; k += 4) acc = fma(S[i * LDS + k], Di[k * LDS + c], acc);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (q == 0) {
-          const double ri = s_rcp[i];
-          Di[i * LDS + c] = c < i ? -acc * ri : (c == i ? ri : 0.0);
-        }
-        __syncthreads();
-      }
-    }
+    diag_factor64(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
     // write L_KK (upper part zeroed) and inv(L_KK)
     double *dK = dinv + B.dinv_off + (int64_t)K * T * T;
     for (int e = tid; e < T * T; e += kThreads) {
@@ -221,8 +289,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       double *gIK = tile_ptr(fac, TI, K);
       load_kmajor(gIK, At);
       __syncthreads();
-      for (int u = warp; u < 16; u += kWarps) {
-        const int R = u >> 2, C = u & 3;
+      // unit (R, C) stops at k = 16 (C + 1): warp w takes columns w % 4 and 3 - w % 4, so
+      // every warp (and SM sub-partition) does the same 5 sixteenths of the k range
+      for (int v = 0; v < 2; ++v) {
+        const int R = 2 * (warp >> 2) + v, C = v == 0 ? (warp & 3) : 3 - (warp & 3);
         double acc[2][4];
         unit_product(At, Bt, R, C, 16 * (C + 1), acc);
         unit_store(gIK, R, C, acc, false);
@@ -400,8 +470,9 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     load_rowmajor(g, Bt);
     __syncthreads();
-    for (int u = warp; u < 16; u += kWarps) {
-      const int R = u >> 2, C = u & 3;
+    // unit (R, C) stops at k = 16 (R + 1): warp w takes rows w / 4 and 3 - w / 4 (balanced)
+    for (int v = 0; v < 2; ++v) {
+      const int R = v == 0 ? (warp >> 2) : 3 - (warp >> 2), C = warp & 3;
       double acc[2][4];
       unit_product(At, Bt, R, C, 16 * (R + 1), acc);
       unit_store(g, R, C, acc, false);
@@ -409,12 +480,14 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-constexpr int kCholSmem = (int)sizeof(double) * 2 * T * LD;
+constexpr int kCholSmem = (int)sizeof(double) * 2 * T * LD;      // operand tiles
+constexpr int kCholSmemDiag = kCholSmem + (int)sizeof(double) * 3 * 256;  // + Tmp
 // dynamic shared memory requested by k_cholesky: more than half of an SM's 228 KB, so that
 // one block runs per SM (measured fastest, see the header)
 constexpr int kCholSmemLaunch = 120 * 1024;
 static_assert(T * LDS <= T * LD, "diagonal scratch inside an operand tile");
-static_assert(kCholSmemLaunch >= kCholSmem, "launch reservation covers the tiles");
+static_assert(kCholSmemLaunch >= kCholSmemDiag, "launch reservation covers the tiles");
+static_assert(kWarps == 8, "unit maps assume 8 warps");
 
 }  // namespace
 
