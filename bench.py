@@ -290,6 +290,7 @@ def leg_summary(r, st, times, kt, x, n, nnz, nblk):
            "factor_bytes": st["factor_bytes"], "pass_bytes": st["pass_bytes"],
            "factor_gflop": round(st["factor_flops"] / 1e9, 3),
            "cholesky_tflops": round(st["factor_flops"] / (st["t_chol_ms"] * 1e-3) / 1e12, 4),
+           "cholesky_split_blocks": st["chol_split_blocks"],
            "kernel_launches": st["kernel_launches"],
            "proj_config": {"ring_slots": st["proj_slots"], "ctas_per_sm": st["proj_ctas_per_sm"],
                            "tuned": st["proj_tuned"]},

@@ -166,6 +166,8 @@ typedef struct cimmino_stats {
   int32_t proj_tuned;         /* 0 default, 1 measured at setup, 2 from the cache     */
   int32_t mr_tc_blocks;       /* blocks whose multi-RHS projection (nrhs > 1) runs on  */
                               /* the tensor cores; the others run on CUDA cores      */
+  int32_t chol_split_blocks;  /* FP64 Cholesky: blocks shared by two CTAs (the largest */
+                              /* ones, when they would set the factorisation time)   */
 } cimmino_stats;
 
 typedef struct cimmino_ctx cimmino_ctx;
@@ -372,8 +374,10 @@ int cimmino_proj_timing(cimmino_ctx *ctx, double *ms_total, int64_t *launches);
 /* Watchdog self-test (failure detection without a GPU fault): one device thread waits,
  * with the same bounded try_wait loop as the projection ring, on an mbarrier that nothing
  * completes.  After limit_us microseconds (or 2^20 polls) it gives up and sets bit 8 of
- * the device error word, which is copied to *err_word.  Needs no context; runs on a
- * stream of its own on the current device.
+ * the device error word.  Then a CTA waits, as one half of a block the FP64 Cholesky splits
+ * over two CTAs, for a partner that never arrives (a flag nothing sets); it gives up after
+ * limit_us and sets bit 16.  The word is copied to *err_word (24 when both gave up).  Needs
+ * no context; runs on a stream of its own on the current device.
  * Returns CIMMINO_ETIMEOUT when the wait gave up (the expected outcome), CIMMINO_OK if
  * it did not, EINVAL (limit_us outside [1, 1e6], NULL err_word), ECUDA, ENOMEM. */
 int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word);

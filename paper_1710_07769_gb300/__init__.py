@@ -95,7 +95,7 @@ class StatsStruct(C.Structure):
                 ("factor_flops", C.c_double), ("t_chol_ms", C.c_double),
                 ("nnz_gram", C.c_int64), ("proj_slots", C.c_int32),
                 ("proj_ctas_per_sm", C.c_int32), ("proj_tuned", C.c_int32),
-                ("mr_tc_blocks", C.c_int32)]
+                ("mr_tc_blocks", C.c_int32), ("chol_split_blocks", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -496,8 +496,9 @@ def aat(A, stream=None):
 
 
 def selftest_wait(limit_us: int = 2000):
-    """Watchdog self-test: a device wait on a barrier nothing completes must give up after
-    limit_us.  Returns (status code, device error word); ETIMEOUT is the expected status."""
+    """Watchdog self-test: a device wait on a barrier nothing completes and the FP64
+    Cholesky's wait for a partner CTA that never arrives must both give up after limit_us.
+    Returns (status code, device error word: 8 | 16); ETIMEOUT is the expected status."""
     L = load()
     word = C.c_int32(0)
     code = L.cimmino_selftest_wait(int(limit_us), C.byref(word))

@@ -231,6 +231,7 @@ struct cimmino_ctx {
   double factor_flops = 0.0;  // algorithmic flops of the envelope Cholesky of all G_i
   double t_chol_ms = 0.0;     // device time of the batched Cholesky launch alone
   int32_t fallbacks = 0;
+  int32_t chol_split = 0;  // FP64 Cholesky blocks shared by two CTAs
   int64_t setup_launches = 0;  // kernels launched by the setup
   double t_setup_ms = 0.0, t_factor_ms = 0.0;
   bool have_aat = false;
@@ -316,6 +317,167 @@ class Stages {
 };
 
 // ------------------------------------------------------------------ setup
+// ---- static schedule of the FP64 Cholesky (k_cholesky)
+// Cost of a block in units of one FP64 64 x 64 x 64 tile product, with weights measured per
+// phase of k_cholesky on GB300: the factor and inverse of a diagonal tile 1.45 (a serial pivot
+// chain on one SM sub-partition), a triangular solve 0.62, a symmetric diagonal update 0.75, a
+// full update 1.
+constexpr double kCostDiag = 1.45, kCostTrsm = 0.62, kCostSymUpd = 0.75;
+// A pair barrier of a split block (a few L2 round trips), in the same unit.
+constexpr double kCostPairSync = 0.03;
+// A block whose cost reaches this fraction of the mean load per CTA is split over two CTAs.
+constexpr double kSplitFraction = 0.9;
+
+struct CholPlan {
+  std::vector<CholItem> items;
+  std::vector<int32_t> ptr;  // ncta + 1
+  int32_t nsplit = 0;
+};
+
+// First-fit decreasing of jobs (sorted by decreasing cost) into bins of capacity cap on top of
+// the loads `load`; false if a job fits nowhere.
+bool ffd_pack(const std::vector<int32_t> &jobs, const std::vector<double> &cost, double cap,
+              std::vector<double> load, std::vector<int32_t> &bin_of) {
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    const double w = cost[jobs[q]];
+    size_t k = 0;
+    while (k < load.size() && load[k] + w > cap) ++k;
+    if (k == load.size()) return false;
+    load[k] += w;
+    bin_of[q] = (int32_t)k;
+  }
+  return true;
+}
+
+// Schedule with the ns largest blocks split: their halves (the diagonal part plus half of the
+// rest, plus three pair barriers per tile column) first in CTAs 2i and 2i+1, the other blocks
+// packed by MULTIFIT: the smallest capacity that first-fit decreasing fills, found by bisection
+// between the lower bound and the greedy longest-first makespan.  Returns the makespan.
+double pack_cholesky(const std::vector<int32_t> &order, const std::vector<double> &cost,
+                     const std::vector<double> &diag, const std::vector<double> &sync,
+                     int32_t maxcta, int32_t ns, CholPlan &P) {
+  const int32_t n = (int32_t)order.size();
+  const int32_t ncta = std::min(maxcta, n + ns);
+  std::vector<double> load(ncta, 0.0);
+  for (int32_t i = 0; i < ns; ++i) {
+    const int32_t b = order[i];
+    load[2 * i] = load[2 * i + 1] = diag[b] + 0.5 * (cost[b] - diag[b]) + sync[b];
+  }
+  std::vector<int32_t> jobs(order.begin() + ns, order.end());
+  std::vector<int32_t> bin_of(jobs.size(), 0);
+  // greedy longest-first (list scheduling): a feasible capacity
+  std::vector<double> l(load);
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    const size_t k = (size_t)(std::min_element(l.begin(), l.end()) - l.begin());
+    l[k] += cost[jobs[q]];
+    bin_of[q] = (int32_t)k;
+  }
+  double hi = 0.0, sum = 0.0, big = 0.0;
+  for (double x : l) hi = std::max(hi, x);
+  for (double x : load) sum += x, big = std::max(big, x);
+  for (int32_t b : jobs) sum += cost[b], big = std::max(big, cost[b]);
+  double lo = std::max(big, sum / ncta);
+  std::vector<int32_t> trial(jobs.size());
+  for (int it = 0; it < 32 && hi - lo > 1e-6 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (ffd_pack(jobs, cost, mid, load, trial)) {
+      hi = mid;
+      bin_of = trial;
+    } else {
+      lo = mid;
+    }
+  }
+  std::vector<std::vector<CholItem>> lists(ncta);
+  for (int32_t i = 0; i < ns; ++i) {
+    lists[2 * i].push_back(CholItem{order[i], 0, 2, i});
+    lists[2 * i + 1].push_back(CholItem{order[i], 1, 2, i});
+  }
+  for (size_t q = 0; q < jobs.size(); ++q) lists[bin_of[q]].push_back(CholItem{jobs[q], 0, 1, 0});
+  P.items.clear();
+  P.ptr.assign(1, 0);
+  double makespan = 0.0;
+  for (int32_t k = 0; k < ncta; ++k) {
+    double t = load[k];  // the split half, if any
+    for (const CholItem &it : lists[k]) {
+      P.items.push_back(it);
+      if (it.nparts == 1) t += cost[it.b];
+    }
+    P.ptr.push_back((int32_t)P.items.size());
+    makespan = std::max(makespan, t);
+  }
+  P.nsplit = ns;
+  return makespan;
+}
+
+// blocks: the blocks to factor; cost / diag: their costs and the diagonal-tile part of them;
+// nt: their tile rows; maxcta: CTAs that can be resident at once.  Tries a ladder of split
+// counts among the blocks whose cost reaches kSplitFraction of the mean load per CTA and keeps
+// the smallest count with the shortest makespan.
+CholPlan plan_cholesky(const std::vector<int32_t> &blocks, const std::vector<double> &cost,
+                       const std::vector<double> &diag, const std::vector<double> &sync,
+                       int32_t maxcta, bool allow_split) {
+  CholPlan best;
+  std::vector<int32_t> order(blocks);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  const int32_t n = (int32_t)order.size();
+  if (n == 0 || maxcta <= 0) {
+    best.ptr.assign(1, 0);
+    return best;
+  }
+  double total = 0.0;
+  for (int32_t b : order) total += cost[b];
+  int32_t nmax = 0;
+  while (allow_split && nmax < n && 2 * (nmax + 1) <= maxcta &&
+         cost[order[nmax]] >= kSplitFraction * total / maxcta)
+    ++nmax;
+  std::vector<int32_t> ladder;
+  for (int32_t ns = 1; ns < nmax; ns = ns < 4 ? ns + 1 : ns + ns / 2) ladder.push_back(ns);
+  if (nmax > 0) ladder.push_back(nmax);
+  double best_t = pack_cholesky(order, cost, diag, sync, maxcta, 0, best);
+  for (int32_t ns : ladder) {
+    CholPlan P;
+    const double t = pack_cholesky(order, cost, diag, sync, maxcta, ns, P);
+    if (t < best_t * (1.0 - 1e-3)) {
+      best_t = t;
+      best = std::move(P);
+    }
+  }
+  return best;
+}
+
+// Uploads a plan and runs k_cholesky on it (the flags and the error word zeroed first);
+// returns after the launch, the buffers stay alive in `keep` until the caller synchronises.
+struct CholLaunchBufs {
+  DBuf<CholItem> items;
+  DBuf<int32_t> ptr, flags, err;
+};
+void run_cholesky64(cimmino_ctx *c, const CholPlan &P, double *pmin, int32_t *pfail,
+                    CholLaunchBufs &keep, cudaStream_t s) {
+  const int32_t ncta = (int32_t)P.ptr.size() - 1;
+  if (ncta <= 0) return;
+  keep.items.alloc(P.items.size());
+  keep.ptr.alloc(P.ptr.size());
+  keep.flags.alloc(std::max<int32_t>(2 * P.nsplit, 1));
+  keep.err.alloc(1);
+  h2d(keep.items.p, P.items.data(), P.items.size(), s);
+  h2d(keep.ptr.p, P.ptr.data(), P.ptr.size(), s);
+  CUDA_TRY(cudaMemsetAsync(keep.flags.p, 0, keep.flags.n * sizeof(int32_t), s));
+  CUDA_TRY(cudaMemsetAsync(keep.err.p, 0, sizeof(int32_t), s));
+  CUDA_TRY(launch_cholesky(c->blk.p, keep.items.p, keep.ptr.p, ncta, P.nsplit > 0, c->trow.p,
+                           c->fac64.p, c->dinv64.p, pmin, pfail, keep.flags.p, keep.err.p, s));
+}
+
+// Resident CTAs of k_cholesky and whether a schedule may split blocks (cooperative launch).
+void cholesky_capacity(int32_t &maxcta, bool &allow_split) {
+  int dev = 0, coop = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  maxcta = cholesky_resident_ctas();
+  if (maxcta <= 0) fail(CIMMINO_ECUDA, "k_cholesky cannot be resident on this device");
+  allow_split = coop != 0;
+}
+
 void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_t *K,
                 const int32_t *const *perms, const int64_t *const *bps) {
   cudaStream_t s = c->stream;
@@ -648,12 +810,16 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   // r_I of every tile row: the diagonal factorisations r_K^3 / 3, the triangular solves
   // r_I r_K^2 of the tiles (I, K) below them, and the trailing products 2 r_I r_J r_K
   // (r_I^2 r_K on the symmetric diagonal tiles J = I) for K < J <= I inside the envelope.
+  // Also the cost of every block for the FP64 Cholesky's schedule (tile counts weighted
+  // with the per-phase times of k_cholesky).
   c->factor_flops = 0.0;
-  std::vector<double> blk_flops(nblk, 0.0);
+  std::vector<double> blk_flops(nblk, 0.0), chol_cost(nblk, 0.0), chol_diag(nblk, 0.0),
+      chol_sync(nblk, 0.0);
   for (int32_t b = 0; b < nblk; ++b) {
     const BlockDesc &B = c->hblk[b];
     auto rows = [&](int32_t I) { return (double)std::min(kTile, B.m - I * kTile); };
     double f = 0.0;
+    int64_t ntrsm = 0, nfull = 0;
     for (int32_t K = 0; K < B.nt; ++K) {
       const double rK = rows(K);
       f += rK * rK * rK / 3.0;
@@ -661,12 +827,19 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
         if (c->htrow[B.trow0 + I].j0 > K) continue;
         const double rI = rows(I);
         f += rI * rK * rK + rI * rI * rK;  // solve of (I, K), update of (I, I)
+        ++ntrsm;
         for (int32_t J = K + 1; J < I; ++J)
-          if (c->htrow[B.trow0 + J].j0 <= K) f += 2.0 * rI * rows(J) * rK;
+          if (c->htrow[B.trow0 + J].j0 <= K) {
+            f += 2.0 * rI * rows(J) * rK;
+            ++nfull;
+          }
       }
     }
     blk_flops[b] = f;
     c->factor_flops += f;
+    chol_diag[b] = kCostDiag * B.nt;
+    chol_cost[b] = chol_diag[b] + (kCostTrsm + kCostSymUpd) * (double)ntrsm + (double)nfull;
+    chol_sync[b] = 3.0 * kCostPairSync * B.nt;
   }
   c->t_setup_ms = tsetup.stop_ms(s);
 
@@ -699,11 +872,20 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     tc_scratch.alloc(cholesky_tc_scratch_floats(off));
     tc_rowblk.alloc(ntrow);
   }
+  // FP64: a static schedule over the resident CTAs (built before the timer starts)
+  CholPlan plan;
+  CholLaunchBufs cbufs;
+  int32_t maxcta = 0;
+  bool allow_split = false;
+  if (fp64) {
+    cholesky_capacity(maxcta, allow_split);
+    plan = plan_cholesky(hlist, chol_cost, chol_diag, chol_sync, maxcta, allow_split);
+    c->chol_split = plan.nsplit;
+  }
   Timer tchol;
   tchol.start(s);
   if (fp64) {
-    launch_cholesky(c->blk.p, blist.p, nblk, c->trow.p, c->fac64.p, c->dinv64.p, pmin.p,
-                    pfail.p, s);
+    run_cholesky64(c, plan, pmin.p, pfail.p, cbufs, s);
   } else {
     launch_cholesky_tc(c->blk.p, blist.p, nblk, nblk, ntrow, c->trow.p, c->fac32.p, c->dinv32.p,
                        tc_scratch.p, off, tc_rowblk.p, pmin.p, pfail.p, c->err_flag.p, s);
@@ -721,7 +903,10 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   std::vector<double> hpmin(nblk);
   d2h(hfail.data(), pfail.p, nblk, s);
   d2h(hpmin.data(), pmin.p, nblk, s);
+  int32_t hcerr = 0;
+  if (cbufs.err.p) d2h(&hcerr, cbufs.err.p, 1, s);
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (hcerr) fail(CIMMINO_ETIMEOUT, "a pair wait of the FP64 Cholesky ran out (split block)");
   if (fp64) {
     for (int32_t b = 0; b < nblk; ++b)
       if (hfail[b])
@@ -754,13 +939,17 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
       h2d(blist.p, fb.data(), fb.size(), s);
       launch_gram_scatter(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->brp.p, c->bci.p,
                           c->bcv.p, c->fac64.p, (int64_t)c->fac64.n, 1, s);
-      launch_cholesky(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
-                      c->dinv64.p, pmin.p, pfail.p, s);
+      if (maxcta == 0) cholesky_capacity(maxcta, allow_split);
+      CholLaunchBufs fbufs;
+      run_cholesky64(c, plan_cholesky(fb, chol_cost, chol_diag, chol_sync, maxcta, allow_split), pmin.p,
+                     pfail.p, fbufs, s);
       launch_ntransform64(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
                           c->dinv64.p, s);
       c->setup_launches += 3;
       d2h(hfail.data(), pfail.p, nblk, s);
+      d2h(&hcerr, fbufs.err.p, 1, s);
       CUDA_TRY(cudaStreamSynchronize(s));
+      if (hcerr) fail(CIMMINO_ETIMEOUT, "a pair wait of the FP64 Cholesky ran out (split block)");
       for (int32_t b : fb)
         if (hfail[b])
           fail(CIMMINO_ESINGULAR, "Gram block " + std::to_string(b) +
@@ -1314,6 +1503,7 @@ int solve_impl(cimmino_ctx *c, int32_t nrhs, double tol, cimmino_stats *stats) {
         o.proj_ctas_per_sm = c->proj_minb;
         o.proj_tuned = c->tuned;
         o.mr_tc_blocks = nrhs > 1 ? c->mr_ntc : 0;
+        o.chol_split_blocks = c->chol_split;
         o.pass_bytes = c->pass_bytes;
         // rhs scale, xi projection, A^T y, CG init, 4 kernels plus the projection per
         // iteration, final stats; several right-hand sides may take two projection kernels
@@ -1552,11 +1742,14 @@ int cimmino_selftest_wait(int32_t limit_us, int32_t *err_word) {
     Allocator mem;
     mem.stream = s;
     AllocScope scope(&mem);
-    DBuf<int32_t> err;
+    DBuf<int32_t> err, flag;
     err.alloc(1);
+    flag.alloc(2);
     cudaError_t e = cudaMemsetAsync(err.p, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 2 * sizeof(int32_t), s);
     if (e == cudaSuccess) {
       launch_wait_selftest((uint64_t)limit_us * 1000ull, err.p, s);
+      launch_pair_selftest((uint64_t)limit_us * 1000ull, flag.p, err.p, s);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(err_word, err.p, sizeof(int32_t), cudaMemcpyDefault, s);

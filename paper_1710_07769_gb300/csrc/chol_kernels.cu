@@ -43,11 +43,25 @@ __device__ __forceinline__ double *tile_ptr(double *fac, const TileRow &tr, int 
   return fac + tr.off + (int64_t)(J - tr.j0) * T * T;
 }
 
+// Global reads of factor tiles.  CG: through L2 only (ld.global.cg), for tiles that the other
+// CTA of a split block writes (this SM's L1 may hold an older copy).
+template <bool CG>
+__device__ __forceinline__ double ldg(const double *p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+template <bool CG>
+__device__ __forceinline__ double2 ldg2(const double *p) {
+  if (CG) return __ldcg(reinterpret_cast<const double2 *>(p));
+  return *reinterpret_cast<const double2 *>(p);
+}
+
 // Load a row-major global tile into k-major shared storage At[k][r] = tile(r, k).
-__device__ __forceinline__ void load_kmajor(const double *__restrict__ g, double *At) {
+template <bool CG = false>
+__device__ __forceinline__ void load_kmajor(const double *g, double *At) {
   for (int e = threadIdx.x; e < T * T; e += kThreads) {
     const int r = e / T, k = e % T;
-    At[k * LD + r] = g[e];
+    At[k * LD + r] = ldg<CG>(g + e);
   }
 }
 // Load a row-major global tile into row-major shared storage Bt[k][c] = tile(k, c).
@@ -90,14 +104,16 @@ __device__ __forceinline__ void lower_unit(int u, int &R, int &C) {
 
 // out(r, c) = acc (mode 0) or out(r, c) -= acc (mode 1) for the lane's elements of unit (R, C)
 // of a row-major global tile.
+template <bool CG = false>
 __device__ __forceinline__ void unit_store(double *out, int R, int C, const double (&acc)[2][4],
                                            bool subtract) {
   const int lane = threadIdx.x & 31, lr = lane >> 2, lc = lane & 3;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    double2 *p = reinterpret_cast<double2 *>(out + (16 * R + 2 * lr + i) * T + 16 * C + 4 * lc);
+    double *q = out + (16 * R + 2 * lr + i) * T + 16 * C + 4 * lc;
+    double2 *p = reinterpret_cast<double2 *>(q);
     if (subtract) {
-      const double2 x0 = p[0], x1 = p[1];
+      const double2 x0 = ldg2<CG>(q), x1 = ldg2<CG>(q + 2);
       p[0] = make_double2(x0.x - acc[i][0], x0.y - acc[i][1]);
       p[1] = make_double2(x1.x - acc[i][2], x1.y - acc[i][3]);
     } else {
@@ -237,23 +253,59 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_cholesky(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
-               const TileRow *__restrict__ trow, double *__restrict__ fac,
-               double *__restrict__ dinv, double *__restrict__ pivmin,
-               int32_t *__restrict__ pivfail) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *At = reinterpret_cast<double *>(smem_raw);  // [T][LD]
-  double *Bt = At + T * LD;                            // [T][LD]
-  double *S = At;                                      // [T][LDS], diagonal phase only
-  double *Di = Bt;                                     // [T][LDS], diagonal phase only
-  double *Tmp = Bt + T * LD;                           // [3 * 256], diagonal phase only
-  __shared__ double s_pmin;
-  __shared__ int s_fail;
-  __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t kPairWaitNs = 2000000000ull;  // a pair wait gives up after ~2 s
+constexpr uint32_t kPairSpins = 1u << 26;         // ... or after this many polls
 
-  const int b = blist[blockIdx.x];
-  const BlockDesc B = blk[b];
+// Barrier of the two CTAs that share a split block: each publishes its epoch in flag[part]
+// and waits, bounded, until flag[1 - part] has reached it.  The fences order the tile writes
+// before the barrier ahead of the other CTA's reads after it, which go to L2 (CG loads).
+// Returns false (and sets `bit` in *err) when the wait ran out.
+__device__ bool pair_sync(int32_t *flag, int part, int32_t epoch, int32_t *err, int *s_ok,
+                          uint64_t limit_ns = kPairWaitNs, int32_t bit = 1) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flag + part, epoch);
+    int ok = 1;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+      int32_t v;
+      asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag + 1 - part) : "memory");
+      if (v >= epoch) break;
+      if (i >= kPairSpins || global_ns() - t0 > limit_ns) {
+        atomicOr(err, bit);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Right-looking Cholesky of one Gram block (the steps in the file header).  SPLIT: the block
+// is shared by two CTAs (part 0 and 1) that meet at pair barriers three times per tile column:
+// part 0 factors the diagonal tile; the triangular solves alternate between the parts; the
+// update rows go to the part with less update work so far (largest rows first).
+template <bool SPLIT>
+__device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part, int32_t *flag,
+                                             const TileRow *__restrict__ trow,
+                                             double *__restrict__ fac, double *__restrict__ dinv,
+                                             double *__restrict__ pivmin,
+                                             int32_t *__restrict__ pivfail, int32_t *err,
+                                             double *At, double *Bt, double *Tmp,
+                                             TileRow *s_tr, unsigned char *s_own, double &s_pmin,
+                                             int &s_fail, int &s_ok) {
+  double *S = At;   // [T][LDS], diagonal phase only
+  double *Di = Bt;  // [T][LDS], diagonal phase only
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int I = tid; I < B.nt; I += kThreads) s_tr[I] = trow[B.trow0 + I];
   const TileRow *tr = s_tr;
@@ -262,32 +314,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     s_fail = 0;
   }
   __syncthreads();
-
+  int32_t epoch = 0;
   for (int K = 0; K < B.nt; ++K) {
     const TileRow TK = tr[K];
     double *gKK = tile_ptr(fac, TK, K);
-    // ---- 1-2. factor the diagonal tile and invert it, in shared memory
-    for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = gKK[e];
-    __syncthreads();
-    diag_factor64(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
-    // write L_KK (upper part zeroed) and inv(L_KK)
     double *dK = dinv + B.dinv_off + (int64_t)K * T * T;
-    for (int e = tid; e < T * T; e += kThreads) {
-      const int r = e / T, c = e % T;
-      gKK[e] = c <= r ? S[r * LDS + c] : 0.0;
-      dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
+    if (!SPLIT || part == 0) {
+      // ---- 1-2. factor the diagonal tile and invert it, in shared memory
+      for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = ldg<SPLIT>(gKK + e);
+      __syncthreads();
+      diag_factor64(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
+      // write L_KK (upper part zeroed) and inv(L_KK)
+      for (int e = tid; e < T * T; e += kThreads) {
+        const int r = e / T, c = e % T;
+        gKK[e] = c <= r ? S[r * LDS + c] : 0.0;
+        dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
+      }
     }
-    __syncthreads();  // L_KK and inv(L_KK) are in global memory; S / Di are free
+    if (SPLIT) {
+      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
+    } else {
+      __syncthreads();  // L_KK and inv(L_KK) are in global memory; S / Di are free
+    }
     // Bt[k][c] = inv(L_KK)(c, k) for the TRSM below (upper triangle: unit column block C
-    // needs k < 16 (C + 1)); read back from dinv (L1-resident)
-    load_kmajor(dK, Bt);
+    // needs k < 16 (C + 1)); read back from dinv
+    load_kmajor<SPLIT>(dK, Bt);
     __syncthreads();
     // ---- 3. L_IK = G_IK * Di^T for every stored tile below the diagonal
+    int q = 0;
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
+      if (SPLIT && (q++ & 1) != part) continue;
       double *gIK = tile_ptr(fac, TI, K);
-      load_kmajor(gIK, At);
+      load_kmajor<SPLIT>(gIK, At);
       __syncthreads();
       // unit (R, C) stops at k = 16 (C + 1): warp w takes columns w % 4 and 3 - w % 4, so
       // every warp (and SM sub-partition) does the same 5 sixteenths of the k range
@@ -299,17 +359,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
     }
+    if (SPLIT) {
+      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
+      // rows of the update: row I costs its tiles (K, I) inside the envelope (3/4 for the
+      // symmetric diagonal one); the larger rows first, each to the part with less so far
+      if (tid == 0) {
+        int w[2] = {0, 0};
+        int act = 0;  // envelope rows in K+1..I
+        for (int I = K + 1; I < B.nt; ++I) act += tr[I].j0 <= K;
+        for (int I = B.nt - 1; I > K; --I) {
+          if (tr[I].j0 > K) continue;
+          const int cost = 4 * act - 1;  // (act - 1) full tiles + 3/4, in quarters
+          const int pick = w[1] < w[0] ? 1 : 0;
+          s_own[I] = (unsigned char)pick;
+          w[pick] += cost;
+          --act;
+        }
+      }
+      __syncthreads();
+    }
     // ---- 4. trailing update G_IJ -= L_IK L_JK^T; a diagonal tile (J = I) is symmetric and
     // only its lower units are updated (the upper triangle of G_II is never read)
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
-      load_kmajor(tile_ptr(fac, TI, K), At);
+      if (SPLIT && s_own[I] != part) continue;
+      load_kmajor<SPLIT>(tile_ptr(fac, TI, K), At);
       for (int J = K + 1; J <= I; ++J) {
         const TileRow TJ = tr[J];
         if (TJ.j0 > K) continue;
         __syncthreads();  // previous use of Bt finished
-        load_kmajor(tile_ptr(fac, TJ, K), Bt);
+        load_kmajor<SPLIT>(tile_ptr(fac, TJ, K), Bt);
         __syncthreads();
         double *gIJ = tile_ptr(fac, TI, J);
         if (J < I) {
@@ -317,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int R = u >> 2, C = u & 3;
             double acc[2][4];
             unit_product(At, Bt, R, C, T, acc);
-            unit_store(gIJ, R, C, acc, true);
+            unit_store<SPLIT>(gIJ, R, C, acc, true);
           }
         } else {
           for (int u = warp; u < 10; u += kWarps) {
@@ -325,17 +405,59 @@ __global__ void __launch_bounds__(kThreads, 1)
             lower_unit(u, R, C);
             double acc[2][4];
             unit_product(At, Bt, R, C, T, acc);
-            unit_store(gIJ, R, C, acc, true);
+            unit_store<SPLIT>(gIJ, R, C, acc, true);
           }
         }
       }
       __syncthreads();
     }
-    __syncthreads();
+    if (SPLIT) {
+      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
+    } else {
+      __syncthreads();
+    }
   }
-  if (tid == 0) {
+  if (tid == 0 && (!SPLIT || part == 0)) {
     pivmin[b] = s_pmin;
     pivfail[b] = s_fail;
+  }
+  __syncthreads();  // the shared tables are reused by the CTA's next block
+}
+
+// Watchdog self-test of the pair wait: part 0 of a pair whose partner never arrives (flag[1]
+// stays 0) must give up after limit_ns and set bit 16 of the error word.
+__global__ void __launch_bounds__(kThreads) k_pair_selftest(uint64_t limit_ns, int32_t *flag,
+                                                            int32_t *err) {
+  __shared__ int s_ok;
+  pair_sync(flag, 0, 1, err, &s_ok, limit_ns, 16);
+}
+
+// One CTA per SM walks its list of blocks items[cta_ptr[c] .. cta_ptr[c + 1]) (a static
+// schedule packed on the host from the blocks' measured tile costs); an item with nparts = 2
+// is half of a split block, first in the lists of both CTAs that share it.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_cholesky(const BlockDesc *__restrict__ blk, const CholItem *__restrict__ items,
+               const int32_t *__restrict__ cta_ptr, const TileRow *__restrict__ trow,
+               double *__restrict__ fac, double *__restrict__ dinv, double *__restrict__ pivmin,
+               int32_t *__restrict__ pivfail, int32_t *__restrict__ pair_flags,
+               int32_t *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *At = reinterpret_cast<double *>(smem_raw);  // [T][LD]
+  double *Bt = At + T * LD;                            // [T][LD]
+  double *Tmp = Bt + T * LD;                           // [3 * 256], diagonal phase only
+  __shared__ double s_pmin;
+  __shared__ int s_fail, s_ok;
+  __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
+  __shared__ unsigned char s_own[kMaxBlockRows / T];
+  for (int32_t i = cta_ptr[blockIdx.x]; i < cta_ptr[blockIdx.x + 1]; ++i) {
+    const CholItem it = items[i];
+    const BlockDesc B = blk[it.b];
+    if (it.nparts == 2)
+      factor_block<true>(B, it.b, it.part, pair_flags + 2 * it.slot, trow, fac, dinv, pivmin,
+                         pivfail, err, At, Bt, Tmp, s_tr, s_own, s_pmin, s_fail, s_ok);
+    else
+      factor_block<false>(B, it.b, 0, nullptr, trow, fac, dinv, pivmin, pivfail, err, At, Bt,
+                          Tmp, s_tr, s_own, s_pmin, s_fail, s_ok);
   }
 }
 
@@ -491,13 +613,42 @@ static_assert(kWarps == 8, "unit maps assume 8 warps");
 
 }  // namespace
 
-void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                     const TileRow *trow, double *fac, double *dinv, double *pivmin,
-                     int32_t *pivfail, cudaStream_t s) {
-  if (nlist <= 0) return;
-  cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemLaunch);
-  k_cholesky<<<(unsigned)nlist, kThreads, kCholSmemLaunch, s>>>(blk, blist, trow, fac, dinv,
-                                                               pivmin, pivfail);
+void launch_pair_selftest(uint64_t limit_ns, int32_t *flag, int32_t *err, cudaStream_t s) {
+  k_pair_selftest<<<1, kThreads, 0, s>>>(limit_ns, flag, err);
+}
+
+int32_t cholesky_resident_ctas() {
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kCholSmemLaunch) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cholesky, kThreads,
+                                                    kCholSmemLaunch) != cudaSuccess)
+    return 0;
+  return nsm * per_sm;
+}
+
+cudaError_t launch_cholesky(const BlockDesc *blk, const CholItem *items, const int32_t *cta_ptr,
+                            int32_t ncta, bool cooperative, const TileRow *trow, double *fac,
+                            double *dinv, double *pivmin, int32_t *pivfail, int32_t *pair_flags,
+                            int32_t *err, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemLaunch);
+  if (e != cudaSuccess) return e;
+  if (!cooperative) {
+    k_cholesky<<<(unsigned)ncta, kThreads, kCholSmemLaunch, s>>>(blk, items, cta_ptr, trow, fac,
+                                                                dinv, pivmin, pivfail, pair_flags,
+                                                                err);
+    return cudaGetLastError();
+  }
+  void *args[] = {(void *)&blk,    (void *)&items,   (void *)&cta_ptr,    (void *)&trow,
+                  (void *)&fac,    (void *)&dinv,    (void *)&pivmin,     (void *)&pivfail,
+                  (void *)&pair_flags, (void *)&err};
+  return cudaLaunchCooperativeKernel((const void *)k_cholesky, dim3((unsigned)ncta),
+                                     dim3(kThreads), args, (size_t)kCholSmemLaunch, s);
 }
 
 void launch_ntransform64(const BlockDesc *blk, const int32_t *blist, int32_t nlist,

@@ -241,10 +241,25 @@ void launch_ntransform_tc(const BlockDesc *blk, int32_t nblk, int32_t ntrow, con
 // chol_kernels.cu
 void launch_transpose_factor(const BlockDesc *blk, int32_t nblk, const TileRow *trow,
                              const TileRow *trowT, const FactorPtrs &f, cudaStream_t s);
-// FP64 blocks (FP64 precision and the FP64 refactorisation of FP32 blocks)
-void launch_cholesky(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
-                     const TileRow *trow, double *fac, double *dinv, double *pivmin,
-                     int32_t *pivfail, cudaStream_t s);
+// FP64 blocks (FP64 precision and the FP64 refactorisation of FP32 blocks) on a static
+// schedule: CTA c factors items[cta_ptr[c] .. cta_ptr[c + 1]).  An item with nparts = 2 is half
+// of a block shared by two CTAs, which meet through pair_flags[2 slot], [2 slot + 1] (zeroed
+// before the launch); such a schedule needs all its CTAs resident at once and is launched
+// cooperatively (ncta <= cholesky_resident_ctas()).  A pair wait that runs out after ~2 s sets
+// *err.
+struct CholItem {
+  int32_t b;       // block
+  int32_t part;    // 0 or 1 of a split block
+  int32_t nparts;  // 1, or 2 for a split block
+  int32_t slot;    // pair-flag slot of a split block
+};
+int32_t cholesky_resident_ctas();
+// watchdog self-test of the pair wait (flag: two zeroed ints; sets bit 16 of *err)
+void launch_pair_selftest(uint64_t limit_ns, int32_t *flag, int32_t *err, cudaStream_t s);
+cudaError_t launch_cholesky(const BlockDesc *blk, const CholItem *items, const int32_t *cta_ptr,
+                            int32_t ncta, bool cooperative, const TileRow *trow, double *fac,
+                            double *dinv, double *pivmin, int32_t *pivfail, int32_t *pair_flags,
+                            int32_t *err, cudaStream_t s);
 // N_KJ = inv(L_KK) L_KJ for the off-diagonal tiles of the listed FP64 blocks (after the Cholesky)
 void launch_ntransform64(const BlockDesc *blk, const int32_t *blist, int32_t nlist,
                          const TileRow *trow, double *fac, const double *dinv, cudaStream_t s);

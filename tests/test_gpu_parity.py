@@ -152,6 +152,29 @@ def test_fp64_factors_stencil_skyline_envelope():
         assert_close(Lg, o.factor(b), 1e-12)
 
 
+def test_fp64_split_block_matches_oracle():
+    """A block that would set the FP64 Cholesky's time on its own (2048 rows with a dense
+    envelope, beside 40 one-tile blocks) is shared by two CTAs that meet at pair barriers:
+    its factor, the small blocks' factors, the projection (Eq. 1.5) and the solve still
+    equal the oracle's."""
+    A = inputs.random_dd(2048 + 40 * 64, 8, 31)
+    bp = np.concatenate([[0], 2048 + 64 * np.arange(41)]).astype(np.int64)
+    s = g.Solver(A, bp)
+    o = oracle.Oracle(A, bp, nthreads=2)
+    f = inputs.matvec(A, np.random.default_rng(4).uniform(-1, 1, A.n))
+    x, st, code = s.solve(f, tol=1e-10)
+    assert code == 0 and st[0]["chol_split_blocks"] >= 1, st[0]
+    for b in (0, 1, 40):
+        Lg, is64 = s.factor(b)
+        assert is64
+        assert_close(Lg, o.factor(b), 1e-12, b)
+    v = np.random.default_rng(2).standard_normal(A.n)
+    assert_close(s.project(v), o.project(v), 1e-12)
+    xo, ito, *_ = o.solve(f)
+    assert abs(st[0]["iters"] - ito) <= 1
+    assert_close(x, xo, 1e-8)
+
+
 def test_fp32_factors_close_to_oracle(sys_small):
     A, perm, f = sys_small
     s = g.Solver(A, RAGGED, perm=perm, precision="fp32_refine")
