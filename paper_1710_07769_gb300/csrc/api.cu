@@ -318,11 +318,11 @@ class Stages {
 
 // ------------------------------------------------------------------ setup
 // ---- static schedule of the FP64 Cholesky (k_cholesky)
-// Cost of a block in units of one FP64 64 x 64 x 64 tile product, with weights measured per
-// phase of k_cholesky on GB300: the factor and inverse of a diagonal tile 1.45 (a serial pivot
-// chain on one SM sub-partition), a triangular solve 0.62, a symmetric diagonal update 0.75, a
-// full update 1.
-constexpr double kCostDiag = 1.45, kCostTrsm = 0.62, kCostSymUpd = 0.75;
+// Cost of a block in units of one full trailing-update tile of k_cholesky (80 us on GB300),
+// with weights fitted to the measured times of the 512 blocks of the n = 2^20 random workload
+// (0.3% mean error): a diagonal tile's factor and inverse 1.43 (a serial pivot chain, partly
+// hidden by the look-ahead), a solved tile (I, K) with the symmetric update of (I, I) 0.81.
+constexpr double kCostDiag = 1.43, kCostTrsmSym = 0.81;
 // A pair barrier of a split block (a few L2 round trips), in the same unit.
 constexpr double kCostPairSync = 0.03;
 // A block whose cost reaches this fraction of the mean load per CTA is split over two CTAs.
@@ -385,6 +385,43 @@ double pack_cholesky(const std::vector<int32_t> &order, const std::vector<double
       bin_of = trial;
     } else {
       lo = mid;
+    }
+  }
+  // local search: move a job out of the most loaded CTA, or swap it for a smaller one, while
+  // that lowers the maximum (bounded number of rounds; long lists are packed finely enough)
+  std::vector<double> bl(load);
+  for (size_t q = 0; q < jobs.size(); ++q) bl[bin_of[q]] += cost[jobs[q]];
+  const int rounds = jobs.size() <= 4096 ? 4 * ncta : 0;
+  for (int round = 0; round < rounds; ++round) {
+    const int32_t h = (int32_t)(std::max_element(bl.begin(), bl.end()) - bl.begin());
+    double best = 1e-9 * bl[h];
+    size_t bq = 0, bi = 0;
+    int32_t bk = -1;
+    bool swap = false;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      if (bin_of[q] != h) continue;
+      const double cq = cost[jobs[q]];
+      for (size_t i = 0; i < jobs.size(); ++i) {  // swaps (q <-> i), i in another CTA
+        const int32_t k = bin_of[i];
+        const double d = cq - cost[jobs[i]];
+        if (k == h || d <= 0.0 || bl[k] + d >= bl[h]) continue;
+        const double gain = bl[h] - std::max(bl[h] - d, bl[k] + d);
+        if (gain > best) best = gain, bq = q, bi = i, bk = k, swap = true;
+      }
+      for (int32_t k = 0; k < ncta; ++k) {  // moves
+        if (k == h || bl[k] + cq >= bl[h]) continue;
+        const double gain = bl[h] - std::max(bl[h] - cq, bl[k] + cq);
+        if (gain > best) best = gain, bq = q, bk = k, swap = false;
+      }
+    }
+    if (bk < 0) break;
+    bl[h] -= cost[jobs[bq]];
+    bl[bk] += cost[jobs[bq]];
+    bin_of[bq] = bk;
+    if (swap) {
+      bl[bk] -= cost[jobs[bi]];
+      bl[h] += cost[jobs[bi]];
+      bin_of[bi] = h;
     }
   }
   std::vector<std::vector<CholItem>> lists(ncta);
@@ -838,7 +875,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     blk_flops[b] = f;
     c->factor_flops += f;
     chol_diag[b] = kCostDiag * B.nt;
-    chol_cost[b] = chol_diag[b] + (kCostTrsm + kCostSymUpd) * (double)ntrsm + (double)nfull;
+    chol_cost[b] = chol_diag[b] + kCostTrsmSym * (double)ntrsm + (double)nfull;
     chol_sync[b] = 3.0 * kCostPairSync * B.nt;
   }
   c->t_setup_ms = tsetup.stop_ms(s);

@@ -1,6 +1,6 @@
 // Batched Cholesky G_i = L_i L_i^T of the Gram blocks in FP64, in place on the tiled
-// factor layout (tile rows J0(I)..I, T x T row-major tiles).  One CTA per block,
-// right-looking over tile columns K:
+// factor layout (tile rows J0(I)..I, T x T row-major tiles), right-looking over tile
+// columns K:
 //   1. factor the diagonal tile (in shared memory, 16 x 16 sub-blocks), record the pivots;
 //   2. invert L_KK (kept in dinv for the triangular solves);
 //   3. L_IK = G_IK * inv(L_KK)^T for the stored tiles below the diagonal;
@@ -8,22 +8,24 @@
 //      and the fill of a Cholesky factor never leaves the envelope of G).
 // Once row K is final (after step 2 of step K), its off-diagonal tiles are replaced by
 // N_KJ = inv(L_KK) L_KJ, i.e. the factor is stored as L = diag(L_II) (I + N): the
-// diagonal tiles keep L_II and dinv keeps inv(L_II).
+// diagonal tiles keep L_II and dinv keeps inv(L_II).  The N transform runs afterwards in a
+// kernel of its own (every tile independent).
 // Pivot monitoring: min_j of the pivots L_jj^2 (G_jj = 1 after the unit row
 // scaling) and a failure flag for a non-positive or non-finite pivot; a failed
 // pivot is replaced by 1 so that the block finishes without NaNs.
 //
-// GB300's FP64 pipe (about 2 FMA lanes per cycle per SM) bounds this kernel, so every
-// tile product is split into 16 x 16 output units, one warp per unit, and the units skip
-// the work that is zero by structure: the symmetric update of a diagonal tile computes
-// its 10 lower units only, and products with the triangular inv(L_KK) stop the k loop
-// where the triangle ends (k <= column for G inv^T, k <= row for inv L).  Work is then
-// close to the algorithmic count.  The N transform of row K runs afterwards in a kernel of
-// its own (every tile independent), and the diagonal scratch shares shared memory with the
-// operand tiles.  One block per SM: on the 512-block random workload (n = 2^20) the
-// factorisation took 79.9 ms with one, 87.3 ms with two and 99.7 ms with three blocks per
-// SM, so the launch reserves enough shared memory to keep the others off the SM (the rest
-// of the SM's 256 KB stays L1 for the tiles every product re-reads).
+// GB300's FP64 pipe bounds this kernel: each SM sub-partition issues about one FP64 warp
+// instruction every 76 cycles (1.06 TFLOP/s over the GPU).  So every tile product is split
+// into 16 x 16 output units, one warp per unit, balanced over the four sub-partitions, and
+// the units skip the work that is zero by structure: the symmetric update of a diagonal
+// tile computes its 10 lower units only, and products with the triangular inv(L_KK) stop
+// the k loop where the triangle ends (k <= column for G inv^T, k <= row for inv L).  The
+// factorisation of a diagonal tile is a serial pivot chain on one sub-partition; with
+// look-ahead (step 1 of K+1 on warps 0-3 beside step 4 of K on warps 4-7) the update fills
+// the other sub-partitions meanwhile.
+// Scheduling: one CTA per SM (shared memory keeps the others off) walks a list of blocks
+// that the host packs from the blocks' tile counts; a block that would set the time alone
+// is shared by two CTAs of a cooperative launch, which meet at bounded pair barriers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -123,8 +125,18 @@ __device__ __forceinline__ void unit_store(double *out, int R, int C, const doub
   }
 }
 
+// Barrier of a group of NT threads: the whole CTA, or warps 0-3 (ID 1) / 4-7 (ID 2).
+template <int ID, int NT>
+__device__ __forceinline__ void group_sync() {
+  if (NT == kThreads)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory");
+}
+
 // Cholesky L L^T of the 64 x 64 SPD tile in S (lower part read, L written over it) and inv(L)
-// into the lower part of Di, by the CTA's threads, in 16 x 16 sub-blocks so that the 64 pivots
+// into the lower part of Di, by the first NT threads of the CTA (all of them, or warps 0-3
+// with barrier 1), in 16 x 16 sub-blocks so that the 64 pivots
 // take 12 barriers instead of two each:
 //   block column k: warp 0 factors the diagonal sub-block (lane r holds row r in registers; the
 //   columns of L reach the other rows by shuffles), the rows below solve against it (a thread
@@ -138,6 +150,7 @@ __device__ __forceinline__ void unit_store(double *out, int R, int C, const doub
 // above the diagonal of S are never read; Di's are zero inside the diagonal sub-blocks and
 // unset elsewhere.  *pmin receives the smallest pivot of the first `rows` rows; a pivot that is
 // not positive and finite sets *fail and is replaced by 1.  Tmp: 3 x 256 doubles.
+template <int NT>
 __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, int rows,
                                            double *pmin, int *fail) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -178,7 +191,7 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
         if (bad) *fail = 1;
       }
     }
-    __syncthreads();
+    group_sync<1, NT>();
     if (k == 3) break;
     // rows below: L_ic = S_ic L_cc^-T, forward substitution along the row, a thread per row
     const int i = b0 + 16 + t;
@@ -194,10 +207,10 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
 #pragma unroll
       for (int c = 0; c < 16; ++c) S[i * LDS + b0 + c] = x[c];
     }
-    __syncthreads();
+    group_sync<1, NT>();
     // trailing lower triangle: S_ic -= sum_m L_im L_cm over the block column
     const int n = T - b0 - 16, w = n + 1;
-    for (int e = t; e < (n / 2) * w; e += kThreads) {
+    for (int e = t; e < (n / 2) * w; e += NT) {
       const int p = e / w, q = e % w;
       const int ii = b0 + 16 + (q <= p ? p : n - 1 - p);
       const int c = b0 + 16 + (q <= p ? q : q - p - 1);
@@ -206,7 +219,7 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
       for (int m = 0; m < 16; ++m) v = fma(-S[ii * LDS + b0 + m], S[c * LDS + b0 + m], v);
       S[ii * LDS + c] = v;
     }
-    __syncthreads();
+    group_sync<1, NT>();
   }
   // inverse of every diagonal sub-block: warp k, lane c < 16 owns column c (entries above the
   // diagonal are zero, so the sums may start at m = 0)
@@ -226,11 +239,11 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
       for (int i = 0; i < 16; ++i) Di[(b0 + i) * LDS + b0 + c] = col[i];
     }
   }
-  __syncthreads();
+  group_sync<1, NT>();
   for (int d = 1; d < 4; ++d) {
     const int np = 4 - d;  // sub-block pairs (i, k = i - d), i = d..3
     // Tmp_p = sum_{k <= m < i} L_im Di_mk
-    for (int e = t; e < np * 256; e += kThreads) {
+    for (int e = t; e < np * 256; e += NT) {
       const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
       const int bi = d + p, bk = p;
       double v = 0.0;
@@ -238,9 +251,9 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
         v = fma(S[(16 * bi + r) * LDS + m], Di[m * LDS + 16 * bk + c], v);
       Tmp[e] = v;
     }
-    __syncthreads();
+    group_sync<1, NT>();
     // Di_ik = -Di_ii Tmp_p
-    for (int e = t; e < np * 256; e += kThreads) {
+    for (int e = t; e < np * 256; e += NT) {
       const int p = e >> 8, r = (e >> 4) & 15, c = e & 15;
       const int bi = d + p, bk = p;
       double v = 0.0;
@@ -249,7 +262,7 @@ __device__ __noinline__ void diag_factor64(double *S, double *Di, double *Tmp, i
         v = fma(Di[(16 * bi + r) * LDS + 16 * bi + m], Tmp[(p << 8) + m * 16 + c], v);
       Di[(16 * bi + r) * LDS + 16 * bk + c] = -v;
     }
-    __syncthreads();
+    group_sync<1, NT>();
   }
 }
 
@@ -323,7 +336,7 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
       // ---- 1-2. factor the diagonal tile and invert it, in shared memory
       for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = ldg<SPLIT>(gKK + e);
       __syncthreads();
-      diag_factor64(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
+      diag_factor64<kThreads>(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
       // write L_KK (upper part zeroed) and inv(L_KK)
       for (int e = tid; e < T * T; e += kThreads) {
         const int r = e / T, c = e % T;
@@ -432,6 +445,148 @@ __global__ void __launch_bounds__(kThreads) k_pair_selftest(uint64_t limit_ns, i
   pair_sync(flag, 0, 1, err, &s_ok, limit_ns, 16);
 }
 
+// The diagonal tile K factored and inverted by warps 0-3 (barrier 1) in their own shared
+// memory S, Di, Tmp; L_KK and inv(L_KK) are written to fac and dinv.
+__device__ __forceinline__ void factor_diag_group(const BlockDesc &B, const TileRow *tr, int K,
+                                                  double *fac, double *dinv, double *S,
+                                                  double *Di, double *Tmp, double *pmin,
+                                                  int *fail) {
+  const int t = threadIdx.x;
+  double *gKK = tile_ptr(fac, tr[K], K);
+  for (int e = t; e < T * T; e += 128) S[(e / T) * LDS + (e % T)] = gKK[e];
+  group_sync<1, 128>();
+  diag_factor64<128>(S, Di, Tmp, B.m - K * T, pmin, fail);
+  double *dK = dinv + B.dinv_off + (int64_t)K * T * T;
+  for (int e = t; e < T * T; e += 128) {
+    const int r = e / T, c = e % T;
+    gKK[e] = c <= r ? S[r * LDS + c] : 0.0;
+    dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
+  }
+}
+
+// Right-looking Cholesky of one Gram block by one CTA with look-ahead.  Step K: all 8 warps
+// solve the tiles (I, K) and update column K+1 (the tiles (I, K+1)); then warps 0-3 factor
+// the diagonal tile K+1 while warps 4-7 update the rest of the trailing matrix (columns K+2 and
+// on).  The factorisation of a diagonal tile is a serial pivot chain that keeps one SM
+// sub-partition busy at a time; the update warps fill the other three meanwhile.
+__device__ __forceinline__ void factor_block_la(const BlockDesc &B, int b,
+                                                const TileRow *__restrict__ trow,
+                                                double *__restrict__ fac,
+                                                double *__restrict__ dinv,
+                                                double *__restrict__ pivmin,
+                                                int32_t *__restrict__ pivfail, double *At,
+                                                double *Bt, double *Sf, double *Dif,
+                                                double *Tmpf, TileRow *s_tr, double &s_pmin,
+                                                int &s_fail) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int I = tid; I < B.nt; I += kThreads) s_tr[I] = trow[B.trow0 + I];
+  if (tid == 0) {
+    s_pmin = 1e300;
+    s_fail = 0;
+  }
+  __syncthreads();
+  const TileRow *tr = s_tr;
+  if (warp < 4) factor_diag_group(B, tr, 0, fac, dinv, Sf, Dif, Tmpf, &s_pmin, &s_fail);
+  __syncthreads();
+  for (int K = 0; K < B.nt; ++K) {
+    // Bt[k][c] = inv(L_KK)(c, k) for the TRSM (upper triangle: unit column block C needs
+    // k < 16 (C + 1))
+    load_kmajor(dinv + B.dinv_off + (int64_t)K * T * T, Bt);
+    __syncthreads();
+    // ---- 3. L_IK = G_IK * inv(L_KK)^T for every stored tile below the diagonal
+    for (int I = K + 1; I < B.nt; ++I) {
+      const TileRow TI = tr[I];
+      if (TI.j0 > K) continue;
+      double *gIK = tile_ptr(fac, TI, K);
+      load_kmajor(gIK, At);
+      __syncthreads();
+      // unit (R, C) stops at k = 16 (C + 1): warp w takes columns w % 4 and 3 - w % 4, so
+      // every warp (and SM sub-partition) does the same 5 sixteenths of the k range
+      for (int v = 0; v < 2; ++v) {
+        const int R = 2 * (warp >> 2) + v, C = v == 0 ? (warp & 3) : 3 - (warp & 3);
+        double acc[2][4];
+        unit_product(At, Bt, R, C, 16 * (C + 1), acc);
+        unit_store(gIK, R, C, acc, false);
+      }
+      __syncthreads();
+    }
+    // ---- 4a. column K+1 of the trailing update, G_{I,K+1} -= L_IK L_{K+1,K}^T (all warps)
+    if (K + 1 < B.nt && tr[K + 1].j0 <= K) {
+      load_kmajor(tile_ptr(fac, tr[K + 1], K), Bt);
+      for (int I = K + 1; I < B.nt; ++I) {
+        const TileRow TI = tr[I];
+        if (TI.j0 > K) continue;
+        load_kmajor(tile_ptr(fac, TI, K), At);
+        __syncthreads();
+        double *g = tile_ptr(fac, TI, K + 1);
+        if (I > K + 1) {
+          for (int u = warp; u < 16; u += kWarps) {
+            const int R = u >> 2, C = u & 3;
+            double acc[2][4];
+            unit_product(At, Bt, R, C, T, acc);
+            unit_store(g, R, C, acc, true);
+          }
+        } else {
+          for (int u = warp; u < 10; u += kWarps) {
+            int R, C;
+            lower_unit(u, R, C);
+            double acc[2][4];
+            unit_product(At, Bt, R, C, T, acc);
+            unit_store(g, R, C, acc, true);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (warp < 4) {
+      // ---- 1-2 of step K+1: the diagonal tile K+1 (updated by every step up to K)
+      if (K + 1 < B.nt) factor_diag_group(B, tr, K + 1, fac, dinv, Sf, Dif, Tmpf, &s_pmin, &s_fail);
+    } else {
+      // ---- 4b. the rest of the trailing update, G_IJ -= L_IK L_JK^T for K+2 <= J <= I, by
+      // warps 4-7 (barrier 2); a diagonal tile (J = I) takes its lower units only
+      const int tu = tid - 128, wl = warp - 4;
+      for (int I = K + 2; I < B.nt; ++I) {
+        const TileRow TI = tr[I];
+        if (TI.j0 > K) continue;
+        const double *gIK = tile_ptr(fac, TI, K);
+        for (int e = tu; e < T * T; e += 128) At[(e % T) * LD + e / T] = gIK[e];
+        for (int J = K + 2; J <= I; ++J) {
+          const TileRow TJ = tr[J];
+          if (TJ.j0 > K) continue;
+          group_sync<2, 128>();  // previous use of Bt finished
+          const double *gJK = tile_ptr(fac, TJ, K);
+          for (int e = tu; e < T * T; e += 128) Bt[(e % T) * LD + e / T] = gJK[e];
+          group_sync<2, 128>();
+          double *gIJ = tile_ptr(fac, TI, J);
+          if (J < I) {
+            for (int u = wl; u < 16; u += 4) {
+              const int R = u >> 2, C = u & 3;
+              double acc[2][4];
+              unit_product(At, Bt, R, C, T, acc);
+              unit_store(gIJ, R, C, acc, true);
+            }
+          } else {
+            for (int u = wl; u < 10; u += 4) {
+              int R, C;
+              lower_unit(u, R, C);
+              double acc[2][4];
+              unit_product(At, Bt, R, C, T, acc);
+              unit_store(gIJ, R, C, acc, true);
+            }
+          }
+        }
+        group_sync<2, 128>();  // At free for the next row
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    pivmin[b] = s_pmin;
+    pivfail[b] = s_fail;
+  }
+  __syncthreads();  // the shared tables are reused by the CTA's next block
+}
+
 // One CTA per SM walks its list of blocks items[cta_ptr[c] .. cta_ptr[c + 1]) (a static
 // schedule packed on the host from the blocks' measured tile costs); an item with nparts = 2
 // is half of a split block, first in the lists of both CTAs that share it.
@@ -444,7 +599,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *At = reinterpret_cast<double *>(smem_raw);  // [T][LD]
   double *Bt = At + T * LD;                            // [T][LD]
-  double *Tmp = Bt + T * LD;                           // [3 * 256], diagonal phase only
+  double *Sf = Bt + T * LD;                            // [T][LDS], warps 0-3's diagonal tile
+  double *Dif = Sf + T * LDS;                          // [T][LDS]
+  double *Tmpf = Dif + T * LDS;                        // [3 * 256]
   __shared__ double s_pmin;
   __shared__ int s_fail, s_ok;
   __shared__ TileRow s_tr[kMaxBlockRows / T];  // the block's tile-row table
@@ -454,10 +611,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const BlockDesc B = blk[it.b];
     if (it.nparts == 2)
       factor_block<true>(B, it.b, it.part, pair_flags + 2 * it.slot, trow, fac, dinv, pivmin,
-                         pivfail, err, At, Bt, Tmp, s_tr, s_own, s_pmin, s_fail, s_ok);
+                         pivfail, err, At, Bt, Tmpf, s_tr, s_own, s_pmin, s_fail, s_ok);
     else
-      factor_block<false>(B, it.b, 0, nullptr, trow, fac, dinv, pivmin, pivfail, err, At, Bt,
-                          Tmp, s_tr, s_own, s_pmin, s_fail, s_ok);
+      factor_block_la(B, it.b, trow, fac, dinv, pivmin, pivfail, At, Bt, Sf, Dif, Tmpf, s_tr,
+                      s_pmin, s_fail);
   }
 }
 
@@ -603,10 +760,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 constexpr int kCholSmem = (int)sizeof(double) * 2 * T * LD;      // operand tiles
-constexpr int kCholSmemDiag = kCholSmem + (int)sizeof(double) * 3 * 256;  // + Tmp
-// dynamic shared memory requested by k_cholesky: more than half of an SM's 228 KB, so that
-// one block runs per SM (measured fastest, see the header)
-constexpr int kCholSmemLaunch = 120 * 1024;
+// + the look-ahead group's diagonal tile, its inverse and scratch
+constexpr int kCholSmemDiag = kCholSmem + (int)sizeof(double) * (2 * T * LDS + 3 * 256);
+// dynamic shared memory of k_cholesky (one CTA per SM)
+constexpr int kCholSmemLaunch = kCholSmemDiag;
 static_assert(T * LDS <= T * LD, "diagonal scratch inside an operand tile");
 static_assert(kCholSmemLaunch >= kCholSmemDiag, "launch reservation covers the tiles");
 static_assert(kWarps == 8, "unit maps assume 8 warps");
