@@ -342,6 +342,30 @@ int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_t *cci, con
                           int32_t K, int32_t cap, uint64_t seed, int32_t *perm,
                           int64_t *block_ptr, double *cutsize);
 
+/* The static schedule of the FP64 Cholesky (the batched factorisation of the G_i that the
+ * setup runs for FP64 blocks), as a host-only function for inspection and tests; the paper has
+ * no counterpart (it factors each block on its own process).  Block b has nt[b] tile rows of
+ * 64, ntrsm[b] stored tiles (I, K) below the diagonal (each solved once, with the symmetric
+ * update of (I, I)) and nfull[b] full trailing-update tiles (I, J), K < J < I.  Its cost, in
+ * units of one full update tile, is 1.43 nt + 0.81 ntrsm + nfull (weights measured on GB300).
+ * The blocks are packed onto at most maxcta CTA lists by MULTIFIT (the smallest capacity that
+ * first-fit decreasing fills) and a move/swap pass; with allow_split, blocks whose cost
+ * reaches 0.9 of the mean load per CTA may be shared by two CTAs (their diagonal tiles on
+ * part 0, the rest halved, plus 0.09 per tile row for the pair barriers), the split count
+ * chosen from a ladder for the shortest makespan.
+ *   ncta        out: lists used (<= maxcta).
+ *   cta_ptr     out, ncta + 1 entries (caller array of maxcta + 1): list k is items
+ *               cta_ptr[k] .. cta_ptr[k+1] - 1.
+ *   items       out, triples (block, part, nparts) (caller array of 3 * (nblk + maxcta / 2));
+ *               a split block appears twice (parts 0 and 1, nparts = 2), first in two lists.
+ *   nsplit      out: split blocks.  makespan: out, the largest list's cost.
+ * Host-only, no GPU.  Errors: EINVAL (nblk < 0, maxcta < 1, NULL pointers, nt < 1 or
+ * negative counts), ENOMEM. */
+int cimmino_cholesky_schedule(int32_t nblk, const int32_t *nt, const int64_t *ntrsm,
+                              const int64_t *nfull, int32_t maxcta, int32_t allow_split,
+                              int32_t *ncta, int32_t *cta_ptr, int32_t *items, int32_t *nsplit,
+                              double *makespan);
+
 /* Algorithm 1 (Section 1.1): the block Cimmino iteration with relaxation parameter
  * omega, x^(t+1) = x^(t) + omega * sum_i A_i^+ (f_i - A_i x^(t)), from x^(0) = 0, for
  * `sweeps` sweeps, on the same setup (scaling, factors, refinement) as the CG solve.

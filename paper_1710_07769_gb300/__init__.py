@@ -20,7 +20,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["FP64", "FP32_REFINE", "DENSE", "SKYLINE", "CimminoError", "Solver", "BatchSolver",
-           "aat", "partition_rip", "sparsify_dense_columns", "selftest_wait", "fp64_peak", "load",
+           "aat", "partition_rip", "sparsify_dense_columns", "cholesky_schedule", "selftest_wait",
+           "fp64_peak", "load",
            "lib_path", "EXPORTS"]
 
 FP64, FP32_REFINE = 0, 1
@@ -38,7 +39,7 @@ EXPORTS = ["cimmino_opts_default", "cimmino_setup", "cimmino_setup_batch", "cimm
            "cimmino_aat_noalloc",
            "cimmino_partition_rip", "cimmino_sparsify_dense_columns", "cimmino_proj_timing",
            "cimmino_selftest_wait", "cimmino_time_kernels", "cimmino_fp64_peak",
-           "cimmino_version"]
+           "cimmino_cholesky_schedule", "cimmino_version"]
 
 
 class CSRStruct(C.Structure):
@@ -160,6 +161,8 @@ def load(build_if_missing: bool = False):
         L.cimmino_sparsify_dense_columns.argtypes = [i64, vp, vp, vp, vp, vp, vp,
                                                      C.POINTER(i64)]
         L.cimmino_aat_noalloc.argtypes = [C.POINTER(CSRStruct), vp, C.POINTER(i64), vp, vp, vp, i64]
+        L.cimmino_cholesky_schedule.argtypes = [i32, vp, vp, vp, i32, i32, C.POINTER(i32), vp, vp,
+                                                C.POINTER(i32), C.POINTER(dbl)]
         L.cimmino_version.restype = C.c_char_p
         for name in EXPORTS:
             if name not in ("cimmino_free", "cimmino_last_error", "cimmino_version",
@@ -529,6 +532,27 @@ def sparsify_dense_columns(A):
                                                orp.ctypes.data, oci.ctypes.data,
                                                ov.ctypes.data, C.byref(w)))
     return orp, oci[: w.value].copy(), ov[: w.value].copy()
+
+
+def cholesky_schedule(nt, ntrsm, nfull, maxcta: int, allow_split: bool = True):
+    """Static schedule of the FP64 Cholesky for blocks with the given tile counts (host
+    only): returns (lists, nsplit, makespan), lists[k] = [(block, part, nparts), ...] of CTA k."""
+    L = load()
+    nt = _host(nt, np.int32)
+    ntrsm, nfull = _host(ntrsm, np.int64), _host(nfull, np.int64)
+    nblk = len(nt)
+    assert len(ntrsm) == nblk and len(nfull) == nblk
+    ncta, nsplit, mk = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    ptr = np.zeros(int(maxcta) + 1, np.int32)
+    items = np.zeros(3 * (nblk + int(maxcta) // 2 + 1), np.int32)
+    _check(L, L.cimmino_cholesky_schedule(nblk, nt.ctypes.data, ntrsm.ctypes.data,
+                                          nfull.ctypes.data, int(maxcta), int(bool(allow_split)),
+                                          C.byref(ncta), ptr.ctypes.data, items.ctypes.data,
+                                          C.byref(nsplit), C.byref(mk)))
+    it = items.reshape(-1, 3)
+    lists = [[tuple(int(v) for v in it[q]) for q in range(ptr[k], ptr[k + 1])]
+             for k in range(ncta.value)]
+    return lists, int(nsplit.value), float(mk.value)
 
 
 def partition_rip(n: int, aat_csr, K: int, cap: Optional[int] = None, eps: float = 0.0,

@@ -332,7 +332,18 @@ struct CholPlan {
   std::vector<CholItem> items;
   std::vector<int32_t> ptr;  // ncta + 1
   int32_t nsplit = 0;
+  double makespan = 0.0;  // largest list, in cost units
 };
+
+// Cost of one block from its tile counts: nt diagonal tiles, ntrsm solved tiles (I, K) (each
+// with the symmetric update of (I, I)) and nfull full trailing updates; diag: the part of it
+// on the diagonal tiles, sync: the pair barriers of one half when the block is split.
+void chol_block_cost(int32_t nt, int64_t ntrsm, int64_t nfull, double &cost, double &diag,
+                     double &sync) {
+  diag = kCostDiag * nt;
+  cost = diag + kCostTrsmSym * (double)ntrsm + (double)nfull;
+  sync = 3.0 * kCostPairSync * nt;
+}
 
 // First-fit decreasing of jobs (sorted by decreasing cost) into bins of capacity cap on top of
 // the loads `load`; false if a job fits nowhere.
@@ -443,6 +454,7 @@ double pack_cholesky(const std::vector<int32_t> &order, const std::vector<double
     makespan = std::max(makespan, t);
   }
   P.nsplit = ns;
+  P.makespan = makespan;
   return makespan;
 }
 
@@ -874,9 +886,7 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
     }
     blk_flops[b] = f;
     c->factor_flops += f;
-    chol_diag[b] = kCostDiag * B.nt;
-    chol_cost[b] = chol_diag[b] + kCostTrsmSym * (double)ntrsm + (double)nfull;
-    chol_sync[b] = 3.0 * kCostPairSync * B.nt;
+    chol_block_cost(B.nt, ntrsm, nfull, chol_cost[b], chol_diag[b], chol_sync[b]);
   }
   c->t_setup_ms = tsetup.stop_ms(s);
 
@@ -1764,6 +1774,43 @@ int cimmino_fp64_peak(double *tflops) {
     return CIMMINO_OK;
   } catch (const Error &e) {
     return set_error(nullptr, e);
+  }
+}
+
+int cimmino_cholesky_schedule(int32_t nblk, const int32_t *nt, const int64_t *ntrsm,
+                              const int64_t *nfull, int32_t maxcta, int32_t allow_split,
+                              int32_t *ncta, int32_t *cta_ptr, int32_t *items, int32_t *nsplit,
+                              double *makespan) {
+  if (nblk < 0 || maxcta < 1 || (nblk > 0 && (!nt || !ntrsm || !nfull || !items)) || !ncta ||
+      !cta_ptr || !nsplit || !makespan) {
+    g_last_error = "nblk >= 0, maxcta >= 1 and non-NULL arrays required";
+    return CIMMINO_EINVAL;
+  }
+  try {
+    std::vector<double> cost(nblk), diag(nblk), sync(nblk);
+    std::vector<int32_t> blocks(nblk);
+    for (int32_t b = 0; b < nblk; ++b) {
+      if (nt[b] < 1 || ntrsm[b] < 0 || nfull[b] < 0) {
+        g_last_error = "block " + std::to_string(b) + ": nt >= 1, ntrsm >= 0, nfull >= 0 required";
+        return CIMMINO_EINVAL;
+      }
+      chol_block_cost(nt[b], ntrsm[b], nfull[b], cost[b], diag[b], sync[b]);
+      blocks[b] = b;
+    }
+    const CholPlan P = plan_cholesky(blocks, cost, diag, sync, maxcta, allow_split != 0);
+    *ncta = (int32_t)P.ptr.size() - 1;
+    for (size_t k = 0; k < P.ptr.size(); ++k) cta_ptr[k] = P.ptr[k];
+    for (size_t q = 0; q < P.items.size(); ++q) {
+      items[3 * q] = P.items[q].b;
+      items[3 * q + 1] = P.items[q].part;
+      items[3 * q + 2] = P.items[q].nparts;
+    }
+    *nsplit = P.nsplit;
+    *makespan = P.makespan;
+    return CIMMINO_OK;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "out of host memory";
+    return CIMMINO_ENOMEM;
   }
 }
 
