@@ -104,6 +104,55 @@ __device__ __forceinline__ void lower_unit(int u, int &R, int &C) {
   C = u - R * (R + 1) / 2;
 }
 
+// Products with a triangular factor in 32 x 4 strips, one warp each, so that the k bound is
+// the same for the whole warp and follows the triangle to within 4 (16 x 16 units stop only at
+// the unit's last column: 15% more FP64 instructions).
+//   COLS (triangle in the columns of Bt, Bt[k][c] = 0 for k > c, the solves G inv(L)^T):
+//     out(32h + lane, 4g + j) = sum_{k < 4g+4} At[k][32h + lane] Bt[k][4g + j], j < 4;
+//   ROWS (triangle in the rows of At, At[k][r] = 0 for k > r, the transform inv(L) L_KJ):
+//     out(4g + i, 32h + lane) = sum_{k < 4g+4} At[k][4g + i] Bt[k][32h + lane], i < 4.
+// Strip (g, h) costs 4g + 4 k steps: warp w takes g = w and g = 15 - w for both h, the same
+// 136 k steps for every warp and SM sub-partition.  The result is written to the row-major
+// global tile out.
+template <bool COLS>
+__device__ __forceinline__ void tri_strips(const double *At, const double *Bt, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    const int g = v < 2 ? warp : 15 - warp, h = v & 1;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int kend = 4 * g + 4;
+#pragma unroll 4
+    for (int k = 0; k < kend; ++k) {
+      if (COLS) {
+        const double a = At[k * LD + 32 * h + lane];
+        const double2 b0 = *reinterpret_cast<const double2 *>(Bt + k * LD + 4 * g);
+        const double2 b1 = *reinterpret_cast<const double2 *>(Bt + k * LD + 4 * g + 2);
+        acc[0] = fma(a, b0.x, acc[0]);
+        acc[1] = fma(a, b0.y, acc[1]);
+        acc[2] = fma(a, b1.x, acc[2]);
+        acc[3] = fma(a, b1.y, acc[3]);
+      } else {
+        const double2 a0 = *reinterpret_cast<const double2 *>(At + k * LD + 4 * g);
+        const double2 a1 = *reinterpret_cast<const double2 *>(At + k * LD + 4 * g + 2);
+        const double b = Bt[k * LD + 32 * h + lane];
+        acc[0] = fma(a0.x, b, acc[0]);
+        acc[1] = fma(a0.y, b, acc[1]);
+        acc[2] = fma(a1.x, b, acc[2]);
+        acc[3] = fma(a1.y, b, acc[3]);
+      }
+    }
+    if (COLS) {
+      double2 *o = reinterpret_cast<double2 *>(out + (32 * h + lane) * T + 4 * g);
+      o[0] = make_double2(acc[0], acc[1]);
+      o[1] = make_double2(acc[2], acc[3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) out[(4 * g + i) * T + 32 * h + lane] = acc[i];
+    }
+  }
+}
+
 // out(r, c) = acc (mode 0) or out(r, c) -= acc (mode 1) for the lane's elements of unit (R, C)
 // of a row-major global tile.
 template <bool CG = false>
@@ -362,14 +411,7 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
       double *gIK = tile_ptr(fac, TI, K);
       load_kmajor<SPLIT>(gIK, At);
       __syncthreads();
-      // unit (R, C) stops at k = 16 (C + 1): warp w takes columns w % 4 and 3 - w % 4, so
-      // every warp (and SM sub-partition) does the same 5 sixteenths of the k range
-      for (int v = 0; v < 2; ++v) {
-        const int R = 2 * (warp >> 2) + v, C = v == 0 ? (warp & 3) : 3 - (warp & 3);
-        double acc[2][4];
-        unit_product(At, Bt, R, C, 16 * (C + 1), acc);
-        unit_store(gIK, R, C, acc, false);
-      }
+      tri_strips<true>(At, Bt, gIK);  // inv(L_KK)^T is upper triangular
       __syncthreads();
     }
     if (SPLIT) {
@@ -500,14 +542,7 @@ __device__ __forceinline__ void factor_block_la(const BlockDesc &B, int b,
       double *gIK = tile_ptr(fac, TI, K);
       load_kmajor(gIK, At);
       __syncthreads();
-      // unit (R, C) stops at k = 16 (C + 1): warp w takes columns w % 4 and 3 - w % 4, so
-      // every warp (and SM sub-partition) does the same 5 sixteenths of the k range
-      for (int v = 0; v < 2; ++v) {
-        const int R = 2 * (warp >> 2) + v, C = v == 0 ? (warp & 3) : 3 - (warp & 3);
-        double acc[2][4];
-        unit_product(At, Bt, R, C, 16 * (C + 1), acc);
-        unit_store(gIK, R, C, acc, false);
-      }
+      tri_strips<true>(At, Bt, gIK);  // inv(L_KK)^T is upper triangular
       __syncthreads();
     }
     // ---- 4a. column K+1 of the trailing update, G_{I,K+1} -= L_IK L_{K+1,K}^T (all warps)
@@ -742,20 +777,13 @@ __global__ void __launch_bounds__(kThreads)
   if (K >= B.nt) return;
   const TileRow TK = trow[B.trow0 + K];
   if (TK.j0 >= K) return;
-  const int warp = threadIdx.x >> 5;
   load_kmajor(dinv + B.dinv_off + (int64_t)K * T * T, At);
   for (int J = TK.j0; J < K; ++J) {
     double *g = tile_ptr(fac, TK, J);
     __syncthreads();
     load_rowmajor(g, Bt);
     __syncthreads();
-    // unit (R, C) stops at k = 16 (R + 1): warp w takes rows w / 4 and 3 - w / 4 (balanced)
-    for (int v = 0; v < 2; ++v) {
-      const int R = v == 0 ? (warp >> 2) : 3 - (warp >> 2), C = warp & 3;
-      double acc[2][4];
-      unit_product(At, Bt, R, C, 16 * (R + 1), acc);
-      unit_store(g, R, C, acc, false);
-    }
+    tri_strips<false>(At, Bt, g);  // inv(L_KK) is lower triangular
   }
 }
 
