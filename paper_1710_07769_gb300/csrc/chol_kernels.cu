@@ -17,9 +17,10 @@
 // GB300's FP64 pipe bounds this kernel: each SM sub-partition issues about one FP64 warp
 // instruction every 76 cycles (1.06 TFLOP/s over the GPU).  So every tile product is split
 // into 16 x 16 output units, one warp per unit, balanced over the four sub-partitions, and
-// the units skip the work that is zero by structure: the symmetric update of a diagonal
-// tile computes its 10 lower units only, and products with the triangular inv(L_KK) stop
-// the k loop where the triangle ends (k <= column for G inv^T, k <= row for inv L).  The
+// the work that is zero by structure is skipped: the symmetric update of a diagonal tile
+// computes its 36 lower 8 x 8 units only, and the products with the triangular inv(L_KK) run
+// in 32 x 4 strips whose k loop ends where the triangle does (k <= column for G inv^T,
+// k <= row for inv L).  The
 // factorisation of a diagonal tile is a serial pivot chain on one sub-partition; with
 // look-ahead (step 1 of K+1 on warps 0-3 beside step 4 of K on warps 4-7) the update fills
 // the other sub-partitions meanwhile.
@@ -98,10 +99,35 @@ __device__ __forceinline__ void unit_product(const double *At, const double *Bt,
   }
 }
 
-// The 10 lower units (R >= C) of a symmetric tile, in the order R = 0..3, C = 0..R.
-__device__ __forceinline__ void lower_unit(int u, int &R, int &C) {
-  R = u >= 6 ? 3 : u >= 3 ? 2 : u >= 1 ? 1 : 0;
-  C = u - R * (R + 1) / 2;
+// Symmetric update of a diagonal tile, out -= At^T Bt on its lower triangle, in the 36 lower
+// 8 x 8 units (R >= C; 16 x 16 units would leave 10 units to 8 or 4 warps, and compute the
+// upper halves of their diagonal units): warp wl of nw takes units wl, wl + nw, ..., the same
+// 9 units per SM sub-partition for nw = 8 and nw = 4.  Lane (lr, lc) = (lane / 4, lane % 4)
+// owns row 8R + lr, columns 8C + 2lc, +1.  The upper parts of the diagonal units are written
+// too (the upper triangle of a diagonal tile is never read).
+template <bool CG = false>
+__device__ __forceinline__ void sym_update8(const double *At, const double *Bt, double *out,
+                                            int wl, int nw) {
+  const int lane = threadIdx.x & 31, lr = lane >> 2, lc = lane & 3;
+#pragma unroll 1
+  for (int u = wl; u < 36; u += nw) {
+    int R = 0;
+    while ((R + 1) * (R + 2) / 2 <= u) ++R;
+    const int C = u - R * (R + 1) / 2;
+    const double *a = At + 8 * R + lr;
+    const double *b = Bt + 8 * C + 2 * lc;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < T; ++k) {
+      const double x = a[k * LD];
+      const double2 y = *reinterpret_cast<const double2 *>(b + k * LD);
+      a0 = fma(x, y.x, a0);
+      a1 = fma(x, y.y, a1);
+    }
+    double *q = out + (8 * R + lr) * T + 8 * C + 2 * lc;
+    const double2 old = ldg2<CG>(q);
+    *reinterpret_cast<double2 *>(q) = make_double2(old.x - a0, old.y - a1);
+  }
 }
 
 // Products with a triangular factor in 32 x 4 strips, one warp each, so that the k bound is
@@ -455,13 +481,7 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
             unit_store<SPLIT>(gIJ, R, C, acc, true);
           }
         } else {
-          for (int u = warp; u < 10; u += kWarps) {
-            int R, C;
-            lower_unit(u, R, C);
-            double acc[2][4];
-            unit_product(At, Bt, R, C, T, acc);
-            unit_store<SPLIT>(gIJ, R, C, acc, true);
-          }
+          sym_update8<SPLIT>(At, Bt, gIJ, warp, kWarps);
         }
       }
       __syncthreads();
@@ -562,13 +582,7 @@ __device__ __forceinline__ void factor_block_la(const BlockDesc &B, int b,
             unit_store(g, R, C, acc, true);
           }
         } else {
-          for (int u = warp; u < 10; u += kWarps) {
-            int R, C;
-            lower_unit(u, R, C);
-            double acc[2][4];
-            unit_product(At, Bt, R, C, T, acc);
-            unit_store(g, R, C, acc, true);
-          }
+          sym_update8(At, Bt, g, warp, kWarps);
         }
         __syncthreads();
       }
@@ -601,13 +615,7 @@ __device__ __forceinline__ void factor_block_la(const BlockDesc &B, int b,
               unit_store(gIJ, R, C, acc, true);
             }
           } else {
-            for (int u = wl; u < 10; u += 4) {
-              int R, C;
-              lower_unit(u, R, C);
-              double acc[2][4];
-              unit_product(At, Bt, R, C, T, acc);
-              unit_store(gIJ, R, C, acc, true);
-            }
+            sym_update8(At, Bt, gIJ, wl, 4);
           }
         }
         group_sync<2, 128>();  // At free for the next row
