@@ -347,7 +347,7 @@ int cimmino_partition_rip(int64_t n, const int64_t *crp, const int32_t *cci, con
  * no counterpart (it factors each block on its own process).  Block b has nt[b] tile rows of
  * 64, ntrsm[b] stored tiles (I, K) below the diagonal (each solved once, with the symmetric
  * update of (I, I)) and nfull[b] full trailing-update tiles (I, J), K < J < I.  Its cost, in
- * units of one full update tile, is 1.43 nt + 0.81 ntrsm + nfull (weights measured on GB300).
+ * units of one full update tile, is 1.41 nt + 0.59 ntrsm + nfull (weights measured on GB300).
  * The blocks are packed onto at most maxcta CTA lists by MULTIFIT (the smallest capacity that
  * first-fit decreasing fills) and a move/swap pass; with allow_split, blocks whose cost
  * reaches 0.9 of the mean load per CTA may be shared by two CTAs (their diagonal tiles on

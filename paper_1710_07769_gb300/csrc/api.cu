@@ -318,11 +318,11 @@ class Stages {
 
 // ------------------------------------------------------------------ setup
 // ---- static schedule of the FP64 Cholesky (k_cholesky)
-// Cost of a block in units of one full trailing-update tile of k_cholesky (80 us on GB300),
+// Cost of a block in units of one full trailing-update tile of k_cholesky (81 us on GB300),
 // with weights fitted to the measured times of the 512 blocks of the n = 2^20 random workload
-// (0.3% mean error): a diagonal tile's factor and inverse 1.43 (a serial pivot chain, partly
-// hidden by the look-ahead), a solved tile (I, K) with the symmetric update of (I, I) 0.81.
-constexpr double kCostDiag = 1.43, kCostTrsmSym = 0.81;
+// (1.9% mean error): a diagonal tile's factor and inverse 1.41 (a serial pivot chain, partly
+// hidden by the look-ahead), a solved tile (I, K) with the symmetric update of (I, I) 0.59.
+constexpr double kCostDiag = 1.41, kCostTrsmSym = 0.59;
 // A pair barrier of a split block (a few L2 round trips), in the same unit.
 constexpr double kCostPairSync = 0.03;
 // A block whose cost reaches this fraction of the mean load per CTA is split over two CTAs.

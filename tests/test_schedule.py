@@ -10,7 +10,7 @@ import pytest
 
 g = pytest.importorskip("paper_1710_07769_gb300")
 
-W_DIAG, W_TRSM, W_SYNC = 1.43, 0.81, 0.09
+W_DIAG, W_TRSM, W_SYNC = 1.41, 0.59, 0.09
 
 
 def costs(nt, ntr, nfu):
