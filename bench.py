@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (nominal, 152 SMs at 2070 MHz)
 TRAFFIC = {"k_proj_fp64_convdiff3d_64": 659753728, "k_proj_fp32_convdiff3d_64": 726496512,
            "k_proj_fp64_random_dd_n1048576_k8_K512": 3138300000,
            "k_proj_fp32_random_dd_n1048576_k8_K512": 3357500000,
-           "k_cholesky_fp64_random_dd_n1048576_k8_K512": 4994159616}
+           "k_cholesky_fp64_random_dd_n1048576_k8_K512": 5032485376}
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 # projection configurations measured by the library's autotuner during the warm-up steps
 # and reused (from this file) by every later setup of the run
