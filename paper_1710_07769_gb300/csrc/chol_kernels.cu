@@ -379,12 +379,12 @@ __device__ bool pair_sync(int32_t *flag, int part, int32_t epoch, int32_t *err, 
   return *s_ok != 0;
 }
 
-// Right-looking Cholesky of one Gram block (the steps in the file header).  SPLIT: the block
-// is shared by two CTAs (part 0 and 1) that meet at pair barriers three times per tile column:
-// part 0 factors the diagonal tile; the triangular solves alternate between the parts; the
-// update rows go to the part with less update work so far (largest rows first).
-template <bool SPLIT>
-__device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part, int32_t *flag,
+// Right-looking Cholesky of one Gram block (the steps in the file header) shared by two CTAs
+// (part 0 and 1) that meet at pair barriers three times per tile column: part 0 factors the
+// diagonal tile; the triangular solves alternate between the parts; the update rows go to the
+// part with less update work so far (largest rows first).  Tiles the other part writes are
+// read through L2 (CG loads).
+__device__ __forceinline__ void factor_block_split(const BlockDesc &B, int b, int part, int32_t *flag,
                                              const TileRow *__restrict__ trow,
                                              double *__restrict__ fac, double *__restrict__ dinv,
                                              double *__restrict__ pivmin,
@@ -407,9 +407,9 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
     const TileRow TK = tr[K];
     double *gKK = tile_ptr(fac, TK, K);
     double *dK = dinv + B.dinv_off + (int64_t)K * T * T;
-    if (!SPLIT || part == 0) {
+    if (part == 0) {
       // ---- 1-2. factor the diagonal tile and invert it, in shared memory
-      for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = ldg<SPLIT>(gKK + e);
+      for (int e = tid; e < T * T; e += kThreads) S[(e / T) * LDS + (e % T)] = ldg<true>(gKK + e);
       __syncthreads();
       diag_factor64<kThreads>(S, Di, Tmp, B.m - K * T, &s_pmin, &s_fail);
       // write L_KK (upper part zeroed) and inv(L_KK)
@@ -419,58 +419,52 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
         dK[e] = c <= r ? Di[r * LDS + c] : 0.0;
       }
     }
-    if (SPLIT) {
-      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
-    } else {
-      __syncthreads();  // L_KK and inv(L_KK) are in global memory; S / Di are free
-    }
-    // Bt[k][c] = inv(L_KK)(c, k) for the TRSM below (upper triangle: unit column block C
-    // needs k < 16 (C + 1)); read back from dinv
-    load_kmajor<SPLIT>(dK, Bt);
+    if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
+    // Bt[k][c] = inv(L_KK)(c, k) for the triangular solves below (upper triangular); read back
+    // from dinv
+    load_kmajor<true>(dK, Bt);
     __syncthreads();
     // ---- 3. L_IK = G_IK * Di^T for every stored tile below the diagonal
     int q = 0;
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
-      if (SPLIT && (q++ & 1) != part) continue;
+      if ((q++ & 1) != part) continue;
       double *gIK = tile_ptr(fac, TI, K);
-      load_kmajor<SPLIT>(gIK, At);
+      load_kmajor<true>(gIK, At);
       __syncthreads();
       tri_strips<true>(At, Bt, gIK);  // inv(L_KK)^T is upper triangular
       __syncthreads();
     }
-    if (SPLIT) {
-      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
-      // rows of the update: row I costs its tiles (K, I) inside the envelope (3/4 for the
-      // symmetric diagonal one); the larger rows first, each to the part with less so far
-      if (tid == 0) {
-        int w[2] = {0, 0};
-        int act = 0;  // envelope rows in K+1..I
-        for (int I = K + 1; I < B.nt; ++I) act += tr[I].j0 <= K;
-        for (int I = B.nt - 1; I > K; --I) {
-          if (tr[I].j0 > K) continue;
-          const int cost = 4 * act - 1;  // (act - 1) full tiles + 3/4, in quarters
-          const int pick = w[1] < w[0] ? 1 : 0;
-          s_own[I] = (unsigned char)pick;
-          w[pick] += cost;
-          --act;
-        }
+    if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
+    // rows of the update: row I costs its tiles (K, I) inside the envelope (3/4 for the
+    // symmetric diagonal one); the larger rows first, each to the part with less so far
+    if (tid == 0) {
+      int w[2] = {0, 0};
+      int act = 0;  // envelope rows in K+1..I
+      for (int I = K + 1; I < B.nt; ++I) act += tr[I].j0 <= K;
+      for (int I = B.nt - 1; I > K; --I) {
+        if (tr[I].j0 > K) continue;
+        const int cost = 4 * act - 1;  // (act - 1) full tiles + 3/4, in quarters
+        const int pick = w[1] < w[0] ? 1 : 0;
+        s_own[I] = (unsigned char)pick;
+        w[pick] += cost;
+        --act;
       }
-      __syncthreads();
     }
+    __syncthreads();
     // ---- 4. trailing update G_IJ -= L_IK L_JK^T; a diagonal tile (J = I) is symmetric and
     // only its lower units are updated (the upper triangle of G_II is never read)
     for (int I = K + 1; I < B.nt; ++I) {
       const TileRow TI = tr[I];
       if (TI.j0 > K) continue;
-      if (SPLIT && s_own[I] != part) continue;
-      load_kmajor<SPLIT>(tile_ptr(fac, TI, K), At);
+      if (s_own[I] != part) continue;
+      load_kmajor<true>(tile_ptr(fac, TI, K), At);
       for (int J = K + 1; J <= I; ++J) {
         const TileRow TJ = tr[J];
         if (TJ.j0 > K) continue;
         __syncthreads();  // previous use of Bt finished
-        load_kmajor<SPLIT>(tile_ptr(fac, TJ, K), Bt);
+        load_kmajor<true>(tile_ptr(fac, TJ, K), Bt);
         __syncthreads();
         double *gIJ = tile_ptr(fac, TI, J);
         if (J < I) {
@@ -478,21 +472,17 @@ __device__ __forceinline__ void factor_block(const BlockDesc &B, int b, int part
             const int R = u >> 2, C = u & 3;
             double acc[2][4];
             unit_product(At, Bt, R, C, T, acc);
-            unit_store<SPLIT>(gIJ, R, C, acc, true);
+            unit_store<true>(gIJ, R, C, acc, true);
           }
         } else {
-          sym_update8<SPLIT>(At, Bt, gIJ, warp, kWarps);
+          sym_update8<true>(At, Bt, gIJ, warp, kWarps);
         }
       }
       __syncthreads();
     }
-    if (SPLIT) {
-      if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
-    } else {
-      __syncthreads();
-    }
+    if (!pair_sync(flag, part, ++epoch, err, &s_ok)) break;
   }
-  if (tid == 0 && (!SPLIT || part == 0)) {
+  if (tid == 0 && part == 0) {
     pivmin[b] = s_pmin;
     pivfail[b] = s_fail;
   }
@@ -551,8 +541,7 @@ __device__ __forceinline__ void factor_block_la(const BlockDesc &B, int b,
   if (warp < 4) factor_diag_group(B, tr, 0, fac, dinv, Sf, Dif, Tmpf, &s_pmin, &s_fail);
   __syncthreads();
   for (int K = 0; K < B.nt; ++K) {
-    // Bt[k][c] = inv(L_KK)(c, k) for the TRSM (upper triangle: unit column block C needs
-    // k < 16 (C + 1))
+    // Bt[k][c] = inv(L_KK)(c, k) for the triangular solves (upper triangular)
     load_kmajor(dinv + B.dinv_off + (int64_t)K * T * T, Bt);
     __syncthreads();
     // ---- 3. L_IK = G_IK * inv(L_KK)^T for every stored tile below the diagonal
@@ -653,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const CholItem it = items[i];
     const BlockDesc B = blk[it.b];
     if (it.nparts == 2)
-      factor_block<true>(B, it.b, it.part, pair_flags + 2 * it.slot, trow, fac, dinv, pivmin,
+      factor_block_split(B, it.b, it.part, pair_flags + 2 * it.slot, trow, fac, dinv, pivmin,
                          pivfail, err, At, Bt, Tmpf, s_tr, s_own, s_pmin, s_fail, s_ok);
     else
       factor_block_la(B, it.b, trow, fac, dinv, pivmin, pivfail, At, Bt, Sf, Dif, Tmpf, s_tr,
@@ -771,8 +760,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // N_KJ = inv(L_KK) L_KJ in place for every off-diagonal tile of tile row K of the listed
-// blocks (one CTA per block and tile row); inv(L_KK) is lower triangular, so unit row block R
-// needs k < 16 (R + 1).
+// blocks (one CTA per block and tile row); inv(L_KK) is lower triangular, so the strips of
+// rows 4g..4g+3 stop at k = 4g + 4.
 __global__ void __launch_bounds__(kThreads)
     k_ntransform64(const BlockDesc *__restrict__ blk, const int32_t *__restrict__ blist,
                    const TileRow *__restrict__ trow, double *__restrict__ fac,
