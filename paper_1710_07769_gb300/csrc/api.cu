@@ -497,24 +497,39 @@ CholPlan plan_cholesky(const std::vector<int32_t> &blocks, const std::vector<dou
 
 // Uploads a plan and runs k_cholesky on it (the flags and the error word zeroed first);
 // returns after the launch, the buffers stay alive in `keep` until the caller synchronises.
+// A plan with split blocks needs all its CTAs resident at once (a cooperative launch); if the
+// device refuses that (other work holding SMs), `replan` (the same blocks without splits) runs
+// as a plain grid instead.  Returns the split blocks of the plan that ran.
 struct CholLaunchBufs {
   DBuf<CholItem> items;
   DBuf<int32_t> ptr, flags, err;
 };
-void run_cholesky64(cimmino_ctx *c, const CholPlan &P, double *pmin, int32_t *pfail,
-                    CholLaunchBufs &keep, cudaStream_t s) {
-  const int32_t ncta = (int32_t)P.ptr.size() - 1;
-  if (ncta <= 0) return;
-  keep.items.alloc(P.items.size());
-  keep.ptr.alloc(P.ptr.size());
-  keep.flags.alloc(std::max<int32_t>(2 * P.nsplit, 1));
-  keep.err.alloc(1);
-  h2d(keep.items.p, P.items.data(), P.items.size(), s);
-  h2d(keep.ptr.p, P.ptr.data(), P.ptr.size(), s);
-  CUDA_TRY(cudaMemsetAsync(keep.flags.p, 0, keep.flags.n * sizeof(int32_t), s));
-  CUDA_TRY(cudaMemsetAsync(keep.err.p, 0, sizeof(int32_t), s));
-  CUDA_TRY(launch_cholesky(c->blk.p, keep.items.p, keep.ptr.p, ncta, P.nsplit > 0, c->trow.p,
-                           c->fac64.p, c->dinv64.p, pmin, pfail, keep.flags.p, keep.err.p, s));
+template <typename Replan>
+int32_t run_cholesky64(cimmino_ctx *c, const CholPlan &P, Replan replan, double *pmin,
+                       int32_t *pfail, CholLaunchBufs &keep, cudaStream_t s) {
+  auto run = [&](const CholPlan &Q) {
+    const int32_t ncta = (int32_t)Q.ptr.size() - 1;
+    keep.items.alloc(Q.items.size());
+    keep.ptr.alloc(Q.ptr.size());
+    keep.flags.alloc(std::max<int32_t>(2 * Q.nsplit, 1));
+    keep.err.alloc(1);
+    h2d(keep.items.p, Q.items.data(), Q.items.size(), s);
+    h2d(keep.ptr.p, Q.ptr.data(), Q.ptr.size(), s);
+    CUDA_TRY(cudaMemsetAsync(keep.flags.p, 0, keep.flags.n * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(keep.err.p, 0, sizeof(int32_t), s));
+    return launch_cholesky(c->blk.p, keep.items.p, keep.ptr.p, ncta, Q.nsplit > 0, c->trow.p,
+                           c->fac64.p, c->dinv64.p, pmin, pfail, keep.flags.p, keep.err.p, s);
+  };
+  if ((int32_t)P.ptr.size() - 1 <= 0) return 0;
+  cudaError_t e = run(P);
+  if (P.nsplit > 0 && e == cudaErrorCooperativeLaunchTooLarge) {
+    (void)cudaGetLastError();  // a refused launch ran nothing
+    const CholPlan Q = replan();
+    CUDA_TRY(run(Q));
+    return Q.nsplit;
+  }
+  CUDA_TRY(e);
+  return P.nsplit;
 }
 
 // Resident CTAs of k_cholesky and whether a schedule may split blocks (cooperative launch).
@@ -927,12 +942,14 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
   if (fp64) {
     cholesky_capacity(maxcta, allow_split);
     plan = plan_cholesky(hlist, chol_cost, chol_diag, chol_sync, maxcta, allow_split);
-    c->chol_split = plan.nsplit;
   }
   Timer tchol;
   tchol.start(s);
   if (fp64) {
-    run_cholesky64(c, plan, pmin.p, pfail.p, cbufs, s);
+    c->chol_split = run_cholesky64(
+        c, plan,
+        [&] { return plan_cholesky(hlist, chol_cost, chol_diag, chol_sync, maxcta, false); },
+        pmin.p, pfail.p, cbufs, s);
   } else {
     launch_cholesky_tc(c->blk.p, blist.p, nblk, nblk, ntrow, c->trow.p, c->fac32.p, c->dinv32.p,
                        tc_scratch.p, off, tc_rowblk.p, pmin.p, pfail.p, c->err_flag.p, s);
@@ -988,13 +1005,15 @@ void setup_impl(cimmino_ctx *c, int32_t nsys, const cimmino_csr *A, const int32_
                           c->bcv.p, c->fac64.p, (int64_t)c->fac64.n, 1, s);
       if (maxcta == 0) cholesky_capacity(maxcta, allow_split);
       CholLaunchBufs fbufs;
-      run_cholesky64(c, plan_cholesky(fb, chol_cost, chol_diag, chol_sync, maxcta, allow_split), pmin.p,
-                     pfail.p, fbufs, s);
+      run_cholesky64(
+          c, plan_cholesky(fb, chol_cost, chol_diag, chol_sync, maxcta, allow_split),
+          [&] { return plan_cholesky(fb, chol_cost, chol_diag, chol_sync, maxcta, false); },
+          pmin.p, pfail.p, fbufs, s);
       launch_ntransform64(c->blk.p, blist.p, (int32_t)fb.size(), c->trow.p, c->fac64.p,
                           c->dinv64.p, s);
       c->setup_launches += 3;
       d2h(hfail.data(), pfail.p, nblk, s);
-      d2h(&hcerr, fbufs.err.p, 1, s);
+      if (fbufs.err.p) d2h(&hcerr, fbufs.err.p, 1, s);
       CUDA_TRY(cudaStreamSynchronize(s));
       if (hcerr) fail(CIMMINO_ETIMEOUT, "a pair wait of the FP64 Cholesky ran out (split block)");
       for (int32_t b : fb)
